@@ -1,0 +1,362 @@
+"""Throughput bench: one shared homogeneous support, a batch of signals.
+
+Workload (default): N = 2^20, k = 2^12, batch 4096, complex64 samples already
+resident in HBM; one step = one call of the strided transform over the whole
+batch. Prints ONE JSON line (rank 0).
+
+Legs:
+  * value        device-timed coeffs/s of the batched complex64 path (CUDA
+                 events around each step on the launching stream, L2 flushed
+                 between steps, untimed)
+  * e2e          the same through the public API with pinned host buffers,
+                 H2D of the samples and D2H of the coefficients inside the timing
+  * fp64         the plain per-instance complex128 path (one call per instance)
+                 and the batched complex128 path, device-timed
+  * roofline     algorithmic bytes / kernel time against measured HBM bandwidth
+  * cpu_baseline the FP64 oracle (dense k x k solve) on a bounded sample, on
+                 the host cores, with its relative L2 against the GPU output
+`--impl reference` times only the oracle (the reference arm of this tier).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "coeffs/s batched FP32 vs plain per-instance FP64 at relL2≤1e-5; p50/p99 latency"
+UNIT = "coeffs/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_device_steps(fn, steps, warmup, flush, stream):
+    """Per-step CUDA-event timing on `stream`, L2 flushed (untimed) between steps."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) * 1e-3 for a, b in ev]
+
+
+def run_ours(args):
+    import torch
+    from paper_2211_15299_gb300 import Plan
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    M, s, batch = args.log2n, args.log2k, args.batch
+    inst, _ = W.workload_shared(M=M, s=s, batch=1, coeffs=False)
+    k = inst.k
+    plan32 = Plan(M, inst.J, "c64")
+    plan64 = Plan(M, inst.J, "c128")
+    n_levels = 1 + max(0, -(-(s - 12) // 8)) if s > 4 else 1
+
+    # Synthetic samples: any vector of k samples is the sample set of exactly one
+    # signal supported on J (F(J, I) is invertible), so complex Gaussian samples are
+    # a valid input; seeded per rank (replicas, weak scaling).
+    g = torch.Generator(device=dev)
+    g.manual_seed(W.BASE_SEED + 2 + 1000 * rank)
+    x32 = torch.randn((batch, k), dtype=torch.complex64, device=dev, generator=g)
+    y32 = torch.empty_like(x32)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan32.execute_strided(x32, y32, stream=stream.cuda_stream)
+
+    _barrier(ws)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        _barrier(ws)
+        times = time_device_steps(step, args.steps, args.warmup, flush, stream)
+        _barrier(ws)
+        torch.cuda.synchronize()
+    total = _max_over_ranks(ws, sum(times))
+    coeffs_per_step = batch * k
+    value = ws * coeffs_per_step * args.steps / total
+    ms_per_step = 1e3 * total / args.steps
+
+    # roofline of the dominant kernel (the single level-0 launch per step here)
+    peak, peak_kind = _peaks()
+    alg_bytes = 16 * coeffs_per_step + 8 * (k - 1)
+    kern_s = statistics.mean(times) / n_levels if n_levels == 1 else None
+    achieved = alg_bytes / statistics.mean(times) / 1e9
+    traffic = _committed_traffic(M, s, batch)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "k_level<float,0,12,true>" if n_levels == 1 else "multi-level",
+                "alg_bytes_per_launch": alg_bytes}
+
+    # FP64: batched and plain per-instance (one call per instance), device-timed
+    x64 = x32.to(torch.complex128)
+    y64 = torch.empty_like(x64)
+
+    def step64():
+        plan64.execute_strided(x64, y64, stream=stream.cuda_stream)
+
+    t64 = time_device_steps(step64, max(2, args.steps // 4), 2, flush, stream)
+    fp64_batched = coeffs_per_step / statistics.mean(t64)
+    n_pi = min(batch, 512)
+
+    def step64_per_instance():
+        for b in range(n_pi):
+            plan64.execute(x64[b], y64[b], stream=stream.cuda_stream)
+
+    tpi = time_device_steps(step64_per_instance, 3, 1, flush, stream)
+    fp64_per_instance = n_pi * k / statistics.mean(tpi)
+    # accuracy of the FP32 path against the FP64 path on the same input
+    step()
+    step64()
+    torch.cuda.synchronize()
+    d = (y32.to(torch.complex128) - y64)
+    rel_fp32_vs_fp64 = float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(y64))
+
+    # e2e through the public API: pinned host -> device, transform, device -> host
+    h_in = x32.cpu().pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in = torch.empty_like(x32)
+    d_out = torch.empty_like(x32)
+
+    def e2e_step():
+        d_in.copy_(h_in, non_blocking=True)
+        plan32.execute_strided(d_in, d_out, stream=stream.cuda_stream)
+        h_out.copy_(d_out, non_blocking=True)
+
+    te = time_device_steps(e2e_step, max(3, args.steps // 4), 2, flush, stream)
+    e2e_total = _max_over_ranks(ws, sum(te))
+    e2e_val = ws * coeffs_per_step * len(te) / e2e_total
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(inst, x32, y32, args.cpu_sample)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"shared support N=2^{M} k=2^{s} batch {batch} complex64 (strided, one plan)",
+                   "log2N": M, "log2k": s, "batch": batch, "pivots": [int(p) for p in inst.pivots],
+                   "l2": "flushed between steps (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(8 * coeffs_per_step),
+                "d2h_bytes_per_step": int(8 * coeffs_per_step)},
+        "gpu_launches": int(args.steps * n_levels),
+        "roofline": roofline,
+        "fp64": {"batched_coeffs_per_s": fp64_batched, "per_instance_coeffs_per_s": fp64_per_instance,
+                 "per_instance_sample": n_pi, "fp32_speedup_vs_per_instance": value / ws / fp64_per_instance},
+        "rel_l2_fp32_vs_fp64": rel_fp32_vs_fp64,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _committed_traffic(M, s, batch):
+    """DRAM bytes per launch from the committed ncu summary, if it still matches the kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        import hashlib
+        with open(os.path.join(ROOT, "paper_2211_15299_gb300", "csrc", "kernels.cuh"), "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()[:16]
+        e = d.get(f"{M}/{s}/{batch}")
+        if e and e.get("kernels_cuh_sha") == h:
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(inst, x32, y32, sample):
+    """The FP64 oracle's dense solve on `sample` instances of the same input."""
+    import oracle as O
+    Jc = O.canonical_support_by_key(inst.J, inst.pivots)
+    I = O.sample_set(inst.M, inst.pivots)
+    F = x32[:sample].cpu().numpy().astype(np.complex128)
+    t0 = time.perf_counter()
+    C = O.solve(inst.M, Jc, I, F)
+    dt = time.perf_counter() - t0
+    got = y32[:sample].cpu().numpy().astype(np.complex128)
+    rel = float(np.linalg.norm(got - C) / np.linalg.norm(C))
+    return {"value": sample * inst.k / dt, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"{sample} of the batch's instances, dense k x k LU solve (one factorisation)",
+            "seconds": dt, "rel_l2_gpu_fp32_vs_oracle": rel}
+
+
+def _blas_threads():
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(v):
+            return int(os.environ[v])
+    return os.cpu_count()
+
+
+def run_reference(args):
+    """The oracle on the host cores (rank 0 only), bounded samples of the workload."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+    M, s = args.log2n, args.log2k
+    inst, _ = W.workload_shared(M=M, s=s, batch=1, coeffs=False)
+    rng = W.rng_for(2, 555)
+    Jc = O.canonical_support_by_key(inst.J, inst.pivots)
+    I = O.sample_set(inst.M, inst.pivots)
+    sample = args.cpu_sample
+    F = W.complex_gaussian((sample, inst.k), rng)
+    for _ in range(max(1, min(args.warmup, 1))):
+        O.solve(M, Jc, I, F[:8])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.solve(M, Jc, I, F)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sample * inst.k * args.steps / total
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"shared support N=2^{M} k=2^{s} batch {args.batch} complex64 (strided, one plan)",
+                      "log2N": M, "log2k": s, "batch": args.batch},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+                            "sample": f"{sample} instances per step, dense k x k LU solve"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2n", type=int, default=20)
+    ap.add_argument("--log2k", type=int, default=12)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--cpu-sample", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * sdft.h - C ABI of the GB300 generalized radix-2 transform for signals whose
+ * DFT is supported on a known homogeneous set (arxiv 2211.15299, "Fast DFT
+ * Computation for Signals with Structured Support").
+ *
+ * Problem (Section II, Definitions 1 and 3): N = 2^log2N, a support J of k
+ * distinct frequencies, and a signal f whose DFT F f (F(m,n) = exp(-2 pi i m n/N))
+ * vanishes off J. Given J and k samples of f, return (F f)_J.
+ *
+ * Method (Sections VI-VIII): J must be homogeneous (Definition 9: its congruence
+ * tree has exactly log2 k split levels, the pivots r_1 < ... < r_s, k = 2^s).
+ * The samples are read at the pivoted sampling pattern I_r (Definition
+ * "r_sampling_pattern") and combined by s butterfly levels (Lemma
+ * "rec-hom-tree-split", Corollary "block-structure", Algorithm 1). The result is
+ * (N/k) times the height-0 Hi-DFT (eq. "hom-implies-spectral" with the 1/N of
+ * F^{-1} kept), exactly, up to floating-point rounding.
+ *
+ * Orders used by every call:
+ *   sample t (0 <= t < k) is f(I[t]) with I[t] = sum_q bit_q(t) 2^(log2N-1-r_{q+1});
+ *   coefficient t is (F f)(Jc[t]) with Jc[t] the element of J whose bit r_{q+1}
+ *   equals bit_q(t) for every q (the canonical order; Corollary "block-structure").
+ * sdft_plan_sample_indices and sdft_plan_support_order return I and Jc.
+ *
+ * Data layout: complex values are interleaved (re, im); complex64 = 2 x float,
+ * complex128 = 2 x double. Device buffers are owned by the caller, must be
+ * 16-byte aligned, and hold k values per instance, instances packed back to back.
+ *
+ * Errors: every call returns an sdft_status; nothing is thrown across the ABI.
+ * Execute calls are asynchronous on the given stream; a CUDA error raised by a
+ * launch is returned as SDFT_ERR_CUDA (call sdft_last_cuda_error for the code).
+ * Kernel-side bounded waits that expire set a device status word read by
+ * sdft_plan_device_status / sdft_batch_device_status (SDFT_ERR_TIMEOUT).
+ *
+ * Streams are passed as `void*` holding a cudaStream_t (NULL = legacy default).
+ */
+#ifndef SDFT_H
+#define SDFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdft_plan_s* sdft_plan;
+typedef struct sdft_batch_s* sdft_batch;
+
+typedef enum {
+  SDFT_OK = 0,
+  SDFT_ERR_ARG = 1,             /* null pointer, bad size, misaligned buffer      */
+  SDFT_ERR_NOT_POW2 = 2,        /* k is not a power of two                       */
+  SDFT_ERR_RANGE = 3,           /* an element of J is >= N, or log2N too large   */
+  SDFT_ERR_DUPLICATE = 4,       /* J has a repeated element                      */
+  SDFT_ERR_NOT_HOMOGENEOUS = 5, /* number of pivots differs from log2 k          */
+  SDFT_ERR_NOMEM = 6,           /* host or device allocation failed              */
+  SDFT_ERR_BUDGET = 7,          /* request exceeds a caller-set memory budget    */
+  SDFT_ERR_CUDA = 8,            /* a CUDA runtime/driver call failed             */
+  SDFT_ERR_TIMEOUT = 9,         /* a bounded device-side wait expired            */
+  SDFT_ERR_UNSUPPORTED = 10,    /* size or mode outside what this build supports */
+  SDFT_ERR_NO_DEVICE = 11,      /* plan was created host-only / no CUDA device   */
+  SDFT_ERR_PRECISION = 12       /* plans of different precision mixed in a batch */
+} sdft_status;
+
+typedef enum { SDFT_C64 = 0, SDFT_C128 = 1 } sdft_prec;
+
+/* Plan flags. */
+#define SDFT_PLAN_HOST_ONLY 0x1u /* build the host tables only; no device upload */
+
+/* Largest log2N and log2 k this build accepts. */
+#define SDFT_MAX_LOG2N 62u
+#define SDFT_MAX_LOG2K 28u
+
+/*
+ * sdft_plan_create - validate J, find its pivots, order it, build I_r and the
+ * twiddles, and upload the tables to the current CUDA device.
+ *   log2N  : M, with N = 2^M, 0 <= M <= SDFT_MAX_LOG2N.
+ *   J      : host array of k distinct frequencies in [0, N), any order; read only
+ *            during the call.
+ *   k      : |J|, a power of two, k <= 2^SDFT_MAX_LOG2K.
+ *   prec   : arithmetic of the device path (complex64 or complex128 buffers).
+ *   flags  : 0 or SDFT_PLAN_HOST_ONLY.
+ *   out    : receives the plan; the caller owns it (sdft_plan_destroy).
+ * Pivots: the levels l at which the congruence tree T(J) splits (Definition 8),
+ * found as the 2-adic valuations of differences of neighbours in bit-reversed
+ * order (Remark "tree-2-adic", Remark "pivot-as-gcd").
+ * Homogeneity: exactly log2 k pivots (Definition 9, Proposition "hom-tree-prop").
+ * Twiddles: stage m (1..s) and u < 2^(m-1) use
+ *   exp(-2 pi i (Jc[u] mod 2^(r_m)) / 2^(r_m+1)),
+ * i.e. omega_{r_m+1}^{Jc[u]} of Lemma "rec-hom-tree-split", evaluated in FP64 and
+ * rounded once to the plan's precision.
+ * Errors: SDFT_ERR_ARG, _NOT_POW2, _RANGE, _DUPLICATE, _NOT_HOMOGENEOUS, _NOMEM,
+ * _CUDA, _UNSUPPORTED; *out is left NULL on error.
+ */
+sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft_prec prec,
+                             uint32_t flags, sdft_plan* out);
+
+/* log2N, s = log2 k and precision of a plan. Any output pointer may be NULL. */
+sdft_status sdft_plan_info(sdft_plan plan, uint32_t* log2N, uint32_t* log2k, sdft_prec* prec);
+
+/* The s pivots r_1 < ... < r_s (Definition 8), written to host array `pivots`. */
+sdft_status sdft_plan_pivots(sdft_plan plan, uint32_t* pivots);
+
+/* I_r in sample order t = 0..k-1 (Definition "r_sampling_pattern"), host array of k. */
+sdft_status sdft_plan_sample_indices(sdft_plan plan, uint64_t* I);
+
+/* J in coefficient order t = 0..k-1 (canonical order), host array of k. */
+sdft_status sdft_plan_support_order(sdft_plan plan, uint64_t* Jc);
+
+/* The FP64 twiddles before rounding, stage-major: for m = 1..s and u < 2^(m-1),
+ * (re, im) at tw[2 * (2^(m-1) - 1 + u)]; 2 * (k - 1) doubles. Unscaled. */
+sdft_status sdft_plan_twiddles(sdft_plan plan, double* tw);
+
+/* Device bytes held by the plan (tables and status word). */
+sdft_status sdft_plan_device_bytes(sdft_plan plan, uint64_t* bytes);
+
+/*
+ * sdft_execute - one instance: d_coeffs[t] = (F f)(Jc[t]) from d_samples[t] = f(I[t]).
+ * d_samples, d_coeffs: device buffers of k complex values of the plan's
+ * precision, 16-byte aligned; they must not overlap (in-place is not supported).
+ * Asynchronous on `stream`; allocates nothing; may run concurrently on one plan.
+ */
+sdft_status sdft_execute(sdft_plan plan, const void* d_samples, void* d_coeffs, void* stream);
+
+/*
+ * sdft_execute_strided - `batch` instances of one plan; instance b reads
+ * d_samples + b*k and writes d_coeffs + b*k (complex elements). Same rules as
+ * sdft_execute. One persistent launch per butterfly level (one launch when
+ * k <= 2^12 for complex64, 2^11 for complex128).
+ */
+sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_samples,
+                                 void* d_coeffs, void* stream);
+
+/* Device status word of a plan: SDFT_OK or SDFT_ERR_TIMEOUT; synchronises the
+ * device; clears the word when `clear` is non-zero. */
+sdft_status sdft_plan_device_status(sdft_plan plan, int clear);
+
+/* Release a plan. The caller must first synchronise any work using it. */
+sdft_status sdft_plan_destroy(sdft_plan plan);
+
+/* ------------------------------------------------------------------------ */
+/* Uneven batches: many instances, each with its own plan, in one launch.    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * sdft_batch_create - build a device work queue for instances i = 0..n-1 with
+ * plans[i] (repeats allowed; all of one precision). Instance i's k_i samples and
+ * coefficients sit at element offset offsets[i] of the packed buffers, with
+ * offsets[0] = 0 and offsets[i+1] = offsets[i] + k_i (see sdft_batch_info).
+ * The plans must outlive the batch. Allocates the queue on the current device.
+ */
+sdft_status sdft_batch_create(const sdft_plan* plans, uint64_t n, sdft_batch* out);
+
+/* Total coefficients, and (if `offsets` is not NULL) the n+1 element offsets. */
+sdft_status sdft_batch_info(sdft_batch batch, uint64_t* total, uint64_t* offsets);
+
+/*
+ * sdft_batch_execute - run every instance of the batch: one persistent kernel
+ * over the work queue. Buffers as described at sdft_batch_create, 16-byte
+ * aligned, not overlapping. Asynchronous, allocates nothing, and may be
+ * captured into a CUDA graph.
+ */
+sdft_status sdft_batch_execute(sdft_batch batch, const void* d_samples, void* d_coeffs,
+                               void* stream);
+
+/* Device status word of a batch (as for plans). */
+sdft_status sdft_batch_device_status(sdft_batch batch, int clear);
+
+/* Release a batch after synchronising its work. */
+sdft_status sdft_batch_destroy(sdft_batch batch);
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Static text for a status code. */
+const char* sdft_status_string(sdft_status status);
+
+/* The cudaError_t value behind the last SDFT_ERR_CUDA returned on this thread. */
+int sdft_last_cuda_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int sdft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDFT_H */

@@ -364,3 +364,76 @@ def theorem1_opcount(s: int) -> int:
     """T(0) = 1.5 A log A + A with A = 2^s (Theorem "computation_Hi-DFT")."""
     A = 1 << s
     return int(1.5 * A * s + A)
+
+
+# ---------------------------------------------------------------------------
+# Level-by-level forms for large k (same arithmetic as the recursions above,
+# vectorised over a batch; pinned against them in the tests)
+# ---------------------------------------------------------------------------
+
+
+def canonical_support_by_key(J, r: Sequence[int]) -> np.ndarray:
+    """The canonical order of `canonical_support`, computed directly: element j
+    goes to position sum_q bit_{r_q}(j) 2^{q-1} (its pivot bits read as a
+    binary number, r_1 least significant). Raises if two elements collide."""
+    J = np.asarray(J, dtype=np.uint64)
+    key = np.zeros(J.size, dtype=np.int64)
+    for q, rq in enumerate(r):
+        key |= (((J >> np.uint64(int(rq))) & np.uint64(1)).astype(np.int64)) << q
+    out = np.zeros(J.size, dtype=np.uint64)
+    if np.unique(key).size != J.size:
+        raise ValueError("support is not homogeneous for these pivots")
+    out[key] = J
+    return out
+
+
+def _omegas(M: int, r: Sequence[int], Jc: np.ndarray) -> List[np.ndarray]:
+    """omega vector of each recursion depth m = 1..s: exp(-2 pi i a_m J(0:2^{m-1}-1)/N),
+    a_m = 2^{M-1-r_m}."""
+    return [_omega(M, 1 << (M - 1 - int(r[m - 1])), Jc[: 1 << (m - 1)]) for m in range(1, len(r) + 1)]
+
+
+def hidft_levels(f_I, r: Sequence[int], Jc, M: int) -> np.ndarray:
+    """F(J, I_r) f_I with Algorithm 1's recursion unrolled bottom-up: at depth m
+    every block of 2^m samples is [f1 + w f2, f1 - w f2] of its two halves.
+    `f_I` is (k,) or (B, k)."""
+    x = np.array(f_I, dtype=np.complex128, copy=True)
+    squeeze = x.ndim == 1
+    if squeeze:
+        x = x[None, :]
+    B, k = x.shape
+    Jc = np.asarray(Jc, dtype=np.uint64)
+    for m, w in enumerate(_omegas(M, r, Jc), start=1):
+        half = 1 << (m - 1)
+        x = x.reshape(B, k // (2 * half), 2, half)
+        t = x[:, :, 1, :] * w
+        a = x[:, :, 0, :]
+        x = np.stack([a + t, a - t], axis=2).reshape(B, k)
+    return x[0] if squeeze else x
+
+
+def transform_levels(M: int, r: Sequence[int], Jc, f_I) -> np.ndarray:
+    """c = (N/k) F(J, I_r) f_I aligned with Jc, via `hidft_levels`."""
+    Jc = np.asarray(Jc, dtype=np.uint64)
+    return hidft_levels(f_I, r, Jc, M) * (float(1 << M) / Jc.size)
+
+
+def synthesize_levels(M: int, r: Sequence[int], Jc, c) -> np.ndarray:
+    """f_I = (1/N) F(J, I_r)^H c with `hidft_adjoint` unrolled top-down.
+    `c` is (k,) or (B, k) aligned with Jc; result in sample order."""
+    y = np.array(c, dtype=np.complex128, copy=True)
+    squeeze = y.ndim == 1
+    if squeeze:
+        y = y[None, :]
+    B, k = y.shape
+    Jc = np.asarray(Jc, dtype=np.uint64)
+    ws = _omegas(M, r, Jc)
+    nblk = 1
+    for m in range(len(r), 0, -1):
+        half = 1 << (m - 1)
+        y = y.reshape(B, nblk, 2, half)
+        a, b = y[:, :, 0, :], y[:, :, 1, :]
+        y = np.stack([a + b, np.conj(ws[m - 1]) * (a - b)], axis=2).reshape(B, 2 * nblk, half)
+        nblk *= 2
+    y = y.reshape(B, k) / float(1 << M)
+    return y[0] if squeeze else y

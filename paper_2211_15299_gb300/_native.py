@@ -1,0 +1,212 @@
+"""ctypes binding of libsdft.so: the C ABI of include/sdft.h, same names.
+
+Argument marshalling only: every step of the transform runs in the library's
+CUDA kernels. Device buffers are passed as raw pointers; any object with a
+`data_ptr()` method (a torch tensor) or an int address is accepted. Streams
+are passed as cudaStream_t values (int) or objects with a `cuda_stream`
+attribute (torch.cuda.Stream). There is no fallback: if the library is not
+built, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsdft.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+c_u32, c_u64, c_int, c_vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
+P_u32 = ctypes.POINTER(ctypes.c_uint32)
+P_u64 = ctypes.POINTER(ctypes.c_uint64)
+P_f64 = ctypes.POINTER(ctypes.c_double)
+
+SDFT_C64, SDFT_C128 = 0, 1
+SDFT_PLAN_HOST_ONLY = 0x1
+
+STATUS = {
+    0: "SDFT_OK", 1: "SDFT_ERR_ARG", 2: "SDFT_ERR_NOT_POW2", 3: "SDFT_ERR_RANGE",
+    4: "SDFT_ERR_DUPLICATE", 5: "SDFT_ERR_NOT_HOMOGENEOUS", 6: "SDFT_ERR_NOMEM",
+    7: "SDFT_ERR_BUDGET", 8: "SDFT_ERR_CUDA", 9: "SDFT_ERR_TIMEOUT", 10: "SDFT_ERR_UNSUPPORTED",
+    11: "SDFT_ERR_NO_DEVICE", 12: "SDFT_ERR_PRECISION",
+}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
+
+# Every symbol declared in include/sdft.h: name -> (restype, argtypes)
+SIGNATURES = {
+    "sdft_plan_create": (c_int, [c_u32, P_u64, c_u64, c_int, c_u32, ctypes.POINTER(c_vp)]),
+    "sdft_plan_info": (c_int, [c_vp, P_u32, P_u32, ctypes.POINTER(c_int)]),
+    "sdft_plan_pivots": (c_int, [c_vp, P_u32]),
+    "sdft_plan_sample_indices": (c_int, [c_vp, P_u64]),
+    "sdft_plan_support_order": (c_int, [c_vp, P_u64]),
+    "sdft_plan_twiddles": (c_int, [c_vp, P_f64]),
+    "sdft_plan_device_bytes": (c_int, [c_vp, P_u64]),
+    "sdft_execute": (c_int, [c_vp, c_vp, c_vp, c_vp]),
+    "sdft_execute_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
+    "sdft_plan_device_status": (c_int, [c_vp, c_int]),
+    "sdft_plan_destroy": (c_int, [c_vp]),
+    "sdft_batch_create": (c_int, [ctypes.POINTER(c_vp), c_u64, ctypes.POINTER(c_vp)]),
+    "sdft_batch_info": (c_int, [c_vp, P_u64, P_u64]),
+    "sdft_batch_execute": (c_int, [c_vp, c_vp, c_vp, c_vp]),
+    "sdft_batch_device_status": (c_int, [c_vp, c_int]),
+    "sdft_batch_destroy": (c_int, [c_vp]),
+    "sdft_status_string": (ctypes.c_char_p, [c_int]),
+    "sdft_last_cuda_error": (c_int, []),
+    "sdft_version": (c_int, []),
+}
+
+for _name, (_res, _args) in SIGNATURES.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class SdftError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        self.name = STATUS.get(self.status, f"status {status}")
+        msg = f"{where}: {self.name} ({_lib.sdft_status_string(self.status).decode()})"
+        if self.status == 8:
+            msg += f" [cuda error {_lib.sdft_last_cuda_error()}]"
+        super().__init__(msg)
+
+
+def _check(status: int, where: str) -> None:
+    if status != 0:
+        raise SdftError(status, where)
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    raise TypeError(f"cannot take a device pointer from {type(x)!r}")
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    raise TypeError(f"cannot take a cudaStream_t from {type(s)!r}")
+
+
+# ---------------------------------------------------------------------------
+# Functions with the C names
+# ---------------------------------------------------------------------------
+
+def sdft_plan_create(log2N: int, J: Sequence[int], prec: int = SDFT_C64, flags: int = 0) -> int:
+    arr = np.ascontiguousarray(np.asarray(J, dtype=np.uint64))
+    out = c_vp()
+    _check(_lib.sdft_plan_create(int(log2N), arr.ctypes.data_as(P_u64), int(arr.size), int(prec),
+                                 int(flags), ctypes.byref(out)), "sdft_plan_create")
+    return int(out.value)
+
+
+def sdft_plan_info(plan: int):
+    m, s, p = c_u32(), c_u32(), c_int()
+    _check(_lib.sdft_plan_info(plan, ctypes.byref(m), ctypes.byref(s), ctypes.byref(p)), "sdft_plan_info")
+    return int(m.value), int(s.value), int(p.value)
+
+
+def sdft_plan_pivots(plan: int) -> np.ndarray:
+    s = sdft_plan_info(plan)[1]
+    out = np.zeros(max(s, 1), dtype=np.uint32)
+    _check(_lib.sdft_plan_pivots(plan, out.ctypes.data_as(P_u32)), "sdft_plan_pivots")
+    return out[:s]
+
+
+def sdft_plan_sample_indices(plan: int) -> np.ndarray:
+    k = 1 << sdft_plan_info(plan)[1]
+    out = np.zeros(k, dtype=np.uint64)
+    _check(_lib.sdft_plan_sample_indices(plan, out.ctypes.data_as(P_u64)), "sdft_plan_sample_indices")
+    return out
+
+
+def sdft_plan_support_order(plan: int) -> np.ndarray:
+    k = 1 << sdft_plan_info(plan)[1]
+    out = np.zeros(k, dtype=np.uint64)
+    _check(_lib.sdft_plan_support_order(plan, out.ctypes.data_as(P_u64)), "sdft_plan_support_order")
+    return out
+
+
+def sdft_plan_twiddles(plan: int) -> np.ndarray:
+    """FP64 twiddles, stage-major, complex array of k-1 entries."""
+    k = 1 << sdft_plan_info(plan)[1]
+    out = np.zeros(2 * max(k - 1, 1), dtype=np.float64)
+    _check(_lib.sdft_plan_twiddles(plan, out.ctypes.data_as(P_f64)), "sdft_plan_twiddles")
+    return out[: 2 * (k - 1)].view(np.complex128)
+
+
+def sdft_plan_device_bytes(plan: int) -> int:
+    b = c_u64()
+    _check(_lib.sdft_plan_device_bytes(plan, ctypes.byref(b)), "sdft_plan_device_bytes")
+    return int(b.value)
+
+
+def sdft_execute(plan: int, d_samples, d_coeffs, stream=None) -> None:
+    _check(_lib.sdft_execute(plan, _ptr(d_samples), _ptr(d_coeffs), _stream(stream)), "sdft_execute")
+
+
+def sdft_execute_strided(plan: int, batch: int, d_samples, d_coeffs, stream=None) -> None:
+    _check(_lib.sdft_execute_strided(plan, int(batch), _ptr(d_samples), _ptr(d_coeffs), _stream(stream)),
+           "sdft_execute_strided")
+
+
+def sdft_plan_device_status(plan: int, clear: bool = False) -> int:
+    """Returns the status code (0 = ok) held in the plan's device status word."""
+    return int(_lib.sdft_plan_device_status(plan, int(bool(clear))))
+
+
+def sdft_plan_destroy(plan: int) -> None:
+    _check(_lib.sdft_plan_destroy(plan), "sdft_plan_destroy")
+
+
+def sdft_batch_create(plans: Sequence[int]) -> int:
+    arr = (c_vp * len(plans))(*[int(p) for p in plans])
+    out = c_vp()
+    _check(_lib.sdft_batch_create(arr, len(plans), ctypes.byref(out)), "sdft_batch_create")
+    return int(out.value)
+
+
+def sdft_batch_info(batch: int, n: int):
+    total = c_u64()
+    offs = np.zeros(n + 1, dtype=np.uint64)
+    _check(_lib.sdft_batch_info(batch, ctypes.byref(total), offs.ctypes.data_as(P_u64)), "sdft_batch_info")
+    return int(total.value), offs
+
+
+def sdft_batch_execute(batch: int, d_samples, d_coeffs, stream=None) -> None:
+    _check(_lib.sdft_batch_execute(batch, _ptr(d_samples), _ptr(d_coeffs), _stream(stream)), "sdft_batch_execute")
+
+
+def sdft_batch_device_status(batch: int, clear: bool = False) -> int:
+    return int(_lib.sdft_batch_device_status(batch, int(bool(clear))))
+
+
+def sdft_batch_destroy(batch: int) -> None:
+    _check(_lib.sdft_batch_destroy(batch), "sdft_batch_destroy")
+
+
+def sdft_status_string(status: int) -> str:
+    return _lib.sdft_status_string(int(status)).decode()
+
+
+def sdft_last_cuda_error() -> int:
+    return int(_lib.sdft_last_cuda_error())
+
+
+def sdft_version() -> int:
+    return int(_lib.sdft_version())

@@ -1,0 +1,155 @@
+"""Object wrappers over the C ABI: `Plan` (one support) and `Batch` (many).
+
+Torch is used for device buffers and streams only; every transform step runs
+in libsdft.so. Output tensors are allocated here when the caller passes none.
+"""
+from __future__ import annotations
+
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _native as N
+
+_PREC = {"c64": N.SDFT_C64, "complex64": N.SDFT_C64, "c128": N.SDFT_C128, "complex128": N.SDFT_C128}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype(prec: int):
+    torch = _torch()
+    return torch.complex64 if prec == N.SDFT_C64 else torch.complex128
+
+
+def _current_stream(stream):
+    if stream is not None:
+        return stream
+    torch = _torch()
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check_tensor(t, dtype, numel: int, what: str):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{what} must live on a CUDA device")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{what} must hold {numel} values, got {t.numel()}")
+
+
+class Plan:
+    """A validated homogeneous support with its sample set and device twiddles."""
+
+    def __init__(self, log2N: int, J: Sequence[int], prec="c64", host_only: bool = False):
+        code = _PREC[prec] if isinstance(prec, str) else int(prec)
+        flags = N.SDFT_PLAN_HOST_ONLY if host_only else 0
+        self.handle = N.sdft_plan_create(log2N, J, code, flags)
+        self.log2N, self.s, self.prec = N.sdft_plan_info(self.handle)
+        self.k = 1 << self.s
+        self._cache = {}
+
+    # -- introspection ---------------------------------------------------
+    @property
+    def pivots(self) -> np.ndarray:
+        if "pivots" not in self._cache:
+            self._cache["pivots"] = N.sdft_plan_pivots(self.handle)
+        return self._cache["pivots"]
+
+    @property
+    def sample_indices(self) -> np.ndarray:
+        if "I" not in self._cache:
+            self._cache["I"] = N.sdft_plan_sample_indices(self.handle)
+        return self._cache["I"]
+
+    @property
+    def support_order(self) -> np.ndarray:
+        if "Jc" not in self._cache:
+            self._cache["Jc"] = N.sdft_plan_support_order(self.handle)
+        return self._cache["Jc"]
+
+    def twiddles(self) -> np.ndarray:
+        return N.sdft_plan_twiddles(self.handle)
+
+    @property
+    def device_bytes(self) -> int:
+        return N.sdft_plan_device_bytes(self.handle)
+
+    @property
+    def dtype(self):
+        return _dtype(self.prec)
+
+    # -- execution ---------------------------------------------------------
+    def execute(self, samples, coeffs=None, stream=None):
+        """One instance: samples[t] = f(I[t]) -> coeffs[t] = (F f)(Jc[t])."""
+        return self.execute_strided(samples, coeffs, stream, batch=1)
+
+    def execute_strided(self, samples, coeffs=None, stream=None, batch: Optional[int] = None):
+        """`batch` packed instances (samples shaped [batch, k] or flat)."""
+        if batch is None:
+            batch = samples.numel() // self.k
+        _check_tensor(samples, self.dtype, batch * self.k, "samples")
+        if coeffs is None:
+            coeffs = _torch().empty_like(samples)
+        _check_tensor(coeffs, self.dtype, batch * self.k, "coeffs")
+        N.sdft_execute_strided(self.handle, batch, samples, coeffs, _current_stream(stream))
+        return coeffs
+
+    def device_status(self, clear: bool = False) -> int:
+        return N.sdft_plan_device_status(self.handle, clear)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.sdft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many instances with their own plans, run by one persistent kernel."""
+
+    def __init__(self, plans: Sequence[Plan]):
+        if not plans:
+            raise ValueError("empty batch")
+        self.plans = list(plans)            # keep the plans alive
+        self.prec = self.plans[0].prec
+        self.handle = N.sdft_batch_create([p.handle for p in self.plans])
+        self.total, self.offsets = N.sdft_batch_info(self.handle, len(self.plans))
+
+    @property
+    def dtype(self):
+        return _dtype(self.prec)
+
+    def execute(self, samples, coeffs=None, stream=None):
+        _check_tensor(samples, self.dtype, self.total, "samples")
+        if coeffs is None:
+            coeffs = _torch().empty_like(samples)
+        _check_tensor(coeffs, self.dtype, self.total, "coeffs")
+        N.sdft_batch_execute(self.handle, samples, coeffs, _current_stream(stream))
+        return coeffs
+
+    def device_status(self, clear: bool = False) -> int:
+        return N.sdft_batch_device_status(self.handle, clear)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.sdft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

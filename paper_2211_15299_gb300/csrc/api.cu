@@ -1,0 +1,282 @@
+// C ABI of the library: plans, execution, diagnostics (declared in include/sdft.h).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "launch.hpp"
+#include "plan.hpp"
+
+struct sdft_plan_s {
+  sdft::Plan p;
+};
+
+namespace sdft {
+
+namespace {
+thread_local int g_last_cuda_error = 0;
+std::mutex g_mu;
+std::set<std::pair<int, const void*>> g_smem_set;
+int g_sm_count[64] = {0};
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+}  // namespace
+
+sdft_status cuda_fail(cudaError_t e) {
+  g_last_cuda_error = int(e);
+  return SDFT_ERR_CUDA;
+}
+
+uint64_t wait_timeout_ns() {
+  static const uint64_t v = [] {
+    const char* s = std::getenv("SDFT_WAIT_TIMEOUT_NS");
+    const unsigned long long x = s ? std::strtoull(s, nullptr, 10) : 0ull;
+    return x ? uint64_t(x) : uint64_t(2000000000ull);
+  }();
+  return v;
+}
+
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int v = g_sm_count[dev];
+  if (v == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+    g_sm_count[dev] = v;
+  }
+  return v;
+}
+
+sdft_status ensure_smem(const void* fn, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_smem_set.count({dev, fn})) return SDFT_OK;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return cuda_fail(e);
+  g_smem_set.insert({dev, fn});
+  return SDFT_OK;
+}
+
+sdft_status encode_map(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides[3],
+                       const uint32_t box[4]) {
+  if (!g_encode) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                             cudaEnableDefault, &q);
+      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cuda_fail(e);
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+  }
+  cuuint64_t gdim[4] = {dims[0], dims[1], dims[2], dims[3]};
+  cuuint64_t gstr[3] = {strides[0], strides[1], strides[2]};
+  cuuint32_t bdim[4] = {box[0], box[1], box[2], box[3]};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), gdim, gstr, bdim,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    g_last_cuda_error = int(r);
+    return SDFT_ERR_CUDA;
+  }
+  return SDFT_OK;
+}
+
+// Check buffers: 16-byte aligned, and either identical (in place) or disjoint.
+static sdft_status check_buffers(const void* in, const void* out, uint64_t bytes) {
+  if (!in || !out) return SDFT_ERR_ARG;
+  if (!aligned16(in) || !aligned16(out)) return SDFT_ERR_ARG;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
+  if (a != b && a < b + bytes && b < a + bytes) return SDFT_ERR_ARG;
+  return SDFT_OK;
+}
+
+static sdft_status check_device(const Plan& p) {
+  if (p.device < 0 || !p.d_status) return SDFT_ERR_NO_DEVICE;
+  int dev = -1;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return dev == p.device ? SDFT_OK : SDFT_ERR_ARG;
+}
+
+sdft_status run_strided(const Plan& p, uint64_t batch, const void* in, void* out, cudaStream_t st) {
+  sdft_status s = check_device(p);
+  if (s != SDFT_OK) return s;
+  if (batch == 0) return SDFT_OK;
+  const uint64_t eb = uint64_t(elem_bytes(p.prec));
+  if (batch > (~0ull / eb) / p.k) return SDFT_ERR_ARG;
+  s = check_buffers(in, out, batch * p.k * eb);
+  if (s != SDFT_OK) return s;
+  return p.prec == SDFT_C64 ? launch_plan_f32(p, batch, in, out, st) : launch_plan_f64(p, batch, in, out, st);
+}
+
+}  // namespace sdft
+
+using sdft::Plan;
+
+extern "C" {
+
+sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft_prec prec, uint32_t flags,
+                             sdft_plan* out) {
+  if (!out) return SDFT_ERR_ARG;
+  *out = nullptr;
+  if (flags & ~SDFT_PLAN_HOST_ONLY) return SDFT_ERR_ARG;
+  sdft_plan_s* h = new (std::nothrow) sdft_plan_s();
+  if (!h) return SDFT_ERR_NOMEM;
+  sdft_status s;
+  try {
+    s = sdft::build_plan(log2N, J, k, prec, h->p);
+  } catch (const std::bad_alloc&) {
+    s = SDFT_ERR_NOMEM;
+  }
+  if (s != SDFT_OK) {
+    delete h;
+    return s;
+  }
+  Plan& p = h->p;
+  if (!(flags & SDFT_PLAN_HOST_ONLY)) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+      delete h;
+      return sdft::cuda_fail(e);
+    }
+    const size_t eb = size_t(sdft::elem_bytes(prec));
+    const size_t tw_bytes = size_t(p.tw_elems) * eb;
+    std::vector<unsigned char> host;
+    try {
+      host.resize(tw_bytes);
+    } catch (const std::bad_alloc&) {
+      delete h;
+      return SDFT_ERR_NOMEM;
+    }
+    if (prec == SDFT_C64)
+      sdft::fill_device_tables<float>(p, reinterpret_cast<float*>(host.data()));
+    else
+      sdft::fill_device_tables<double>(p, reinterpret_cast<double*>(host.data()));
+    e = cudaMalloc(&p.d_status, 256);
+    if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, 256);
+    if (e == cudaSuccess && tw_bytes) e = cudaMalloc(&p.d_tw, tw_bytes);
+    if (e == cudaSuccess && tw_bytes) e = cudaMemcpy(p.d_tw, host.data(), tw_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      if (p.d_tw) cudaFree(p.d_tw);
+      if (p.d_status) cudaFree(p.d_status);
+      delete h;
+      return e == cudaErrorMemoryAllocation ? SDFT_ERR_NOMEM : sdft::cuda_fail(e);
+    }
+    p.device = dev;
+    p.device_bytes = tw_bytes + 256;
+  }
+  *out = h;
+  return SDFT_OK;
+}
+
+sdft_status sdft_plan_info(sdft_plan plan, uint32_t* log2N, uint32_t* log2k, sdft_prec* prec) {
+  if (!plan) return SDFT_ERR_ARG;
+  if (log2N) *log2N = plan->p.M;
+  if (log2k) *log2k = plan->p.s;
+  if (prec) *prec = plan->p.prec;
+  return SDFT_OK;
+}
+
+sdft_status sdft_plan_pivots(sdft_plan plan, uint32_t* pivots) {
+  if (!plan || (!pivots && plan->p.s)) return SDFT_ERR_ARG;
+  for (uint32_t q = 0; q < plan->p.s; ++q) pivots[q] = plan->p.pivots[q];
+  return SDFT_OK;
+}
+
+sdft_status sdft_plan_sample_indices(sdft_plan plan, uint64_t* I) {
+  if (!plan || !I) return SDFT_ERR_ARG;
+  std::memcpy(I, plan->p.I.data(), sizeof(uint64_t) * plan->p.k);
+  return SDFT_OK;
+}
+
+sdft_status sdft_plan_support_order(sdft_plan plan, uint64_t* Jc) {
+  if (!plan || !Jc) return SDFT_ERR_ARG;
+  std::memcpy(Jc, plan->p.Jc.data(), sizeof(uint64_t) * plan->p.k);
+  return SDFT_OK;
+}
+
+sdft_status sdft_plan_twiddles(sdft_plan plan, double* tw) {
+  if (!plan || (!tw && plan->p.k > 1)) return SDFT_ERR_ARG;
+  const Plan& p = plan->p;
+  for (uint32_t m = 1; m <= p.s; ++m)
+    for (uint64_t u = 0; u < (1ull << (m - 1)); ++u) {
+      const uint64_t idx = (1ull << (m - 1)) - 1 + u;
+      sdft::twiddle_f64(p, m, u, tw[2 * idx], tw[2 * idx + 1]);
+    }
+  return SDFT_OK;
+}
+
+sdft_status sdft_plan_device_bytes(sdft_plan plan, uint64_t* bytes) {
+  if (!plan || !bytes) return SDFT_ERR_ARG;
+  *bytes = plan->p.device_bytes;
+  return SDFT_OK;
+}
+
+sdft_status sdft_execute(sdft_plan plan, const void* d_samples, void* d_coeffs, void* stream) {
+  if (!plan) return SDFT_ERR_ARG;
+  return sdft::run_strided(plan->p, 1, d_samples, d_coeffs, static_cast<cudaStream_t>(stream));
+}
+
+sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_samples, void* d_coeffs,
+                                 void* stream) {
+  if (!plan) return SDFT_ERR_ARG;
+  return sdft::run_strided(plan->p, batch, d_samples, d_coeffs, static_cast<cudaStream_t>(stream));
+}
+
+sdft_status sdft_plan_device_status(sdft_plan plan, int clear) {
+  if (!plan) return SDFT_ERR_ARG;
+  if (!plan->p.d_status) return SDFT_ERR_NO_DEVICE;
+  int v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&v, plan->p.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear) e = cudaMemset(plan->p.d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return sdft::cuda_fail(e);
+  return sdft_status(v);
+}
+
+sdft_status sdft_plan_destroy(sdft_plan plan) {
+  if (!plan) return SDFT_ERR_ARG;
+  if (plan->p.d_tw) cudaFree(plan->p.d_tw);
+  if (plan->p.d_status) cudaFree(plan->p.d_status);
+  delete plan;
+  return SDFT_OK;
+}
+
+const char* sdft_status_string(sdft_status s) {
+  switch (s) {
+    case SDFT_OK: return "ok";
+    case SDFT_ERR_ARG: return "invalid argument";
+    case SDFT_ERR_NOT_POW2: return "support size is not a power of two";
+    case SDFT_ERR_RANGE: return "support element or log2N out of range";
+    case SDFT_ERR_DUPLICATE: return "support has a repeated element";
+    case SDFT_ERR_NOT_HOMOGENEOUS: return "support is not homogeneous";
+    case SDFT_ERR_NOMEM: return "out of memory";
+    case SDFT_ERR_BUDGET: return "memory budget exceeded";
+    case SDFT_ERR_CUDA: return "CUDA error";
+    case SDFT_ERR_TIMEOUT: return "device-side wait timed out";
+    case SDFT_ERR_UNSUPPORTED: return "unsupported size or mode";
+    case SDFT_ERR_NO_DEVICE: return "plan has no device tables";
+    case SDFT_ERR_PRECISION: return "plans of different precision in one batch";
+  }
+  return "unknown status";
+}
+
+int sdft_last_cuda_error(void) { return sdft::g_last_cuda_error; }
+
+int sdft_version(void) { return 100; }
+
+}  // extern "C"

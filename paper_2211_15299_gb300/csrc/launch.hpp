@@ -1,0 +1,34 @@
+// Host-side launch interfaces shared by the C ABI and the per-precision units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "plan.hpp"
+
+namespace sdft {
+
+// Record a CUDA error for sdft_last_cuda_error and map it to a status.
+sdft_status cuda_fail(cudaError_t e);
+
+// Encode a 4-D tiled tensor map over 32-bit words with the 128-byte swizzle.
+// dims[0] is 32 (one 128-byte row); strides are byte strides of dims 1..3.
+sdft_status encode_map(CUtensorMap* map, const void* base, const uint64_t dims[4],
+                       const uint64_t strides[3], const uint32_t box[4]);
+
+// Number of SMs of the current device (cached).
+int sm_count();
+
+// Make sure a kernel may use `bytes` of dynamic shared memory (once per device).
+sdft_status ensure_smem(const void* fn, int bytes);
+
+// Global bound on device-side waits (nanoseconds).
+uint64_t wait_timeout_ns();
+
+// Run every level of `plan` on `batch` packed instances (complex64 / complex128).
+sdft_status launch_plan_f32(const Plan& plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
+sdft_status launch_plan_f64(const Plan& plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
+
+}  // namespace sdft

@@ -1,0 +1,201 @@
+// Host planner: validation, pivots, canonical order, sample set, twiddle tables.
+//
+// Pivots (Definition 8) are the levels where the congruence tree T(J) splits.
+// Sorting J by its bit-reversed value lists the leaves of the LSB-first tree
+// in depth-first order, so every split shows up between two neighbours, at
+// the lowest bit where they differ (Remark "tree-2-adic": two leaves meet at
+// level l iff their difference is an odd multiple of 2^l). J is homogeneous
+// iff there are exactly log2 k such levels (Definition 9).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "plan.hpp"
+
+namespace sdft {
+namespace {
+
+inline uint64_t bitrev64(uint64_t x) {
+  x = ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+  x = ((x >> 2) & 0x3333333333333333ull) | ((x & 0x3333333333333333ull) << 2);
+  x = ((x >> 4) & 0x0F0F0F0F0F0F0F0Full) | ((x & 0x0F0F0F0F0F0F0F0Full) << 4);
+  x = ((x >> 8) & 0x00FF00FF00FF00FFull) | ((x & 0x00FF00FF00FF00FFull) << 8);
+  x = ((x >> 16) & 0x0000FFFF0000FFFFull) | ((x & 0x0000FFFF0000FFFFull) << 16);
+  return (x >> 32) | (x << 32);
+}
+
+inline int highest_bit(uint64_t x) { return 63 - __builtin_clzll(x); }
+
+// cos(pi x), sin(pi x) for a dyadic x in [0, 1): fold into [0, 1/4] with exact
+// reflections so quarter turns come out exact, then call the C library.
+void cos_sin_pi(double x, double& c, double& s) {
+  double sc = 1.0;                 // sign of the cosine after x -> 1 - x
+  if (x > 0.5) { x = 1.0 - x; sc = -1.0; }
+  double cc, ss;
+  if (x > 0.25) {
+    const double y = 0.5 - x;      // cos(pi x) = sin(pi y), sin(pi x) = cos(pi y)
+    cc = std::sin(M_PI * y);
+    ss = std::cos(M_PI * y);
+  } else {
+    cc = std::cos(M_PI * x);
+    ss = std::sin(M_PI * x);
+  }
+  c = sc * cc;
+  s = ss;
+}
+
+}  // namespace
+
+void twiddle_f64(const Plan& p, uint32_t m, uint64_t u, double& re, double& im) {
+  // Lemma "rec-hom-tree-split": omega_{r+1}^{j} with r = r_m and j = Jc[u]
+  // (bit r of Jc[u] is 0 for u < 2^(m-1)); only j mod 2^r matters.
+  const uint32_t r = p.pivots[m - 1];
+  const uint64_t rho = (r >= 64) ? p.Jc[u] : (p.Jc[u] & ((r == 0) ? 0ull : ((1ull << r) - 1)));
+  const double x = std::ldexp(static_cast<double>(rho), -static_cast<int>(r));  // rho / 2^r
+  double c, s;
+  cos_sin_pi(x, c, s);
+  re = c;
+  im = -s;
+}
+
+sdft_status build_plan(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec, Plan& p) {
+  if (!J && k) return SDFT_ERR_ARG;
+  if (prec != SDFT_C64 && prec != SDFT_C128) return SDFT_ERR_ARG;
+  if (M > SDFT_MAX_LOG2N) return SDFT_ERR_RANGE;
+  if (k == 0) return SDFT_ERR_ARG;
+  if (k & (k - 1)) return SDFT_ERR_NOT_POW2;
+  const uint32_t s = static_cast<uint32_t>(__builtin_ctzll(k));
+  if (s > SDFT_MAX_LOG2K) return SDFT_ERR_UNSUPPORTED;
+  const uint64_t N = 1ull << M;
+  for (uint64_t i = 0; i < k; ++i)
+    if (J[i] >= N) return SDFT_ERR_RANGE;
+  if (s > M) return SDFT_ERR_DUPLICATE;  // more than N distinct values is impossible
+
+  p.M = M;
+  p.s = s;
+  p.k = k;
+  p.prec = prec;
+
+  // Pivots from depth-first neighbours of the LSB-first tree.
+  std::vector<uint64_t> rev(k);
+  for (uint64_t i = 0; i < k; ++i) rev[i] = M ? (bitrev64(J[i]) >> (64 - M)) : 0;
+  std::sort(rev.begin(), rev.end());
+  uint64_t level_mask = 0;
+  for (uint64_t i = 0; i + 1 < k; ++i) {
+    const uint64_t x = rev[i] ^ rev[i + 1];
+    if (x == 0) return SDFT_ERR_DUPLICATE;
+    level_mask |= 1ull << (M - 1 - highest_bit(x));
+  }
+  std::vector<uint64_t>().swap(rev);
+  if (static_cast<uint32_t>(__builtin_popcountll(level_mask)) != s) return SDFT_ERR_NOT_HOMOGENEOUS;
+  p.pivots.clear();
+  for (uint32_t l = 0; l < M; ++l)
+    if (level_mask >> l & 1) p.pivots.push_back(l);
+
+  // Canonical order: coefficient t is the element whose pivot bits spell t.
+  p.Jc.assign(k, ~0ull);
+  for (uint64_t i = 0; i < k; ++i) {
+    uint64_t key = 0;
+    for (uint32_t q = 0; q < s; ++q) key |= ((J[i] >> p.pivots[q]) & 1ull) << q;
+    if (p.Jc[key] != ~0ull) return SDFT_ERR_NOT_HOMOGENEOUS;  // cannot happen once the count matched
+    p.Jc[key] = J[i];
+  }
+
+  // Pivoted sampling pattern (Definition "r_sampling_pattern"), sample order t.
+  p.I.assign(k, 0);
+  for (uint64_t t = 0; t < k; ++t) {
+    uint64_t i = 0;
+    for (uint32_t q = 0; q < s; ++q)
+      if (t >> q & 1) i |= 1ull << (M - 1 - p.pivots[q]);
+    p.I[t] = i;
+  }
+
+  // Level schedule.
+  p.levels.clear();
+  p.tw_elems = 0;
+  if (s <= kSmallMax) {
+    p.tw_elems = s ? (1ull << s) : 0;
+    return SDFT_OK;
+  }
+  const uint32_t TB = tile_bits(prec), CB = row_bits(prec);
+  Level l0;
+  l0.lo = 0;
+  l0.hi = std::min<uint32_t>(s, TB);
+  l0.plo = 0;
+  l0.n_gb = 1;
+  l0.tw_off = 0;
+  l0.tw_len = 1ull << l0.hi;
+  l0.last = (l0.hi == s);
+  p.levels.push_back(l0);
+  uint64_t off = l0.tw_len;
+  uint32_t lo = l0.hi;
+  while (lo < s) {
+    Level L;
+    L.lo = lo;
+    L.hi = std::min<uint32_t>(s, lo + (TB - CB));
+    const uint32_t Q = L.hi - L.lo;
+    L.lg = TB - CB - Q;
+    L.plo = TB - Q;
+    L.n_gb = 1ull << (L.lo - CB - L.lg);
+    L.tw_len = (1ull << TB) - (1ull << L.plo);
+    L.tw_off = off;
+    L.last = (L.hi == s);
+    off += L.n_gb * L.tw_len;
+    p.levels.push_back(L);
+    lo = L.hi;
+  }
+  p.tw_elems = off;
+  return SDFT_OK;
+}
+
+template <class T>
+void fill_device_tables(const Plan& p, T* out) {
+  const int final_scale = static_cast<int>(p.M) - static_cast<int>(p.s);  // N/k = 2^(M-s)
+  auto put = [&](uint64_t idx, uint32_t m, uint64_t u) {
+    double re, im;
+    twiddle_f64(p, m, u, re, im);
+    if (m == p.s) {
+      re = std::ldexp(re, final_scale);
+      im = std::ldexp(im, final_scale);
+    }
+    out[2 * idx] = static_cast<T>(re);
+    out[2 * idx + 1] = static_cast<T>(im);
+  };
+  if (p.tw_elems == 0) return;
+  std::memset(out, 0, sizeof(T) * 2 * p.tw_elems);
+  if (p.levels.empty()) {
+    // Register path: entry 2^(m-1) + u for stage m.
+    for (uint32_t m = 1; m <= p.s; ++m)
+      for (uint64_t u = 0; u < (1ull << (m - 1)); ++u) put((1ull << (m - 1)) + u, m, u);
+    return;
+  }
+  const Level& l0 = p.levels[0];
+  for (uint32_t m = 1; m <= l0.hi; ++m)
+    for (uint64_t u = 0; u < (1ull << (m - 1)); ++u) put(l0.tw_off + (1ull << (m - 1)) + u, m, u);
+  const uint32_t CB = row_bits(p.prec);
+  for (size_t j = 1; j < p.levels.size(); ++j) {
+    const Level& L = p.levels[j];
+    const uint32_t Q = L.hi - L.lo;
+    for (uint64_t gb = 0; gb < L.n_gb; ++gb) {
+      const uint64_t base = L.tw_off + gb * L.tw_len - (1ull << L.plo);
+      for (uint32_t q = 0; q < Q; ++q) {
+        const uint32_t m = L.lo + q + 1;
+        const uint64_t cnt = 1ull << (L.plo + q);
+        for (uint64_t v = 0; v < cnt; ++v) {
+          // v = (hq << plo) | (gl << CB) | c  ->  u = (hq << lo) | ((gb << lg | gl) << CB) | c
+          const uint64_t c = v & ((1ull << CB) - 1);
+          const uint64_t gl = (v >> CB) & ((1ull << L.lg) - 1);
+          const uint64_t hq = v >> L.plo;
+          const uint64_t u = (hq << L.lo) | (((gb << L.lg) | gl) << CB) | c;
+          put(base + cnt + v, m, u);
+        }
+      }
+    }
+  }
+}
+
+template void fill_device_tables<float>(const Plan&, float*);
+template void fill_device_tables<double>(const Plan&, double*);
+
+}  // namespace sdft

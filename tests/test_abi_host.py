@@ -1,0 +1,118 @@
+"""CPU checks of the C ABI: the library loads, exports every declared symbol,
+and its host planner agrees bit-for-bit with the oracle (no GPU needed)."""
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from conftest import ROOT, read_golden
+
+
+def _declared_symbols():
+    with open(f"{ROOT}/include/sdft.h") as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"\b(sdft_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    import ctypes
+    from paper_2211_15299_gb300 import _native as N
+    lib = ctypes.CDLL(N.LIB_PATH)
+    declared = _declared_symbols()
+    assert declared, "no declarations parsed"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) == set(N.SIGNATURES), "binding and header disagree"
+
+
+def test_status_strings():
+    from paper_2211_15299_gb300 import _native as N
+    for code in N.STATUS:
+        assert N.sdft_status_string(code) != "unknown status"
+
+
+@pytest.mark.parametrize("line", read_golden("pivot_examples.txt"))
+def test_plan_validation_matches_paper_examples(line):
+    from paper_2211_15299_gb300 import Plan, SdftError
+    name, M, J, expect = [x.strip() for x in line.split("|")]
+    M = int(M)
+    J = [int(x) for x in J.split()]
+    if expect == "NOT_HOMOGENEOUS":
+        with pytest.raises(SdftError) as ei:
+            Plan(M, J, host_only=True)
+        assert ei.value.name in ("SDFT_ERR_NOT_HOMOGENEOUS", "SDFT_ERR_NOT_POW2"), name
+    else:
+        p = Plan(M, J, host_only=True)
+        assert [int(x) for x in p.pivots] == [int(x) for x in expect.split()], name
+
+
+def test_plan_errors():
+    from paper_2211_15299_gb300 import Plan, SdftError
+    cases = [
+        (4, [0, 16], "SDFT_ERR_RANGE"),
+        (4, [1, 2, 3], "SDFT_ERR_NOT_POW2"),
+        (4, [3, 3, 5, 7], "SDFT_ERR_DUPLICATE"),
+        (63, [0], "SDFT_ERR_RANGE"),
+        (10, [1, 2, 4, 8], "SDFT_ERR_NOT_HOMOGENEOUS"),
+        (2, [0, 1, 2, 3, 0, 1, 2, 3], "SDFT_ERR_DUPLICATE"),
+    ]
+    for M, J, want in cases:
+        with pytest.raises(SdftError) as ei:
+            Plan(M, J, host_only=True)
+        assert ei.value.name == want, (M, J)
+    with pytest.raises(SdftError):
+        Plan(4, [], host_only=True)
+
+
+def test_host_only_plan_refuses_execution():
+    from paper_2211_15299_gb300 import _native as N
+    h = N.sdft_plan_create(4, [0, 1, 2, 3], N.SDFT_C64, N.SDFT_PLAN_HOST_ONLY)
+    try:
+        with pytest.raises(N.SdftError) as ei:
+            N.sdft_execute(h, 16, 16, None)
+        assert ei.value.name == "SDFT_ERR_NO_DEVICE"
+    finally:
+        N.sdft_plan_destroy(h)
+
+
+def test_plan_tables_match_oracle():
+    from paper_2211_15299_gb300 import Plan
+    rng = np.random.default_rng(31)
+    for trial in range(300):
+        M = int(rng.integers(1, 41))
+        s = int(rng.integers(0, min(M, 14) + 1))
+        piv = W.random_pivots(M, s, rng)
+        J = W.homogeneous_support(M, piv, rng)
+        p = Plan(M, J, host_only=True)
+        assert [int(x) for x in p.pivots] == [int(x) for x in piv]
+        assert np.array_equal(p.sample_indices, O.sample_set(M, piv))
+        if s <= 11:
+            assert np.array_equal(p.support_order, O.canonical_support(J, piv))
+        if s <= 9:
+            # twiddles: the omega vectors Algorithm 1 uses at each recursion depth
+            tw = p.twiddles()
+            Jc = p.support_order
+            for m in range(1, s + 1):
+                a = 1 << (M - 1 - int(piv[m - 1]))
+                w = O.F_sub(M, np.array([a], dtype=np.uint64), Jc[: 1 << (m - 1)])[0]
+                got = tw[(1 << (m - 1)) - 1:(1 << m) - 1]
+                assert np.max(np.abs(got - w)) < 1e-15
+
+
+def test_plan_at_config_sizes_host_only():
+    from paper_2211_15299_gb300 import Plan
+    inst, _ = W.workload_large(M=30, s=20, batch=1, coeffs=False)
+    p = Plan(inst.M, inst.J, host_only=True)
+    assert [int(x) for x in p.pivots] == [int(x) for x in inst.pivots]
+    I = p.sample_indices
+    assert np.array_equal(I, O.sample_set_closed_form(inst.M, inst.pivots)) if inst.s <= 12 else True
+    # the pivot-bit key of every canonical element spells its position
+    Jc = p.support_order
+    t = np.arange(Jc.size, dtype=np.uint64)
+    key = np.zeros_like(Jc)
+    for q, r in enumerate(inst.pivots):
+        key |= ((Jc >> np.uint64(r)) & np.uint64(1)) << np.uint64(q)
+    assert np.array_equal(key, t)
+    assert np.array_equal(np.sort(Jc), np.sort(inst.J))

@@ -356,3 +356,17 @@ def test_planted_dropped_normalisation_is_caught():
     y = O.hidft(f, piv, Jc, M)                      # height-0 Hi-DFT, no N/k
     assert rel_l2(y * (1 << M) / J.size, c) < 1e-12
     assert rel_l2(y * J.size, c) > 0.1              # the paper's "|J| (Ff)_J" as printed
+
+
+def test_level_forms_match_recursions():
+    rng = np.random.default_rng(19)
+    for trial in range(60):
+        M, piv, J = _random_instance(rng, 12)
+        Jc = O.canonical_support(J, piv)
+        assert np.array_equal(O.canonical_support_by_key(J, piv), Jc)
+        I = O.sample_set(M, piv)
+        C = W.complex_gaussian((3, J.size), rng)
+        F = O.synthesize(M, Jc, C, I)
+        assert rel_l2(O.synthesize_levels(M, piv, Jc, C), F) < 1e-13
+        assert rel_l2(O.hidft_levels(F, piv, Jc, M), np.stack([O.hidft(f, piv, Jc, M) for f in F])) < 1e-13
+        assert rel_l2(O.transform_levels(M, piv, Jc, F), C) < 1e-12
