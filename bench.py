@@ -196,6 +196,10 @@ def run_ours(args):
                 "kernel": "k_level<float,0,12,true>" if n_levels == 1 else "multi-level",
                 "alg_bytes_per_launch": alg_bytes}
 
+    if args.only_fp32:
+        if rank == 0:
+            print(json.dumps({"value": value, "unit": UNIT, "ms_per_step": ms_per_step, "roofline": roofline}))
+        return
     # FP64: batched and plain per-instance (one call per instance), device-timed
     x64 = x32.to(torch.complex128)
     y64 = torch.empty_like(x64)
@@ -349,6 +353,7 @@ def main():
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only-fp32", action="store_true", help="time the complex64 leg only (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
