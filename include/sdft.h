@@ -117,7 +117,7 @@ sdft_status sdft_plan_device_bytes(sdft_plan plan, uint64_t* bytes);
 /*
  * sdft_execute - one instance: d_coeffs[t] = (F f)(Jc[t]) from d_samples[t] = f(I[t]).
  * d_samples, d_coeffs: device buffers of k complex values of the plan's
- * precision, 16-byte aligned; they must not overlap (in-place is not supported).
+ * precision, 16-byte aligned; either the same buffer (in place) or disjoint.
  * Asynchronous on `stream`; allocates nothing; may run concurrently on one plan.
  */
 sdft_status sdft_execute(sdft_plan plan, const void* d_samples, void* d_coeffs, void* stream);
@@ -131,7 +131,10 @@ sdft_status sdft_execute(sdft_plan plan, const void* d_samples, void* d_coeffs, 
 sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_samples,
                                  void* d_coeffs, void* stream);
 
-/* Device status word of a plan: SDFT_OK or SDFT_ERR_TIMEOUT; synchronises the
+/* Device status word of a plan: SDFT_OK, SDFT_ERR_TIMEOUT, or a launch
+ * self-check code above 0xff (0x101: dynamic shared memory smaller than the
+ * kernel's layout; 0x102: tensor-map parameter not 64-byte aligned; 0x103:
+ * twiddle table not 16-byte aligned; the kernel did no work). Synchronises the
  * device; clears the word when `clear` is non-zero. */
 sdft_status sdft_plan_device_status(sdft_plan plan, int clear);
 

@@ -166,6 +166,11 @@ sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft
       sdft::fill_device_tables<float>(p, reinterpret_cast<float*>(host.data()));
     else
       sdft::fill_device_tables<double>(p, reinterpret_cast<double*>(host.data()));
+    if (!p.levels.empty()) {  // entries 1..15 of the level-0 table go into kernel parameters
+      for (int i = 0; i < 30 && size_t(2 + i) < 2 * size_t(p.tw_elems); ++i)
+        p.tw0[i] = prec == SDFT_C64 ? double(reinterpret_cast<const float*>(host.data())[2 + i])
+                                    : reinterpret_cast<const double*>(host.data())[2 + i];
+    }
     e = cudaMalloc(&p.d_status, 256);
     if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, 256);
     if (e == cudaSuccess && tw_bytes) e = cudaMalloc(&p.d_tw, tw_bytes);

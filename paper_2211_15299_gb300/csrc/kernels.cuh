@@ -38,7 +38,14 @@ template <> struct KT<double> {
 };
 
 constexpr uint32_t kTileBytes = 32768;
-constexpr uint32_t kLevelSmem = 3 * kTileBytes + 64 + 1024;   // 2 data tiles, twiddles, barriers, align
+
+// Launch self-check failures recorded in the device status word (see sdft.h:
+// values above 255 are launch-check codes, below are sdft_status values).
+constexpr int kBadSmem = 0x101;   // less dynamic shared memory than the layout needs
+constexpr int kBadMap = 0x102;    // tensor map parameter not 64-byte aligned
+constexpr int kBadTable = 0x103;  // twiddle table not 16-byte aligned
+constexpr int kBufs = 3;                                             // tiles in flight per CTA
+constexpr uint32_t kLevelSmem = kBufs * kTileBytes + 64 + 1024;     // tiles, barriers, alignment slack
 
 // ---- swizzled tile addressing -------------------------------------------------
 // byte(T) = (T >> CB) * 128 + ((col_chunk(T) ^ (row(T) & 7)) << 4) + sub(T) * ES.
@@ -87,12 +94,62 @@ __device__ __forceinline__ void bfly_scaled(double2& a, double2& b, const double
   a.y = fma(a.y, sc, ti);
 }
 
+// ---- pass schedule ------------------------------------------------------------------
+// Stage bits [PLO, PHI) of a tile run in passes. Pass p covers the 4-bit window
+// starting at the first stage bit not yet done (or the top window of the tile)
+// and runs the stages of that window that are still pending.
+constexpr int pass_done(int TB, int PLO, int PHI, int p) {
+  int d = PLO;
+  for (int i = 0; i < p; ++i) {
+    const int b = (d + 4 <= TB) ? d : TB - 4;
+    d = (b + 4 < PHI) ? b + 4 : PHI;
+  }
+  return d;
+}
+constexpr int pass_b(int TB, int PLO, int PHI, int p) {
+  const int d = pass_done(TB, PLO, PHI, p);
+  return (d + 4 <= TB) ? d : TB - 4;
+}
+constexpr int pass_shi(int TB, int PLO, int PHI, int p) {
+  const int b = pass_b(TB, PLO, PHI, p);
+  return (b + 4 < PHI) ? b + 4 : PHI;
+}
+constexpr int n_passes(int TB, int PLO, int PHI) {
+  int p = 0;
+  while (pass_done(TB, PLO, PHI, p) < PHI) ++p;
+  return p;
+}
+// Distinct twiddles a thread needs in one pass: stage bit m1 uses 2^(m1-B).
+constexpr int pass_ntw(int B, int SLO, int SHI) {
+  int n = 0;
+  for (int m1 = SLO; m1 < SHI; ++m1) n += 1 << (m1 - B);
+  return n;
+}
+// Twiddle sources per pass: a B = 0 pass (the same 15 entries for every thread)
+// reads kernel parameters; the top pass (B = TB - 4, the largest table region)
+// holds its entries in registers across tiles; any other pass reads its small
+// table region through the L1 cache.
+enum TwSrc { kTwParam = 0, kTwReg = 1, kTwGlobal = 2 };
+constexpr int pass_src(int TB, int B) { return B == 0 ? kTwParam : (B == TB - 4 ? kTwReg : kTwGlobal); }
+constexpr int reg_twiddles(int TB, int PLO, int PHI) {
+  int n = 0;
+  for (int p = 0; p < n_passes(TB, PLO, PHI); ++p) {
+    const int b = pass_b(TB, PLO, PHI, p);
+    if (pass_src(TB, b) == kTwReg) n += pass_ntw(b, pass_done(TB, PLO, PHI, p), pass_shi(TB, PLO, PHI, p));
+  }
+  return n;
+}
+
 // ---- one pass: stages with stage bits [SLO, SHI) on 16 elements per thread --------
-// The thread covers tile-index bits [B, B+4); its other bits come from tid.
-// Twiddles live in shared memory indexed absolutely: stage bit m1, position u
-// at entry 2^m1 + u.
-template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE>
-__device__ __forceinline__ void tile_pass(char* buf, const char* tws, uint32_t tid, R sc) {
+// The thread covers tile-index bits [B, B+4); its other bits (F) come from tid.
+// Stage bit m1 on the element pair (e, e | 2^q), q = m1 - B, uses the table
+// entry 2^m1 + u with u = (F mod 2^B) + ((e mod 2^q) << B); `w` holds exactly
+// those entries in order (m1 ascending, then e mod 2^q).
+// SRC = kTwParam / kTwReg: `w` holds exactly the pass's entries in order
+// (m1 ascending, then e mod 2^q). SRC = kTwGlobal: `w` is the absolute-indexed
+// table in global memory.
+template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SRC>
+__device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc) {
   using C = typename KT<R>::C;
   static_assert(B >= 0 && B + 4 <= KT<R>::TB, "pass bits out of tile");
   static_assert(SLO >= B && SHI <= B + 4 && SLO < SHI, "stage bits out of pass");
@@ -114,20 +171,23 @@ __device__ __forceinline__ void tile_pass(char* buf, const char* tws, uint32_t t
       v[e] = *reinterpret_cast<const C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)));
     }
   }
-  const char* twb = tws + (F & LOWM) * sizeof(C);
 #pragma unroll
   for (int m1 = SLO; m1 < SHI; ++m1) {
     const int q = m1 - B;
+    const int off = pass_ntw(B, SLO, m1);
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       if ((e >> q) & 1) continue;
       const int eh = e | (1 << q);
-      const uint32_t uE = (uint32_t(e) << B) & ((1u << m1) - 1u);
-      const C w = *reinterpret_cast<const C*>(twb + ((1u << m1) + uE) * sizeof(C));
-      if (SCALE && m1 == SHI - 1)
-        bfly_scaled(v[e], v[eh], w, sc);
+      C wt;
+      if constexpr (SRC == kTwGlobal)
+        wt = __ldg(w + (1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B));
       else
-        bfly(v[e], v[eh], w);
+        wt = w[off + (e & ((1 << q) - 1))];
+      if (SCALE && m1 == SHI - 1)
+        bfly_scaled(v[e], v[eh], wt, sc);
+      else
+        bfly(v[e], v[eh], wt);
     }
   }
   if constexpr (B == 0 && KT<R>::ES == 8) {
@@ -146,23 +206,53 @@ __device__ __forceinline__ void tile_pass(char* buf, const char* tws, uint32_t t
   __syncthreads();
 }
 
-// Stage bits [DONE, PHI) in passes of at most four; the pass covering them is
-// the 4-bit window starting at DONE (or the top window of the tile).
-template <class R, int PHI, bool LAST, int DONE>
-__device__ __forceinline__ void run_passes(char* buf, const char* tws, uint32_t tid, R sc) {
-  if constexpr (DONE < PHI) {
-    constexpr int TB = KT<R>::TB;
-    constexpr int B = (DONE + 4 <= TB) ? DONE : TB - 4;
-    constexpr int SHI = (B + 4 < PHI) ? B + 4 : PHI;
+// Load the register twiddles of every B > 0 pass from a table indexed
+// absolutely (entry 2^m1 + u), in the order tile_pass consumes them.
+template <class R, int PLO, int PHI, int P = 0, int ROFF = 0>
+__device__ __forceinline__ void load_reg_twiddles(const typename KT<R>::C* __restrict__ tw, uint32_t tid,
+                                                  typename KT<R>::C* wreg) {
+  constexpr int TB = KT<R>::TB;
+  if constexpr (P < n_passes(TB, PLO, PHI)) {
+    constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
+    if constexpr (pass_src(TB, B) == kTwReg) {
+      const typename KT<R>::C* base = tw + (tid & ((1u << B) - 1u));
+#pragma unroll
+      for (int m1 = SLO; m1 < SHI; ++m1)
+#pragma unroll
+        for (int v = 0; v < (1 << (m1 - B)); ++v)
+          wreg[ROFF + pass_ntw(B, SLO, m1) + v] = __ldg(base + (1u << m1) + (uint32_t(v) << B));
+      load_reg_twiddles<R, PLO, PHI, P + 1, ROFF + pass_ntw(B, SLO, SHI)>(tw, tid, wreg);
+    } else {
+      load_reg_twiddles<R, PLO, PHI, P + 1, ROFF>(tw, tid, wreg);
+    }
+  }
+}
+
+template <class R, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0>
+__device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* wreg, const typename KT<R>::C* w0,
+                                           const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc) {
+  constexpr int TB = KT<R>::TB;
+  if constexpr (P < n_passes(TB, PLO, PHI)) {
+    constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
     constexpr bool FINAL = (SHI == PHI);
-    tile_pass<R, B, DONE, SHI, LAST && FINAL, FINAL>(buf, tws, tid, sc);
-    run_passes<R, PHI, LAST, SHI>(buf, tws, tid, sc);
+    constexpr int SRC = pass_src(TB, B);
+    if constexpr (SRC == kTwParam) {
+      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, w0, tid, sc);
+      run_passes<R, PLO, PHI, LAST, P + 1, ROFF>(buf, wreg, w0, twg, tid, sc);
+    } else if constexpr (SRC == kTwGlobal) {
+      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, twg, tid, sc);
+      run_passes<R, PLO, PHI, LAST, P + 1, ROFF>(buf, wreg, w0, twg, tid, sc);
+    } else {
+      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, wreg + ROFF, tid, sc);
+      run_passes<R, PLO, PHI, LAST, P + 1, ROFF + pass_ntw(B, SLO, SHI)>(buf, wreg, w0, twg, tid, sc);
+    }
   }
 }
 
 // ---- persistent level kernel ----------------------------------------------------
 // Tile i of a level: a = i / nB selects the twiddle table (a group block for
 // later levels), b = i % nB; TMA coordinates {0, a*a_step1 + b*b_step1, 0, b*b_step3}.
+template <class R>
 struct LevelArgs {
   uint64_t n_tiles;
   uint64_t nB;
@@ -174,6 +264,7 @@ struct LevelArgs {
   double scale;            // N/k, used when LAST
   int* status;             // device status word
   uint64_t timeout_ns;     // bound on every mbarrier wait
+  typename KT<R>::C tw0[16];  // tw0[i] = level-0 table entry i + 1 (stage bits 0..3), i < 15
 };
 
 __device__ __forceinline__ char* align1024(char* p) {
@@ -182,80 +273,103 @@ __device__ __forceinline__ char* align1024(char* p) {
   return reinterpret_cast<char*>(a + ((1024u - (s & 1023u)) & 1023u));
 }
 
-template <class R>
-__device__ __forceinline__ void load_table(char* tws, const LevelArgs& args, uint64_t tab, uint32_t tid) {
-  const uint4* src = reinterpret_cast<const uint4*>(static_cast<const char*>(args.tw) +
-                                                    tab * args.tw_stride * sizeof(typename KT<R>::C));
-  uint4* dst = reinterpret_cast<uint4*>(tws + uint64_t(args.tw_first) * sizeof(typename KT<R>::C));
-  const uint32_t n16 = uint32_t(args.tw_len * sizeof(typename KT<R>::C) / 16);
-  for (uint32_t j = tid; j < n16; j += KT<R>::NT) dst[j] = __ldg(src + j);
-}
-
+// Pipeline per CTA (kBufs = 3 tile buffers): tile j waits on full[j % 3], runs
+// its passes in place, and leaves through a TMA store issued by thread 0. The
+// buffer of tile j-1 is refilled with tile j+2 once its store has finished
+// reading shared memory (wait_group.read 1 leaves only tile j's store pending),
+// so two loads stay in flight behind the tile being computed.
 template <class R, int PLO, int PHI, bool LAST>
 __global__ void __launch_bounds__(KT<R>::NT, 2)
-    k_level(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap dst, const LevelArgs args) {
+    k_level(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap dst,
+            const __grid_constant__ LevelArgs<R> args) {
+  using C = typename KT<R>::C;
+  constexpr int NREG = reg_twiddles(KT<R>::TB, PLO, PHI);
   extern __shared__ char smem_raw[];
   char* smem = align1024(smem_raw);
-  char* tws = smem + 2 * kTileBytes;
-  const uint32_t bar0 = ptx::smem_addr(smem + 3 * kTileBytes);
+  const uint32_t bar0 = ptx::smem_addr(smem + kBufs * kTileBytes);
   const uint32_t tid = threadIdx.x;
+  // Self-check of the launch before any shared-memory or TMA access: enough
+  // dynamic shared memory for the aligned layout, tensor maps 64-byte aligned,
+  // twiddle tables 16-byte aligned. A failed check records a status and exits.
+  {
+    const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 8 * kBufs;
+    int bad = 0;
+    if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
+    else if ((reinterpret_cast<uintptr_t>(&src) | reinterpret_cast<uintptr_t>(&dst)) & 63u) bad = kBadMap;
+    else if (reinterpret_cast<uintptr_t>(args.tw) & 15u) bad = kBadTable;
+    if (bad) {
+      if (tid == 0) atomicCAS(args.status, 0, bad);
+      return;
+    }
+  }
   const uint64_t G = gridDim.x;
   const uint64_t t0 = args.n_tiles * blockIdx.x / G;
   const uint64_t t1 = args.n_tiles * (blockIdx.x + 1) / G;
   if (t0 >= t1) return;
+  const uint64_t n = t1 - t0;
 
-  auto issue_load = [&](uint64_t i, uint32_t b) {
+  auto coords = [&](uint64_t i, int& c1, int& c3) {
     const int64_t a = int64_t(i / args.nB), bb = int64_t(i % args.nB);
+    c1 = int(a * args.a_step1 + bb * args.b_step1);
+    c3 = int(bb * args.b_step3);
+  };
+  auto issue_load = [&](uint64_t j) {  // local tile index j -> buffer j % kBufs
+    const uint32_t b = uint32_t(j % kBufs);
     const uint32_t bar = bar0 + 8 * b;
+    int c1, c3;
+    coords(t0 + j, c1, c3);
     ptx::mbar_arrive_expect_tx(bar, kTileBytes);
-    ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &src, bar, 0,
-                     int(a * args.a_step1 + bb * args.b_step1), 0, int(bb * args.b_step3));
+    ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &src, bar, 0, c1, 0, c3);
   };
 
   if (tid == 0) {
-    ptx::mbar_init(bar0, 1);
-    ptx::mbar_init(bar0 + 8, 1);
+    for (int b = 0; b < kBufs; ++b) ptx::mbar_init(bar0 + 8 * b, 1);
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&src);
     ptx::prefetch_tensormap(&dst);
-    issue_load(t0, 0);
-    if (t0 + 1 < t1) issue_load(t0 + 1, 1);
+    for (uint64_t j = 0; j < n && j < uint64_t(kBufs); ++j) issue_load(j);
   }
+  __syncthreads();
   const R sc = R(args.scale);
+  const C* tw = static_cast<const C*>(args.tw) - args.tw_first;
+  C wreg[NREG > 0 ? NREG : 1];
+  const C* twt = tw;
   uint64_t cur_tab = ~0ull;
   bool aborted = false;
-  uint64_t it = 0;
-  for (uint64_t i = t0; i < t1; ++i, ++it) {
-    const uint32_t b = uint32_t(it & 1);
+  uint64_t j = 0;
+  for (; j < n; ++j) {
+    const uint32_t b = uint32_t(j % kBufs);
     char* buf = smem + b * kTileBytes;
-    const uint64_t tab = args.tw_stride ? i / args.nB : 0;
-    if (tab != cur_tab) {
-      load_table<R>(tws, args, tab, tid);
+    const uint64_t tab = args.tw_stride ? (t0 + j) / args.nB : 0;
+    if (tab != cur_tab) {  // uniform across the CTA
+      twt = tw + tab * args.tw_stride;
+      load_reg_twiddles<R, PLO, PHI>(twt, tid, wreg);
       cur_tab = tab;
     }
-    const bool ok = ptx::mbar_wait_bounded(bar0 + 8 * b, uint32_t((it >> 1) & 1), args.timeout_ns);
+    const bool ok = ptx::mbar_wait_bounded(bar0 + 8 * b, uint32_t((j / kBufs) & 1), args.timeout_ns);
     if (__syncthreads_or(!ok)) {
       aborted = true;
       break;
     }
-    run_passes<R, PHI, LAST, PLO>(buf, tws, tid, sc);
+    run_passes<R, PLO, PHI, LAST>(buf, wreg, args.tw0, twt, tid, sc);
     if (tid == 0) {
-      const int64_t a = int64_t(i / args.nB), bb = int64_t(i % args.nB);
-      ptx::tma_store_4d(&dst, ptx::smem_addr(buf), 0, int(a * args.a_step1 + bb * args.b_step1), 0,
-                        int(bb * args.b_step3));
+      int c1, c3;
+      coords(t0 + j, c1, c3);
+      ptx::tma_store_4d(&dst, ptx::smem_addr(buf), 0, c1, 0, c3);
       ptx::bulk_commit();
-      if (i + 2 < t1) {
-        ptx::bulk_wait_read<0>();
-        issue_load(i + 2, b);
+      if (j >= 1 && j + 2 < n) {
+        ptx::bulk_wait_read<1>();   // the store of tile j-1 has left its buffer
+        issue_load(j + 2);
       }
     }
   }
   if (tid == 0) {
     if (aborted) {
-      // Let copies already in flight land before the CTA's shared memory is released.
-      // Pending loads: tile `it` (buffer it & 1) and tile it + 1 (the other buffer).
-      for (uint64_t j = it; j < it + 2 && t0 + j < t1; ++j)
-        ptx::mbar_wait_bounded(bar0 + 8 * uint32_t(j & 1), uint32_t((j >> 1) & 1), args.timeout_ns);
+      // Let loads already issued (tiles j .. max(j+1, kBufs-1)) land before the
+      // CTA's shared memory is released.
+      const uint64_t last = (j + 1 > uint64_t(kBufs - 1)) ? j + 1 : uint64_t(kBufs - 1);
+      for (uint64_t q = j; q <= last && q < n; ++q)
+        ptx::mbar_wait_bounded(bar0 + 8 * uint32_t(q % kBufs), uint32_t((q / kBufs) & 1), args.timeout_ns);
       atomicExch(args.status, int(SDFT_ERR_TIMEOUT));
     }
     ptx::bulk_wait<0>();

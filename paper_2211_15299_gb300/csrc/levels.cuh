@@ -8,7 +8,7 @@
 namespace sdft {
 
 template <class R, int PLO, int PHI, bool LAST>
-sdft_status launch_level(int grid, const CUtensorMap& src, const CUtensorMap& dst, const LevelArgs& a,
+sdft_status launch_level(int grid, const CUtensorMap& src, const CUtensorMap& dst, const LevelArgs<R>& a,
                          cudaStream_t st) {
   auto fn = k_level<R, PLO, PHI, LAST>;
   sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(kLevelSmem));
@@ -21,7 +21,7 @@ sdft_status launch_level(int grid, const CUtensorMap& src, const CUtensorMap& ds
 // Level 0: stage bits [0, PHI).
 template <class R, int PHI = 5>
 sdft_status dispatch_first(int phi, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
-                           const LevelArgs& a, cudaStream_t st) {
+                           const LevelArgs<R>& a, cudaStream_t st) {
   constexpr int TB = KT<R>::TB;
   if constexpr (PHI > TB) {
     return SDFT_ERR_UNSUPPORTED;
@@ -40,7 +40,7 @@ sdft_status dispatch_first(int phi, bool last, int grid, const CUtensorMap& src,
 // Later levels: virtual stage bits [TB - Q, TB).
 template <class R, int Q = 1>
 sdft_status dispatch_later(int q, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
-                           const LevelArgs& a, cudaStream_t st) {
+                           const LevelArgs<R>& a, cudaStream_t st) {
   constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
   if constexpr (Q > TB - CB) {
     return SDFT_ERR_UNSUPPORTED;
@@ -94,7 +94,8 @@ sdft_status launch_plan(const Plan& p, uint64_t batch, const void* in, void* out
     sdft_status s = encode_map(&ms, in, dims, strides, box);
     if (s == SDFT_OK) s = encode_map(&md, out, dims, strides, box);
     if (s != SDFT_OK) return s;
-    LevelArgs a{};
+    LevelArgs<R> a{};
+    for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
     a.n_tiles = n_tiles;
     a.nB = n_tiles;
     a.a_step1 = 0;
@@ -123,7 +124,8 @@ sdft_status launch_plan(const Plan& p, uint64_t batch, const void* in, void* out
     const uint32_t box[4] = {32, 1u << L.lg, 1u << Q, 1};
     sdft_status s = encode_map(&m, out, dims, strides, box);
     if (s != SDFT_OK) return s;
-    LevelArgs a{};
+    LevelArgs<R> a{};
+    for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
     a.n_tiles = L.n_gb * Z;
     a.nB = Z;
     a.a_step1 = int32_t(1u << L.lg);

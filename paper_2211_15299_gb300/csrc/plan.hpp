@@ -57,6 +57,7 @@ struct Plan {
   void* d_tw = nullptr;           // device twiddles (float2 or double2)
   int* d_status = nullptr;        // device status word
   uint64_t device_bytes = 0;
+  double tw0[32] = {0};           // level-0 table entries 1..15 (rounded to prec), for kernel params
 };
 
 // Host-side planning (plan.cpp). Fills everything except the device fields.

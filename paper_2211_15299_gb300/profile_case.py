@@ -1,0 +1,48 @@
+"""Run one transform configuration a few times (for profilers) and report the
+device status word; exits non-zero if the status is not 0.
+
+    python -m paper_2211_15299_gb300.profile_case --log2n 20 --log2k 12 --batch 4096 --reps 4
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--log2n", type=int, default=20)
+    ap.add_argument("--log2k", type=int, default=12)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--reps", type=int, default=4)
+    ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
+    args = ap.parse_args()
+
+    import torch
+
+    import workloads as W
+    from paper_2211_15299_gb300 import Plan
+
+    inst, _ = W.workload_shared(M=args.log2n, s=args.log2k, batch=1, coeffs=False)
+    plan = Plan(args.log2n, inst.J, args.prec)
+    dt = torch.complex64 if args.prec == "c64" else torch.complex128
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1)
+    x = torch.randn((args.batch, inst.k), dtype=dt, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    for _ in range(args.reps):
+        plan.execute_strided(x, y)
+    torch.cuda.synchronize()
+    st = plan.device_status()
+    print(f"profile_case log2n={args.log2n} log2k={args.log2k} batch={args.batch} {args.prec} "
+          f"reps={args.reps} device_status={st:#x}", flush=True)
+    return 0 if st == 0 else 3
+
+
+if __name__ == "__main__":
+    sys.exit(main())
