@@ -147,14 +147,20 @@ sdft_status sdft_plan_destroy(sdft_plan plan);
 
 /*
  * sdft_batch_create - build a device work queue for instances i = 0..n-1 with
- * plans[i] (repeats allowed; all of one precision). Instance i's k_i samples and
- * coefficients sit at element offset offsets[i] of the packed buffers, with
- * offsets[0] = 0 and offsets[i+1] = offsets[i] + k_i (see sdft_batch_info).
- * The plans must outlive the batch. Allocates the queue on the current device.
+ * plans[i] (repeats allowed; all of one precision, all on the current device).
+ * The library chooses the packed layout: instances sit by decreasing k, so each
+ * instance's element offset is a multiple of its k; sdft_batch_info returns the
+ * offset of every instance (in the caller's order) and the total. Work items:
+ * level-0 tiles (several same-size instances per 32 KiB tile), later-level tiles
+ * placed at least 4 x grid items after their instance's previous level, and
+ * ranges of instances with k <= 16. The plans must outlive the batch (the queue
+ * points at their device twiddle tables). Allocates the queue, the dependency
+ * counters and a status word on the device.
  */
 sdft_status sdft_batch_create(const sdft_plan* plans, uint64_t n, sdft_batch* out);
 
-/* Total coefficients, and (if `offsets` is not NULL) the n+1 element offsets. */
+/* Total coefficients, and (if `offsets` is not NULL) n+1 values: offsets[i] is the
+ * element offset of instance i in the packed buffers, offsets[n] the total. */
 sdft_status sdft_batch_info(sdft_batch batch, uint64_t* total, uint64_t* offsets);
 
 /*
@@ -168,6 +174,20 @@ sdft_status sdft_batch_execute(sdft_batch batch, const void* d_samples, void* d_
 
 /* Device status word of a batch (as for plans). */
 sdft_status sdft_batch_device_status(sdft_batch batch, int clear);
+
+/* Diagnostics: override the bound on device-side waits (0 restores the default)
+ * and add `need_bias` to every dependency target. A non-zero bias makes every
+ * later-level tile wait for a count that is never reached, so the launch ends
+ * with SDFT_ERR_TIMEOUT in the status word after `timeout_ns`: it exists to test
+ * that path. */
+sdft_status sdft_batch_set_wait(sdft_batch batch, uint64_t timeout_ns, uint32_t need_bias);
+
+/* Work items, dependency counters and grid size (co-resident CTAs) of a batch;
+ * returns SDFT_ERR_ARG if the item list breaks its ordering invariants (every
+ * dependency target reached exactly, by items at least 4 x grid positions
+ * earlier). A batch built from host-only plans (SDFT_PLAN_HOST_ONLY) has its item
+ * list for inspection (grid taken as 304) but cannot execute. */
+sdft_status sdft_batch_stats(sdft_batch batch, uint64_t* n_items, uint64_t* n_counters, int* grid);
 
 /* Release a batch after synchronising its work. */
 sdft_status sdft_batch_destroy(sdft_batch batch);

@@ -56,6 +56,8 @@ SIGNATURES = {
     "sdft_batch_info": (c_int, [c_vp, P_u64, P_u64]),
     "sdft_batch_execute": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "sdft_batch_device_status": (c_int, [c_vp, c_int]),
+    "sdft_batch_set_wait": (c_int, [c_vp, c_u64, c_u32]),
+    "sdft_batch_stats": (c_int, [c_vp, P_u64, P_u64, ctypes.POINTER(c_int)]),
     "sdft_batch_destroy": (c_int, [c_vp]),
     "sdft_status_string": (ctypes.c_char_p, [c_int]),
     "sdft_last_cuda_error": (c_int, []),
@@ -194,6 +196,16 @@ def sdft_batch_execute(batch: int, d_samples, d_coeffs, stream=None) -> None:
 
 def sdft_batch_device_status(batch: int, clear: bool = False) -> int:
     return int(_lib.sdft_batch_device_status(batch, int(bool(clear))))
+
+
+def sdft_batch_set_wait(batch: int, timeout_ns: int = 0, need_bias: int = 0) -> None:
+    _check(_lib.sdft_batch_set_wait(batch, int(timeout_ns), int(need_bias)), "sdft_batch_set_wait")
+
+
+def sdft_batch_stats(batch: int):
+    ni, nc, g = c_u64(), c_u64(), c_int()
+    _check(_lib.sdft_batch_stats(batch, ctypes.byref(ni), ctypes.byref(nc), ctypes.byref(g)), "sdft_batch_stats")
+    return int(ni.value), int(nc.value), int(g.value)
 
 
 def sdft_batch_destroy(batch: int) -> None:

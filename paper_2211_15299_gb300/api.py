@@ -126,7 +126,25 @@ class Batch:
         self.plans = list(plans)            # keep the plans alive
         self.prec = self.plans[0].prec
         self.handle = N.sdft_batch_create([p.handle for p in self.plans])
-        self.total, self.offsets = N.sdft_batch_info(self.handle, len(self.plans))
+        self.total, offs = N.sdft_batch_info(self.handle, len(self.plans))
+        self.offsets = offs[:-1].astype(np.int64)   # element offset of each instance (caller's order)
+
+    def stats(self):
+        """(work items, dependency counters, grid); raises if the item list breaks its invariants."""
+        return N.sdft_batch_stats(self.handle)
+
+    def set_wait(self, timeout_ns: int = 0, need_bias: int = 0):
+        N.sdft_batch_set_wait(self.handle, timeout_ns, need_bias)
+
+    def pack(self, per_instance):
+        """Host-side helper: place per-instance numpy arrays at their offsets."""
+        out = np.zeros(self.total, dtype=np.complex128)
+        for p, off, x in zip(self.plans, self.offsets, per_instance):
+            out[off:off + p.k] = x
+        return out
+
+    def unpack(self, flat):
+        return [flat[off:off + p.k] for p, off in zip(self.plans, self.offsets)]
 
     @property
     def dtype(self):

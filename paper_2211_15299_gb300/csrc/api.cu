@@ -14,10 +14,6 @@
 #include "launch.hpp"
 #include "plan.hpp"
 
-struct sdft_plan_s {
-  sdft::Plan p;
-};
-
 namespace sdft {
 
 namespace {

@@ -1,13 +1,458 @@
-// Uneven batches (placeholder until the work-queue kernel lands).
-#include "launch.hpp"
+// Uneven batches: many instances with their own plans in one persistent,
+// cooperatively launched work-queue kernel (queue.cuh).
+//
+// Packing: instances are laid out by decreasing k, so every offset is a
+// multiple of its own k (a prefix sum of larger or equal powers of two). One
+// 2-D tensor map per power-of-two box height then covers every level-0 tile of
+// the packed buffers, and one 4-D map per (lo, hi) covers every later-level tile.
+//
+// Item list: level-0 tiles instance by instance (whole same-size instances
+// grouped into power-of-two tiles); an instance's next-level tiles are held back
+// until at least 4 G items (G = grid size) have been emitted after its previous
+// level, then emitted together; no-op items pad the tail where fewer items
+// remain. Consecutive items go to consecutive CTAs, so list order is roughly
+// time order and the intermediate of a multi-level instance is read back from L2.
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "plan.hpp"
+#include "queue.cuh"
+
+namespace sdft {
+
+struct BatchMap {
+  bool first;          // level-0 2-D map (else later-level 4-D map)
+  bool load;           // level 0: load map (box of 2^r rows on the samples) or store map (coefficients)
+  uint32_t r;          // level 0: log2 rows of the box
+  uint32_t lo, hi, lg; // later levels
+};
+
+// Grid size assumed when a batch is built from host-only plans (2 CTAs x 152 SMs).
+constexpr int kHostOnlyGrid = 304;
+
+struct Batch {
+  int device = -1;
+  sdft_prec prec = SDFT_C64;
+  uint64_t n = 0, total = 0;
+  std::vector<uint64_t> offsets;     // user order, plus total
+  std::vector<QItem> items;
+  std::vector<BatchMap> maps;        // slot -> map description
+  QItem* d_items = nullptr;
+  QInst* d_insts = nullptr;
+  uint32_t* d_counters = nullptr;
+  uint64_t n_counters = 0;
+  int* d_status = nullptr;
+  int grid = 0;
+  uint64_t timeout_ns = 0;           // 0: library default
+  uint32_t need_bias = 0;            // diagnostics: added to every dependency target
+};
+
+}  // namespace sdft
+
+struct sdft_batch_s {
+  sdft::Batch b;
+};
+
+namespace sdft {
+namespace {
+
+void free_batch(Batch& b) {
+  if (b.d_items) cudaFree(b.d_items);
+  if (b.d_insts) cudaFree(b.d_insts);
+  if (b.d_counters) cudaFree(b.d_counters);
+  if (b.d_status) cudaFree(b.d_status);
+  b.d_items = nullptr;
+  b.d_insts = nullptr;
+  b.d_counters = nullptr;
+  b.d_status = nullptr;
+}
+
+int log2u(uint64_t x) { return 63 - __builtin_clzll(x); }
+
+// Invariants of an item list: every dependency refers to a counter signalled
+// only by items earlier in the list, reaches its target exactly, and sits at
+// least 4 x grid positions back; level-0 tiles cover aligned rows.
+sdft_status check_items(const Batch& B) {
+  std::vector<uint64_t> sig_count(B.n_counters, 0), sig_last(B.n_counters, 0);
+  const uint64_t lag = 4ull * uint64_t(B.grid);
+  for (uint64_t p = 0; p < B.items.size(); ++p) {
+    const QItem& it = B.items[p];
+    if (it.dep != kNone) {
+      if (it.dep >= B.n_counters) return SDFT_ERR_ARG;
+      if (sig_count[it.dep] != it.need) return SDFT_ERR_ARG;     // all producers precede
+      if (p < sig_last[it.dep] + lag) return SDFT_ERR_ARG;
+    }
+    if (it.sig != kNone) {
+      if (it.sig >= B.n_counters) return SDFT_ERR_ARG;
+      ++sig_count[it.sig];
+      sig_last[it.sig] = p;
+    }
+  }
+  return SDFT_OK;
+}
+
+struct Group {            // later-level tiles of one instance, waiting to be emitted
+  uint64_t ready;         // emit once this many items exist
+  std::vector<QItem> items;
+  int64_t next_inst = -1; // instance whose next level follows this group (-1: none)
+  size_t next_level = 0;
+};
+
+}  // namespace
+
+// Build the item list and device arrays of a batch (plans already validated).
+static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
+  const sdft_prec prec = plans[0]->p.prec;
+  const uint32_t TB = tile_bits(prec), CB = row_bits(prec);
+  const uint32_t NT = prec == SDFT_C64 ? 256 : 128;
+  B.prec = prec;
+  B.n = n;
+  if (B.device >= 0) {
+    B.grid = prec == SDFT_C64 ? queue_grid_f32() : queue_grid_f64();
+    if (B.grid <= 0) return SDFT_ERR_CUDA;
+  } else {
+    B.grid = kHostOnlyGrid;     // host-only batches: item list for inspection only
+  }
+
+  // Pack by decreasing k (stable).
+  std::vector<uint64_t> order(n);
+  for (uint64_t i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](uint64_t a, uint64_t b) { return plans[a]->p.s > plans[b]->p.s; });
+  B.offsets.assign(n + 1, 0);
+  std::vector<QInst> insts(n);
+  uint64_t off = 0;
+  for (uint64_t q = 0; q < n; ++q) {
+    const Plan& p = plans[order[q]]->p;
+    B.offsets[order[q]] = off;
+    insts[q].tw = p.d_tw;
+    insts[q].off = off;
+    insts[q].s = p.s;
+    insts[q].pad = 0;
+    insts[q].scale = std::ldexp(1.0, int(p.M) - int(p.s));
+    off += p.k;
+  }
+  B.total = off;
+  B.offsets[n] = off;
+
+  // Map slots: level-0 load/store pairs at 2r, 2r+1 (r = 0..8); later levels after.
+  B.maps.assign(18, BatchMap{});
+  for (uint32_t r = 0; r <= 8; ++r) {
+    B.maps[2 * r] = BatchMap{true, true, r, 0, 0, 0};
+    B.maps[2 * r + 1] = BatchMap{true, false, r, 0, 0, 0};
+  }
+  std::map<std::pair<uint32_t, uint32_t>, uint32_t> later_slot;
+  auto slot_for = [&](const Level& L) -> int {
+    auto key = std::make_pair(L.lo, L.hi);
+    auto it = later_slot.find(key);
+    if (it != later_slot.end()) return int(it->second);
+    if (B.maps.size() >= size_t(kMaxMaps)) return -1;
+    const uint32_t slot = uint32_t(B.maps.size());
+    B.maps.push_back(BatchMap{false, false, 0, L.lo, L.hi, L.lg});
+    later_slot[key] = slot;
+    return int(slot);
+  };
+
+  const uint64_t lag = 4ull * uint64_t(B.grid);
+  std::vector<QItem>& items = B.items;
+  items.clear();
+  std::deque<Group> pending;
+  uint32_t n_ctr = 0;
+
+  auto later_group = [&](uint64_t q, size_t level, uint32_t dep, uint32_t need, Group& g) -> sdft_status {
+    const Plan& p = plans[order[q]]->p;
+    const Level& L = p.levels[level];
+    const int slot = slot_for(L);
+    if (slot < 0) return SDFT_ERR_UNSUPPORTED;
+    const uint64_t zs = 1ull << (p.s - L.hi);       // z rows of this instance
+    const uint64_t z0 = insts[q].off >> L.hi;
+    if (z0 + zs > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
+    const bool more = level + 1 < p.levels.size();
+    const uint32_t sig = more ? n_ctr++ : kNone;
+    const size_t es = size_t(elem_bytes(prec));
+    for (uint64_t gb = 0; gb < L.n_gb; ++gb)
+      for (uint64_t z = 0; z < zs; ++z) {
+        QItem it{};
+        it.variant = uint16_t(q_variant_later(int(L.hi - L.lo), L.last));
+        it.map = uint16_t(slot);
+        it.count = 1;
+        it.inst = uint32_t(q);
+        it.dep = dep;
+        it.need = need;
+        it.sig = sig;
+        it.c1 = int32_t(gb << L.lg);
+        it.c3 = int32_t(z0 + z);
+        it.tw = static_cast<const char*>(p.d_tw) + (L.tw_off + gb * L.tw_len) * es - (size_t(1) << L.plo) * es;
+        it.scale = insts[q].scale;
+        g.items.push_back(it);
+      }
+    if (more) {
+      g.next_inst = int64_t(q);
+      g.next_level = level + 1;
+    }
+    return SDFT_OK;
+  };
+
+  auto emit = [&](const QItem& it) -> sdft_status {
+    items.push_back(it);
+    while (!pending.empty() && pending.front().ready <= items.size()) {
+      Group g = std::move(pending.front());
+      pending.pop_front();
+      const uint32_t sig = g.items.empty() ? kNone : g.items.front().sig;
+      const uint32_t cnt = uint32_t(g.items.size());
+      for (const QItem& x : g.items) items.push_back(x);
+      if (g.next_inst >= 0) {
+        Group h;
+        h.ready = items.size() + lag;
+        sdft_status s = later_group(uint64_t(g.next_inst), g.next_level, sig, cnt, h);
+        if (s != SDFT_OK) return s;
+        pending.push_back(std::move(h));
+      }
+    }
+    return SDFT_OK;
+  };
+
+  uint64_t q = 0;
+  while (q < n) {
+    const uint32_t s = insts[q].s;
+    if (s <= kSmallMax) {                       // one thread per instance
+      uint64_t cnt = 0;
+      while (q + cnt < n && insts[q + cnt].s <= kSmallMax && cnt < NT) ++cnt;
+      QItem it{};
+      it.variant = uint16_t(kVSmall);
+      it.count = uint32_t(cnt);
+      it.inst = uint32_t(q);
+      it.dep = kNone;
+      it.sig = kNone;
+      sdft_status st = emit(it);
+      if (st != SDFT_OK) return st;
+      q += cnt;
+    } else if (s <= TB) {                       // whole instances per tile
+      uint64_t run = 0;
+      while (q + run < n && insts[q + run].s == s) ++run;
+      const uint64_t G = 1ull << (TB - s);
+      uint64_t left = run;
+      while (left) {
+        const uint64_t cnt = 1ull << log2u(std::min(G, left));
+        const uint64_t rows = cnt << (s - CB);
+        const uint64_t row0 = insts[q].off >> CB;
+        if (row0 + rows > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
+        QItem it{};
+        it.variant = uint16_t(q_variant_first(int(s)));
+        it.map = uint16_t(2 * log2u(rows));
+        it.count = uint32_t(cnt);
+        it.inst = uint32_t(q);
+        it.dep = kNone;
+        it.sig = kNone;
+        it.c1 = int32_t(row0);
+        it.c3 = 0;
+        sdft_status st = emit(it);
+        if (st != SDFT_OK) return st;
+        q += cnt;
+        left -= cnt;
+      }
+    } else {                                    // 2^TB chunks, then later levels
+      const Plan& p = plans[order[q]]->p;
+      const uint64_t chunks = 1ull << (s - TB);
+      const uint32_t sig = n_ctr++;
+      const uint64_t row0 = insts[q].off >> CB;
+      if (row0 + (chunks << (TB - CB)) > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
+      for (uint64_t ch = 0; ch < chunks; ++ch) {
+        QItem it{};
+        it.variant = uint16_t(kVFirstChunk);
+        it.map = uint16_t(2 * (TB - CB));
+        it.count = 1;
+        it.inst = uint32_t(q);
+        it.dep = kNone;
+        it.sig = sig;
+        it.c1 = int32_t(row0 + (ch << (TB - CB)));
+        it.c3 = 0;
+        sdft_status st = emit(it);
+        if (st != SDFT_OK) return st;
+      }
+      Group g;
+      g.ready = items.size() + lag;
+      sdft_status st = later_group(q, 1, sig, uint32_t(chunks), g);
+      if (st != SDFT_OK) return st;
+      pending.push_back(std::move(g));
+      (void)p;
+      ++q;
+    }
+  }
+  // Tail: pad with no-op items so every dependency keeps its distance.
+  while (!pending.empty()) {
+    QItem nop{};
+    nop.variant = uint16_t(kVNop);
+    nop.dep = kNone;
+    nop.sig = kNone;
+    sdft_status st = emit(nop);
+    if (st != SDFT_OK) return st;
+  }
+  B.n_counters = n_ctr;
+  if (B.device < 0) return SDFT_OK;
+
+  // Device arrays.
+  cudaError_t e = cudaMalloc(&B.d_status, 256);
+  if (e == cudaSuccess) e = cudaMemset(B.d_status, 0, 256);
+  if (e == cudaSuccess) e = cudaMalloc(&B.d_items, sizeof(QItem) * std::max<size_t>(items.size(), 1));
+  if (e == cudaSuccess) e = cudaMalloc(&B.d_insts, sizeof(QInst) * std::max<uint64_t>(n, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&B.d_counters, sizeof(uint32_t) * std::max<uint64_t>(n_ctr, 1));
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpy(B.d_items, items.data(), sizeof(QItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(B.d_insts, insts.data(), sizeof(QInst) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SDFT_ERR_NOMEM : cuda_fail(e);
+  return SDFT_OK;
+}
+
+// Encode the batch's tensor maps over (in, out) into the kernel parameters.
+static sdft_status encode_batch_maps(const Batch& B, const void* in, void* out, QParams& prm) {
+  const uint32_t CB = row_bits(B.prec);
+  const uint64_t es = uint64_t(elem_bytes(B.prec));
+  const uint64_t rows = B.total >> CB;
+  for (size_t slot = 0; slot < B.maps.size(); ++slot) {
+    const BatchMap& m = B.maps[slot];
+    std::memset(&prm.maps[slot], 0, sizeof(CUtensorMap));
+    if (m.first) {
+      if (rows < (1ull << m.r)) continue;       // never used: no tile of that height fits
+      const uint64_t dims[4] = {32, rows, 1, 1};
+      const uint64_t strides[3] = {128, rows * 128, rows * 128};
+      const uint32_t box[4] = {32, 1u << m.r, 1, 1};
+      sdft_status s = encode_map(&prm.maps[slot], m.load ? in : out, dims, strides, box);
+      if (s != SDFT_OK) return s;
+    } else {
+      const uint32_t Q = m.hi - m.lo;
+      const uint64_t zs = B.total >> m.hi;
+      const uint64_t dims[4] = {32, 1ull << (m.lo - CB), 1ull << Q, zs};
+      const uint64_t strides[3] = {128, (1ull << m.lo) * es, (1ull << m.hi) * es};
+      const uint32_t box[4] = {32, 1u << m.lg, 1u << Q, 1};
+      sdft_status s = encode_map(&prm.maps[slot], out, dims, strides, box);
+      if (s != SDFT_OK) return s;
+    }
+  }
+  return SDFT_OK;
+}
+
+static sdft_status run_batch(Batch& B, const void* in, void* out, cudaStream_t st) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev != B.device) return SDFT_ERR_ARG;
+  if (!in || !out) return SDFT_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return SDFT_ERR_ARG;
+  const uint64_t bytes = B.total * uint64_t(elem_bytes(B.prec));
+  const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
+  if (a != b && a < b + bytes && b < a + bytes) return SDFT_ERR_ARG;
+  if (B.items.empty()) return SDFT_OK;
+  QParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  sdft_status s = encode_batch_maps(B, in, out, prm);
+  if (s != SDFT_OK) return s;
+  prm.a.items = B.d_items;
+  prm.a.n_items = B.items.size();
+  prm.a.insts = B.d_insts;
+  prm.a.counters = B.d_counters;
+  prm.a.in = in;
+  prm.a.out = out;
+  prm.a.status = B.d_status;
+  prm.a.timeout_ns = B.timeout_ns ? B.timeout_ns : wait_timeout_ns();
+  prm.a.need_bias = B.need_bias;
+  if (B.n_counters) {
+    e = cudaMemsetAsync(B.d_counters, 0, sizeof(uint32_t) * B.n_counters, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  const int grid = int(std::min<uint64_t>(uint64_t(B.grid), B.items.size()));
+  return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, st) : launch_queue_f64(prm, grid, st);
+}
+
+}  // namespace sdft
 
 extern "C" {
-sdft_status sdft_batch_create(const sdft_plan*, uint64_t, sdft_batch* out) {
-  if (out) *out = nullptr;
-  return SDFT_ERR_UNSUPPORTED;
+
+sdft_status sdft_batch_create(const sdft_plan* plans, uint64_t n, sdft_batch* out) {
+  if (!out) return SDFT_ERR_ARG;
+  *out = nullptr;
+  if (!plans || n == 0 || n > 0xffffffffull) return SDFT_ERR_ARG;
+  for (uint64_t i = 0; i < n; ++i)
+    if (!plans[i]) return SDFT_ERR_ARG;
+  // Either every plan is host-only (a batch for inspection) or all live on the current device.
+  const bool host_only = plans[0]->p.device < 0;
+  int dev = -1;
+  if (!host_only) {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return sdft::cuda_fail(e);
+  }
+  for (uint64_t i = 0; i < n; ++i) {
+    if ((plans[i]->p.device < 0) != host_only) return SDFT_ERR_NO_DEVICE;
+    if (!host_only && plans[i]->p.device != dev) return SDFT_ERR_ARG;
+    if (plans[i]->p.prec != plans[0]->p.prec) return SDFT_ERR_PRECISION;
+  }
+  sdft_batch_s* h = new (std::nothrow) sdft_batch_s();
+  if (!h) return SDFT_ERR_NOMEM;
+  h->b.device = dev;
+  sdft_status s;
+  try {
+    s = sdft::build_batch(h->b, plans, n);
+  } catch (const std::bad_alloc&) {
+    s = SDFT_ERR_NOMEM;
+  }
+  if (s != SDFT_OK) {
+    sdft::free_batch(h->b);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return SDFT_OK;
 }
-sdft_status sdft_batch_info(sdft_batch, uint64_t*, uint64_t*) { return SDFT_ERR_UNSUPPORTED; }
-sdft_status sdft_batch_execute(sdft_batch, const void*, void*, void*) { return SDFT_ERR_UNSUPPORTED; }
-sdft_status sdft_batch_device_status(sdft_batch, int) { return SDFT_ERR_UNSUPPORTED; }
-sdft_status sdft_batch_destroy(sdft_batch) { return SDFT_ERR_UNSUPPORTED; }
+
+sdft_status sdft_batch_info(sdft_batch batch, uint64_t* total, uint64_t* offsets) {
+  if (!batch) return SDFT_ERR_ARG;
+  if (total) *total = batch->b.total;
+  if (offsets) std::memcpy(offsets, batch->b.offsets.data(), sizeof(uint64_t) * (batch->b.n + 1));
+  return SDFT_OK;
 }
+
+sdft_status sdft_batch_execute(sdft_batch batch, const void* d_samples, void* d_coeffs, void* stream) {
+  if (!batch) return SDFT_ERR_ARG;
+  if (batch->b.device < 0) return SDFT_ERR_NO_DEVICE;
+  return sdft::run_batch(batch->b, d_samples, d_coeffs, static_cast<cudaStream_t>(stream));
+}
+
+sdft_status sdft_batch_device_status(sdft_batch batch, int clear) {
+  if (!batch) return SDFT_ERR_ARG;
+  if (batch->b.device < 0) return SDFT_ERR_NO_DEVICE;
+  int v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&v, batch->b.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear) e = cudaMemset(batch->b.d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return sdft::cuda_fail(e);
+  return sdft_status(v);
+}
+
+sdft_status sdft_batch_set_wait(sdft_batch batch, uint64_t timeout_ns, uint32_t need_bias) {
+  if (!batch) return SDFT_ERR_ARG;
+  batch->b.timeout_ns = timeout_ns;
+  batch->b.need_bias = need_bias;
+  return SDFT_OK;
+}
+
+sdft_status sdft_batch_stats(sdft_batch batch, uint64_t* n_items, uint64_t* n_counters, int* grid) {
+  if (!batch) return SDFT_ERR_ARG;
+  if (n_items) *n_items = batch->b.items.size();
+  if (n_counters) *n_counters = batch->b.n_counters;
+  if (grid) *grid = batch->b.grid;
+  return sdft::check_items(batch->b);
+}
+
+sdft_status sdft_batch_destroy(sdft_batch batch) {
+  if (!batch) return SDFT_ERR_ARG;
+  sdft::free_batch(batch->b);
+  delete batch;
+  return SDFT_OK;
+}
+
+}  // extern "C"

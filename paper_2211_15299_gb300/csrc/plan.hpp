@@ -72,3 +72,8 @@ void twiddle_f64(const Plan& p, uint32_t m, uint64_t u, double& re, double& im);
 template <class T> void fill_device_tables(const Plan& p, T* out);
 
 }  // namespace sdft
+
+// The opaque handle of the C ABI.
+struct sdft_plan_s {
+  sdft::Plan p;
+};

@@ -1,0 +1,385 @@
+// Persistent work-queue kernel: many instances with their own plans (uneven
+// batches) and multi-level instances with L2-resident intermediates, in one
+// launch.
+//
+// Items (host-built, see batch.cu) are processed round-robin: CTA c takes items
+// c, c + G, c + 2G, ... in list order, on a cooperatively launched grid (all
+// CTAs resident). Item kinds:
+//   * small range: up to NT instances with log2 k <= 4, one thread each;
+//   * level-0 tile: 2^(TB - s) whole instances of size 2^s (s <= TB), or one
+//     2^TB chunk of a larger instance (stage bits [0, min(s, TB)));
+//   * later-level tile: one group block of one instance (stage bits [lo, hi)).
+// A later-level item waits (bounded) until its instance's previous level has
+// signalled every tile; the host places it at least 4 G items after those
+// tiles, so the wait never targets an item of the same CTA that has not yet
+// signalled, and the intermediate is still in L2 when it is read back.
+#pragma once
+
+#include "kernels.cuh"
+#include "launch.hpp"
+
+namespace sdft {
+
+constexpr uint32_t kNone = 0xffffffffu;
+
+struct QItem {            // 48 bytes
+  uint16_t variant;       // kind and template variant, see q_variant_*
+  uint16_t map;           // map slot (level 0: load slot, store slot = map + 1)
+  uint32_t count;         // instances (level 0: tile's instances; small: range length)
+  uint32_t inst;          // first instance
+  uint32_t dep;           // counter to wait on, or kNone
+  uint32_t need;          // value the counter must reach
+  uint32_t sig;           // counter to increment once the item's store is complete, or kNone
+  int32_t c1, c3;         // TMA coordinates of the tile
+  const void* tw;         // later levels: the group block's table, absolute-indexed
+  double scale;           // later levels: N/k of the instance
+};
+
+struct QInst {            // 32 bytes
+  const void* tw;         // level-0 table of the instance's plan, absolute-indexed
+  uint64_t off;           // element offset in the packed buffers
+  uint32_t s;             // log2 k
+  uint32_t pad;
+  double scale;           // N/k
+};
+
+constexpr int kMaxMaps = 40;
+
+struct QArgs {
+  const QItem* items;
+  uint64_t n_items;
+  const QInst* insts;
+  uint32_t* counters;       // zeroed before every launch
+  const void* in;           // packed samples (small items use plain loads)
+  void* out;                // packed coefficients
+  int* status;
+  uint64_t timeout_ns;
+  uint32_t need_bias;       // added to every dependency target (0; non-zero only to test timeouts)
+};
+
+// Kernel parameters: the arguments and the tensor maps over the packed buffers
+// (maps in parameter space are baked into a captured CUDA graph).
+struct QParams {
+  CUtensorMap maps[kMaxMaps];
+  QArgs a;
+};
+
+// Variant ids.
+constexpr int kVSmall = 0;
+constexpr int kVNop = 0x7fff;     // padding item: no data, keeps dependency distances
+constexpr int q_variant_first(int s) { return 1 + (s - 5); }        // level 0, 5 <= s <= TB
+constexpr int kVFirstChunk = 15;                                       // level 0, s > TB
+constexpr int q_variant_later(int Q, bool last) { return 16 + 2 * (Q - 1) + (last ? 1 : 0); }
+
+// ---- one pass with per-instance twiddle tables ------------------------------------
+// Elements of the tile with index T belong to instance (T >> SB) of the tile
+// (SB >= TB: one instance). tab[g] is the absolute-indexed table of the g-th
+// instance among the thread's elements (g = E >> SB), sc[g] its N/k.
+template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SB>
+__device__ __forceinline__ void tile_pass_q(char* buf, const typename KT<R>::C* const* tab, const R* sc,
+                                            uint32_t tid) {
+  using C = typename KT<R>::C;
+  constexpr uint32_t LOWM = (1u << B) - 1u;
+  const uint32_t F = (tid & LOWM) | ((tid >> B) << (B + 4));
+  const uint32_t rF = row_part<R>(F), xF = xor_part<R>(F);
+  C v[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const uint32_t E = uint32_t(e) << B;
+    v[e] = *reinterpret_cast<const C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)));
+  }
+#pragma unroll
+  for (int m1 = SLO; m1 < SHI; ++m1) {
+    const int q = m1 - B;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      if ((e >> q) & 1) continue;
+      const int eh = e | (1 << q);
+      const int g = (SB >= 32) ? 0 : int((uint32_t(e) << B) >> SB);
+      const C wt = __ldg(tab[g] + (1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B));
+      if (SCALE && m1 == SHI - 1)
+        bfly_scaled(v[e], v[eh], wt, sc[g]);
+      else
+        bfly(v[e], v[eh], wt);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const uint32_t E = uint32_t(e) << B;
+    *reinterpret_cast<C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E))) = v[e];
+  }
+  if constexpr (FENCE) ptx::fence_proxy_async_smem();
+  __syncthreads();
+}
+
+template <class R, int PLO, int PHI, bool LAST, int SB, int P = 0>
+__device__ __forceinline__ void run_passes_q(char* buf, const QArgs& a, const QItem& it, uint32_t tid) {
+  using C = typename KT<R>::C;
+  constexpr int TB = KT<R>::TB;
+  if constexpr (P < n_passes(TB, PLO, PHI)) {
+    constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
+    constexpr bool FINAL = (SHI == PHI);
+    constexpr int NG = (SB >= 32 || B + 4 <= SB) ? 1 : (1 << (B + 4 - SB));
+    const C* tab[NG];
+    R sc[NG];
+    if constexpr (SB >= 32) {
+      tab[0] = static_cast<const C*>(it.tw);
+      sc[0] = R(it.scale);
+    } else {
+      const uint32_t F = (tid & ((1u << B) - 1u)) | ((tid >> B) << (B + 4));
+      const uint32_t g0 = (SB >= TB) ? 0u : (F >> SB);
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        // threads beyond the tile's instances compute on stale rows that are never stored
+        const uint32_t gi = (g0 + uint32_t(g) < it.count) ? g0 + uint32_t(g) : 0u;
+        const QInst* ins = a.insts + it.inst + gi;
+        tab[g] = static_cast<const C*>(ins->tw);
+        sc[g] = R(ins->scale);
+      }
+    }
+    tile_pass_q<R, B, SLO, SHI, LAST && FINAL, FINAL, SB>(buf, tab, sc, tid);
+    run_passes_q<R, PLO, PHI, LAST, SB, P + 1>(buf, a, it, tid);
+  }
+}
+
+// Level 0 with 5 <= s <= TB: tiles of whole instances.
+template <class R, int S = 5>
+__device__ __forceinline__ bool dispatch_first_q(int v, char* buf, const QArgs& a, const QItem& it, uint32_t tid) {
+  if constexpr (S > KT<R>::TB) {
+    return false;
+  } else {
+    if (v == q_variant_first(S)) {
+      run_passes_q<R, 0, S, true, S>(buf, a, it, tid);
+      return true;
+    }
+    return dispatch_first_q<R, S + 1>(v, buf, a, it, tid);
+  }
+}
+
+template <class R, int Q = 1>
+__device__ __forceinline__ bool dispatch_later_q(int v, char* buf, const QArgs& a, const QItem& it, uint32_t tid) {
+  constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
+  if constexpr (Q > TB - CB) {
+    return false;
+  } else {
+    if (v == q_variant_later(Q, true)) {
+      run_passes_q<R, TB - Q, TB, true, 32>(buf, a, it, tid);
+      return true;
+    }
+    if (v == q_variant_later(Q, false)) {
+      run_passes_q<R, TB - Q, TB, false, 32>(buf, a, it, tid);
+      return true;
+    }
+    return dispatch_later_q<R, Q + 1>(v, buf, a, it, tid);
+  }
+}
+
+// Small instances: one thread per instance, k <= 16 in registers.
+template <class R, int S>
+__device__ __forceinline__ void small_one(const typename KT<R>::C* __restrict__ in, typename KT<R>::C* __restrict__ out,
+                                          const typename KT<R>::C* __restrict__ tw, R sc) {
+  using C = typename KT<R>::C;
+  constexpr int K = 1 << S;
+  C v[K];
+#pragma unroll
+  for (int e = 0; e < K; ++e) v[e] = in[e];
+#pragma unroll
+  for (int m1 = 0; m1 < S; ++m1) {
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+      if ((e >> m1) & 1) continue;
+      const C w = __ldg(tw + (1u << m1) + (e & ((1 << m1) - 1)));
+      if (m1 == S - 1)
+        bfly_scaled(v[e], v[e | (1 << m1)], w, sc);
+      else
+        bfly(v[e], v[e | (1 << m1)], w);
+    }
+  }
+  if constexpr (S == 0) {
+    v[0].x *= sc;
+    v[0].y *= sc;
+  }
+#pragma unroll
+  for (int e = 0; e < K; ++e) out[e] = v[e];
+}
+
+template <class R>
+__device__ __forceinline__ void run_small(const QArgs& a, const QItem& it, uint32_t tid) {
+  using C = typename KT<R>::C;
+  if (tid >= it.count) return;
+  const QInst ins = a.insts[it.inst + tid];
+  const C* in = static_cast<const C*>(a.in) + ins.off;
+  C* out = static_cast<C*>(a.out) + ins.off;
+  const C* tw = static_cast<const C*>(ins.tw);
+  const R sc = R(ins.scale);
+  switch (ins.s) {
+    case 0: small_one<R, 0>(in, out, tw, sc); break;
+    case 1: small_one<R, 1>(in, out, tw, sc); break;
+    case 2: small_one<R, 2>(in, out, tw, sc); break;
+    case 3: small_one<R, 3>(in, out, tw, sc); break;
+    default: small_one<R, 4>(in, out, tw, sc); break;
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ QParams prm) {
+  const QArgs& a = prm.a;
+  extern __shared__ char smem_raw[];
+  char* smem = align1024(smem_raw);
+  const uint32_t bar0 = ptx::smem_addr(smem + kBufs * kTileBytes);
+  const uint32_t tid = threadIdx.x;
+  {
+    const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 8 * kBufs;
+    int bad = 0;
+    if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
+    else if (reinterpret_cast<uintptr_t>(&prm.maps[0]) & 63u) bad = kBadMap;
+    if (bad) {
+      if (tid == 0) atomicCAS(a.status, 0, bad);
+      return;
+    }
+  }
+  const uint64_t G = gridDim.x;
+  const uint64_t c = blockIdx.x;
+  if (c >= a.n_items) return;
+  const uint64_t n = (a.n_items - c + G - 1) / G;   // items c, c+G, ... below n_items
+  auto item_at = [&](uint64_t j) -> const QItem& { return a.items[c + j * G]; };
+  auto is_tma = [&](const QItem& it) { return it.variant != kVSmall && it.variant != kVNop; };
+
+  bool failed = false;            // thread 0 only: a dependency wait expired
+  uint32_t inflight = 0;          // thread 0 only: buffers with an issued, unconsumed load
+  auto issue_load = [&](uint64_t j) {
+    const QItem& it = item_at(j);
+    if (!is_tma(it)) return;
+    if (it.dep != kNone) {
+      const uint32_t* ctr = a.counters + it.dep;
+      const uint32_t need = it.need + a.need_bias;
+      if (ptx::ld_acquire_gpu(ctr) < need) {
+        const uint64_t t0 = ptx::globaltimer();
+        while (ptx::ld_acquire_gpu(ctr) < need) {
+          if (ptx::globaltimer() - t0 > a.timeout_ns) {
+            failed = true;
+            break;
+          }
+        }
+      }
+      ptx::fence_proxy_async_global();
+    }
+    const uint32_t b = uint32_t(j % kBufs);
+    const uint32_t bar = bar0 + 8 * b;
+    const bool first_level = it.variant < 16;
+    const uint32_t bytes = first_level ? (128u << (it.map / 2)) : kTileBytes;
+    ptx::mbar_arrive_expect_tx(bar, bytes);
+    ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], bar, 0, it.c1, 0, it.c3);
+    inflight |= 1u << b;
+  };
+
+  if (tid == 0) {
+    for (int b = 0; b < kBufs; ++b) ptx::mbar_init(bar0 + 8 * b, 1);
+    ptx::fence_mbar_init();
+    for (uint64_t j = 0; j < n && j < uint64_t(kBufs); ++j) issue_load(j);
+  }
+  __syncthreads();
+  uint32_t phases = 0;            // bit b: parity of the next completion of buffer b
+  uint32_t pending_sig = kNone;   // thread 0: counter of the last stored item not yet signalled
+  bool aborted = false;
+  uint64_t j = 0;
+  for (; j < n; ++j) {
+    const QItem it = item_at(j);
+    const uint32_t b = uint32_t(j % kBufs);
+    char* buf = smem + b * kTileBytes;
+    bool ok = true;
+    if (is_tma(it)) {
+      ok = ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, a.timeout_ns);
+      if (ok) {
+        phases ^= 1u << b;
+        if (tid == 0) inflight &= ~(1u << b);
+      }
+    }
+    if (__syncthreads_or(!ok || (tid == 0 && failed))) {
+      aborted = true;
+      break;
+    }
+    const int v = it.variant;
+    if (v == kVNop) {
+      // nothing to do
+    } else if (v == kVSmall) {
+      run_small<R>(a, it, tid);
+    } else if (v == kVFirstChunk) {
+      run_passes_q<R, 0, KT<R>::TB, false, KT<R>::TB>(buf, a, it, tid);
+    } else if (v < 16) {
+      dispatch_first_q<R>(v, buf, a, it, tid);
+    } else {
+      dispatch_later_q<R>(v, buf, a, it, tid);
+    }
+    if (tid == 0) {
+      bool stored = false;
+      if (is_tma(it)) {
+        const uint32_t slot = (v < 16) ? uint32_t(it.map) + 1u : uint32_t(it.map);
+        ptx::tma_store_4d(&prm.maps[slot], ptx::smem_addr(buf), 0, it.c1, 0, it.c3);
+        ptx::bulk_commit();
+        stored = true;
+      }
+      if (stored) ptx::bulk_wait<1>(); else ptx::bulk_wait<0>();
+      if (pending_sig != kNone) {           // the previous store is complete: publish it
+        ptx::fence_proxy_async_global();
+        ptx::red_add_release_gpu(a.counters + pending_sig, 1u);
+      }
+      pending_sig = stored ? it.sig : kNone;
+      if (j >= 1 && j + 2 < n) issue_load(j + 2);   // into the buffer of item j-1, drained above
+    }
+  }
+  if (tid == 0) {
+    if (aborted || failed) {
+      // Let loads already issued land before the CTA's shared memory is released.
+      for (int b = 0; b < kBufs; ++b)
+        if (inflight >> b & 1u) ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, a.timeout_ns);
+      atomicExch(a.status, int(SDFT_ERR_TIMEOUT));
+    }
+    ptx::bulk_wait<0>();
+    if (!aborted && pending_sig != kNone) {
+      ptx::fence_proxy_async_global();
+      ptx::red_add_release_gpu(a.counters + pending_sig, 1u);
+    }
+  }
+}
+
+}  // namespace sdft
+
+namespace sdft {
+
+// Host launchers (queue_f32.cu, queue_f64.cu).
+sdft_status launch_queue_f32(const QParams& prm, int grid, cudaStream_t st);
+sdft_status launch_queue_f64(const QParams& prm, int grid, cudaStream_t st);
+// Co-resident CTAs of the queue kernel on the current device (occupancy x SMs).
+int queue_grid_f32();
+int queue_grid_f64();
+
+template <class R>
+int queue_grid() {
+  auto fn = k_queue<R>;
+  if (ensure_smem(reinterpret_cast<const void*>(fn), int(kLevelSmem)) != SDFT_OK) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, KT<R>::NT, kLevelSmem) != cudaSuccess) return 0;
+  return per_sm * sm_count();
+}
+
+template <class R>
+sdft_status launch_queue(const QParams& prm, int grid, cudaStream_t st) {
+  auto fn = k_queue<R>;
+  sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(kLevelSmem));
+  if (s != SDFT_OK) return s;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(KT<R>::NT);
+  cfg.dynamicSmemBytes = kLevelSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs resident: dependency waits make progress
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, fn, prm);
+  return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
+}
+
+}  // namespace sdft

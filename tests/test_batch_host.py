@@ -1,0 +1,50 @@
+"""CPU checks of the uneven-batch planner (host-only plans; no GPU)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def _plans(instances, prec="c64"):
+    from paper_2211_15299_gb300 import Plan
+    return [Plan(i.M, i.J, prec, host_only=True) for i in instances]
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_packing_and_item_invariants(prec):
+    from paper_2211_15299_gb300 import Batch
+    insts = W.workload_uneven(count=400, salt=3)
+    plans = _plans(insts, prec)
+    b = Batch(plans)
+    ks = np.array([p.k for p in plans])
+    assert b.total == int(ks.sum())
+    # every instance starts at a multiple of its own k, and the ranges tile [0, total)
+    assert all(int(o) % int(k) == 0 for o, k in zip(b.offsets, ks))
+    spans = sorted((int(o), int(o) + int(k)) for o, k in zip(b.offsets, ks))
+    assert spans[0][0] == 0 and spans[-1][1] == b.total
+    assert all(a[1] == c[0] for a, c in zip(spans, spans[1:]))
+    n_items, n_ctr, grid = b.stats()          # raises if the dependency invariants fail
+    multi = sum(1 for p in plans if p.s > (12 if prec == "c64" else 11))
+    assert n_ctr >= multi and grid == 304 and n_items > 0
+
+
+def test_large_instances_three_levels():
+    from paper_2211_15299_gb300 import Batch
+    rng = W.rng_for(4, 77)
+    insts = []
+    for s in (22, 21, 20, 14, 13, 5, 4, 0):
+        M = s + 4
+        piv = W.random_pivots(M, s, rng)
+        insts.append(W.Instance(M, piv, W.homogeneous_support(M, piv, rng)))
+    b = Batch(_plans(insts))
+    n_items, n_ctr, grid = b.stats()
+    # s = 21, 22 have three levels (two counters each), s = 20, 14, 13 two levels
+    assert n_ctr == 2 + 2 + 1 + 1 + 1
+
+
+def test_host_only_batch_cannot_execute():
+    from paper_2211_15299_gb300 import Batch, SdftError, _native as N
+    b = Batch(_plans(W.workload_uneven(count=5, salt=9)))
+    with pytest.raises(SdftError) as ei:
+        N.sdft_batch_execute(b.handle, 16, 16, None)
+    assert ei.value.name == "SDFT_ERR_NO_DEVICE"

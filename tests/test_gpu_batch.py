@@ -1,0 +1,155 @@
+"""GPU parity of the uneven-batch work-queue kernel against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-12}
+
+
+def _torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def _instances(rng, sizes, M_extra=(0, 8)):
+    out = []
+    for s in sizes:
+        M = max(s, 1) + int(rng.integers(M_extra[0], M_extra[1] + 1))
+        piv = W.random_pivots(M, s, rng)
+        out.append(W.Instance(M, piv, W.homogeneous_support(M, piv, rng)))
+    return out
+
+
+def _run_batch(insts, prec, rng, batch=None):
+    torch = _torch()
+    from paper_2211_15299_gb300 import Batch, Plan
+    plans = [Plan(i.M, i.J, prec) for i in insts]
+    b = Batch(plans) if batch is None else batch
+    Jcs, Cs, Fs = [], [], []
+    for i in insts:
+        Jc = O.canonical_support_by_key(i.J, i.pivots)
+        C = W.complex_gaussian(i.k, rng)
+        Jcs.append(Jc)
+        Cs.append(C)
+        Fs.append(O.synthesize_levels(i.M, i.pivots, Jc, C))
+    np_dt = np.complex64 if prec == 0 else np.complex128
+    flat = b.pack(Fs).astype(np_dt)
+    x = torch.from_numpy(flat).cuda()
+    y = b.execute(x)
+    torch.cuda.synchronize()
+    st = b.device_status()
+    got = b.unpack(y.cpu().numpy().astype(np.complex128))
+    f_in = b.unpack(flat.astype(np.complex128))
+    return b, plans, st, got, f_in, Jcs, Cs
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_uneven_batch_all_paths(prec):
+    rng = np.random.default_rng(900 + prec)
+    tb = 12 if prec == 0 else 11
+    # small (s <= 4), whole-instance tiles with partial groups, one- and two-level large
+    sizes = [0, 1, 2, 3, 4, 4, 5, 5, 5, 6, 7, 8, 8, 9, 10, 11, tb, tb, tb + 1, tb + 2, tb + 4]
+    sizes += list(rng.integers(0, tb + 3, size=40))
+    insts = _instances(rng, [int(s) for s in rng.permutation(sizes)])
+    b, plans, st, got, f_in, Jcs, Cs = _run_batch(insts, prec, rng)
+    assert st == 0
+    for i, inst in enumerate(insts):
+        ref = O.transform_levels(inst.M, inst.pivots, Jcs[i], f_in[i])
+        assert rel_l2(got[i], ref) < TOL[prec], (i, inst.s)
+
+
+def test_uneven_workload_reduced():
+    """The uneven workload's recipe at 400 instances (M in 12..24, s in 4..16)."""
+    rng = np.random.default_rng(4040)
+    insts = W.workload_uneven(count=400, salt=11)
+    b, plans, st, got, f_in, Jcs, Cs = _run_batch(insts, 0, rng)
+    assert st == 0
+    n_items, n_ctr, grid = b.stats()
+    assert n_ctr > 0
+    worst = max(rel_l2(got[i], Cs[i]) for i in range(len(insts)))
+    assert worst < 1e-5
+    for i in range(0, len(insts), 37):
+        ref = O.transform_levels(insts[i].M, insts[i].pivots, Jcs[i], f_in[i])
+        assert rel_l2(got[i], ref) < 1e-5
+
+
+def test_three_level_instances_in_batch():
+    rng = np.random.default_rng(4141)
+    insts = _instances(rng, [21, 13, 20, 6, 0, 21])
+    b, plans, st, got, f_in, Jcs, Cs = _run_batch(insts, 0, rng)
+    assert st == 0
+    for i, inst in enumerate(insts):
+        assert rel_l2(got[i], Cs[i]) < 1e-5, inst.s
+
+
+def test_batch_equals_strided():
+    torch = _torch()
+    from paper_2211_15299_gb300 import Batch, Plan
+    rng = np.random.default_rng(4242)
+    inst, _ = W.workload_shared(M=22, s=14, batch=1, coeffs=False, salt=5)
+    plan = Plan(inst.M, inst.J, 0)
+    B = 12
+    x = torch.randn((B, inst.k), dtype=torch.complex64, device="cuda")
+    ref = plan.execute_strided(x)
+    b = Batch([plan] * B)
+    xb = torch.empty(b.total, dtype=torch.complex64, device="cuda")
+    for i in range(B):
+        xb[b.offsets[i]:b.offsets[i] + inst.k] = x[i]
+    yb = b.execute(xb)
+    torch.cuda.synchronize()
+    for i in range(B):
+        got = yb[b.offsets[i]:b.offsets[i] + inst.k]
+        assert float(torch.linalg.vector_norm(got - ref[i]) / torch.linalg.vector_norm(ref[i])) < 1e-6
+
+
+def test_batch_graph_capture_replay():
+    torch = _torch()
+    from paper_2211_15299_gb300 import Batch, Plan
+    rng = np.random.default_rng(4343)
+    insts = _instances(rng, [14, 9, 3, 12, 16])
+    plans = [Plan(i.M, i.J, 0) for i in insts]
+    b = Batch(plans)
+    x = torch.randn(b.total, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    ref = b.execute(x).clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.execute(x, y, stream=s.cuda_stream)
+    for _ in range(3):
+        y.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref)
+    assert b.device_status() == 0
+
+
+def test_dependency_wait_times_out_and_recovers():
+    """A dependency target that is never reached ends the launch with
+    SDFT_ERR_TIMEOUT in the status word; the context stays usable."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Batch, Plan
+    rng = np.random.default_rng(4444)
+    insts = _instances(rng, [14, 13])
+    plans = [Plan(i.M, i.J, 0) for i in insts]
+    b = Batch(plans)
+    x = torch.randn(b.total, dtype=torch.complex64, device="cuda")
+    b.set_wait(timeout_ns=20_000_000, need_bias=1)
+    b.execute(x)
+    torch.cuda.synchronize()
+    assert b.device_status(clear=True) == 9          # SDFT_ERR_TIMEOUT
+    b.set_wait(0, 0)
+    y = b.execute(x)
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    for i, p in enumerate(plans):
+        ref = p.execute_strided(x[b.offsets[i]:b.offsets[i] + p.k].clone())
+        got = y[b.offsets[i]:b.offsets[i] + p.k]
+        assert float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref)) < 1e-6
