@@ -287,6 +287,49 @@ def _committed_traffic(M, s, batch):
     return None
 
 
+def time_graph(fn, steps, warmup, flush, stream):
+    """Capture `fn` in a CUDA graph and time replays (events on `stream`, L2 flushed between)."""
+    import torch
+    fn()                                    # first call builds any cached work queue
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            fn(s)
+    torch.cuda.synchronize()
+    return time_device_steps(lambda: g.replay(), steps, warmup, flush, stream)
+
+
+def run_large(args):
+    """Large-k leg: N = 2^30, k = 2^20, batch 64, complex64, contiguous and spread pivots."""
+    import torch
+    from paper_2211_15299_gb300 import Plan
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for contiguous in (True, False):
+        inst, _ = W.workload_large(contiguous=contiguous, batch=1, coeffs=False)
+        plan = Plan(inst.M, inst.J, "c64")
+        g = torch.Generator(device=dev)
+        g.manual_seed(W.BASE_SEED + 3)
+        x = torch.randn((args.large_batch, inst.k), dtype=torch.complex64, device=dev, generator=g)
+        y = torch.empty_like(x)
+
+        def step(s=None):
+            plan.execute_strided(x, y, stream=(s or stream).cuda_stream)
+
+        t = time_graph(step, args.steps, args.warmup, flush, stream)
+        coeffs = args.large_batch * inst.k
+        mean = statistics.mean(t)
+        res["contiguous" if contiguous else "spread"] = {
+            "coeffs_per_s": coeffs / mean, "ms_per_step": 1e3 * mean,
+            "alg_GBps": 16 * coeffs / mean / 1e9, "pivots": [int(p) for p in inst.pivots]}
+    return res
+
+
 def cpu_baseline(inst, x32, y32, sample):
     """The FP64 oracle's dense solve on `sample` instances of the same input."""
     import oracle as O
@@ -356,11 +399,15 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only-fp32", action="store_true", help="time the complex64 leg only (profiling)")
+    ap.add_argument("--large", action="store_true", help="time only the large-k leg (N=2^30, k=2^20)")
+    ap.add_argument("--large-batch", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.large:
+        print(json.dumps({"large_k": run_large(args)}), flush=True)
     else:
         run_ours(args)
 

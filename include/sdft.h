@@ -131,6 +131,28 @@ sdft_status sdft_execute(sdft_plan plan, const void* d_samples, void* d_coeffs, 
 sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_samples,
                                  void* d_coeffs, void* stream);
 
+/* Execution strategy of a multi-level plan (k > 2^12 for complex64, 2^11 for
+ * complex128) in sdft_execute / sdft_execute_strided:
+ *   SDFT_STRATEGY_LEVELS: one persistent launch per butterfly level (default);
+ *   SDFT_STRATEGY_QUEUE : one persistent launch over a work queue whose
+ *     later-level tiles follow their instance's previous level, so the
+ *     intermediate is read back from L2; the first call with a given batch size
+ *     builds and caches the queue (allocates: make that call before capturing
+ *     a CUDA graph). Single-level plans ignore the strategy. */
+typedef enum { SDFT_STRATEGY_LEVELS = 1, SDFT_STRATEGY_QUEUE = 2 } sdft_strategy;
+sdft_status sdft_plan_set_strategy(sdft_plan plan, sdft_strategy strategy);
+
+/*
+ * sdft_plan_autotune - time both strategies on `batch` instances in the given
+ * buffers (each run `reps` times after one warm-up, CUDA events on `stream`),
+ * keep the faster one for the plan and report the mean times in milliseconds
+ * (any output pointer may be NULL). Synchronises `stream`. The buffers are
+ * overwritten. Single-level plans report SDFT_STRATEGY_LEVELS and time it only.
+ */
+sdft_status sdft_plan_autotune(sdft_plan plan, uint64_t batch, const void* d_samples, void* d_coeffs,
+                               void* stream, int reps, sdft_strategy* chosen, float* ms_levels,
+                               float* ms_queue);
+
 /* Device status word of a plan: SDFT_OK, SDFT_ERR_TIMEOUT, or a launch
  * self-check code above 0xff (0x101: dynamic shared memory smaller than the
  * kernel's layout; 0x102: tensor-map parameter not 64-byte aligned; 0x103:

@@ -29,6 +29,7 @@ P_u64 = ctypes.POINTER(ctypes.c_uint64)
 P_f64 = ctypes.POINTER(ctypes.c_double)
 
 SDFT_C64, SDFT_C128 = 0, 1
+SDFT_STRATEGY_LEVELS, SDFT_STRATEGY_QUEUE = 1, 2
 SDFT_PLAN_HOST_ONLY = 0x1
 
 STATUS = {
@@ -50,6 +51,9 @@ SIGNATURES = {
     "sdft_plan_device_bytes": (c_int, [c_vp, P_u64]),
     "sdft_execute": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "sdft_execute_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
+    "sdft_plan_set_strategy": (c_int, [c_vp, c_int]),
+    "sdft_plan_autotune": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_int, ctypes.POINTER(c_int),
+                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "sdft_plan_device_status": (c_int, [c_vp, c_int]),
     "sdft_plan_destroy": (c_int, [c_vp]),
     "sdft_batch_create": (c_int, [ctypes.POINTER(c_vp), c_u64, ctypes.POINTER(c_vp)]),
@@ -165,6 +169,18 @@ def sdft_execute(plan: int, d_samples, d_coeffs, stream=None) -> None:
 def sdft_execute_strided(plan: int, batch: int, d_samples, d_coeffs, stream=None) -> None:
     _check(_lib.sdft_execute_strided(plan, int(batch), _ptr(d_samples), _ptr(d_coeffs), _stream(stream)),
            "sdft_execute_strided")
+
+
+def sdft_plan_set_strategy(plan: int, strategy: int) -> None:
+    _check(_lib.sdft_plan_set_strategy(plan, int(strategy)), "sdft_plan_set_strategy")
+
+
+def sdft_plan_autotune(plan: int, batch: int, d_samples, d_coeffs, stream=None, reps: int = 5):
+    """Returns (chosen strategy, ms per call with per-level launches, ms with the work queue)."""
+    ch, a, b = c_int(), ctypes.c_float(), ctypes.c_float()
+    _check(_lib.sdft_plan_autotune(plan, int(batch), _ptr(d_samples), _ptr(d_coeffs), _stream(stream), int(reps),
+                                   ctypes.byref(ch), ctypes.byref(a), ctypes.byref(b)), "sdft_plan_autotune")
+    return int(ch.value), float(a.value), float(b.value)
 
 
 def sdft_plan_device_status(plan: int, clear: bool = False) -> int:

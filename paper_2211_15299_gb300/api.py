@@ -102,6 +102,20 @@ class Plan:
         N.sdft_execute_strided(self.handle, batch, samples, coeffs, _current_stream(stream))
         return coeffs
 
+    def set_strategy(self, strategy: str):
+        """'levels' (one launch per butterfly level) or 'queue' (one work-queue launch)."""
+        N.sdft_plan_set_strategy(self.handle, {"levels": N.SDFT_STRATEGY_LEVELS, "queue": N.SDFT_STRATEGY_QUEUE}[strategy])
+
+    def autotune(self, samples, coeffs=None, stream=None, reps: int = 5):
+        """Time both strategies on these buffers, keep the faster; returns
+        (strategy name, ms levels, ms queue)."""
+        batch = samples.numel() // self.k
+        _check_tensor(samples, self.dtype, batch * self.k, "samples")
+        if coeffs is None:
+            coeffs = _torch().empty_like(samples)
+        ch, a, b = N.sdft_plan_autotune(self.handle, batch, samples, coeffs, _current_stream(stream), reps)
+        return ("levels" if ch == N.SDFT_STRATEGY_LEVELS else "queue"), a, b
+
     def device_status(self, clear: bool = False) -> int:
         return N.sdft_plan_device_status(self.handle, clear)
 

@@ -77,6 +77,9 @@ def build(verbose: bool = False, force: bool = False, xptxas: bool = False) -> s
         tag = _digest([src] + headers, flags)
         obj = os.path.join(BUILD, f"{name}.{tag}.o")
         objs.append(obj)
+        for old in os.listdir(BUILD):          # drop objects of older versions of this source
+            if old.startswith(name + ".") and old.endswith(".o") and os.path.join(BUILD, old) != obj:
+                os.remove(os.path.join(BUILD, old))
         if force or not os.path.exists(obj):
             jobs.append((src, obj))
     if jobs:

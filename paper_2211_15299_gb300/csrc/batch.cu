@@ -16,6 +16,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -50,6 +51,7 @@ struct Batch {
   int grid = 0;
   uint64_t timeout_ns = 0;           // 0: library default
   uint32_t need_bias = 0;            // diagnostics: added to every dependency target
+  int* d_status_shared = nullptr;    // if set, report into this word instead of d_status
 };
 
 }  // namespace sdft
@@ -358,7 +360,7 @@ static sdft_status run_batch(Batch& B, const void* in, void* out, cudaStream_t s
   prm.a.counters = B.d_counters;
   prm.a.in = in;
   prm.a.out = out;
-  prm.a.status = B.d_status;
+  prm.a.status = B.d_status_shared ? B.d_status_shared : B.d_status;
   prm.a.timeout_ns = B.timeout_ns ? B.timeout_ns : wait_timeout_ns();
   prm.a.need_bias = B.need_bias;
   if (B.n_counters) {
@@ -367,6 +369,70 @@ static sdft_status run_batch(Batch& B, const void* in, void* out, cudaStream_t s
   }
   const int grid = int(std::min<uint64_t>(uint64_t(B.grid), B.items.size()));
   return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, st) : launch_queue_f64(prm, grid, st);
+}
+
+// Cached queues of strided multi-level execution, keyed by batch size.
+struct StridedQueues {
+  std::mutex mu;
+  std::vector<std::pair<uint64_t, Batch*>> entries;   // most recent last
+};
+constexpr size_t kStridedQueueCache = 4;
+
+sdft_status run_strided_queue(sdft_plan_s* plan, uint64_t batch, const void* in, void* out, cudaStream_t st) {
+  Plan& p = plan->p;
+  if (batch > 0xffffffffull) return SDFT_ERR_UNSUPPORTED;
+  {
+    static std::mutex create_mu;
+    std::lock_guard<std::mutex> lk(create_mu);
+    if (!p.queues) p.queues = new (std::nothrow) StridedQueues();
+    if (!p.queues) return SDFT_ERR_NOMEM;
+  }
+  StridedQueues* q = static_cast<StridedQueues*>(p.queues);
+  Batch* b = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(q->mu);
+    for (auto& e : q->entries)
+      if (e.first == batch) b = e.second;
+    if (!b) {
+      b = new (std::nothrow) Batch();
+      if (!b) return SDFT_ERR_NOMEM;
+      b->device = p.device;
+      sdft_status s;
+      try {
+        std::vector<sdft_plan> plans(batch, plan);
+        s = build_batch(*b, plans.data(), batch);
+      } catch (const std::bad_alloc&) {
+        s = SDFT_ERR_NOMEM;
+      }
+      if (s != SDFT_OK) {
+        free_batch(*b);
+        delete b;
+        return s;
+      }
+      b->d_status_shared = p.d_status;     // report into the plan's status word
+      if (q->entries.size() >= kStridedQueueCache) {
+        // The oldest queue may still be in use by work in flight: synchronise first.
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e);
+        free_batch(*q->entries.front().second);
+        delete q->entries.front().second;
+        q->entries.erase(q->entries.begin());
+      }
+      q->entries.push_back({batch, b});
+    }
+  }
+  return run_batch(*b, in, out, st);
+}
+
+void free_strided_queues(Plan& p) {
+  if (!p.queues) return;
+  StridedQueues* q = static_cast<StridedQueues*>(p.queues);
+  for (auto& e : q->entries) {
+    free_batch(*e.second);
+    delete e.second;
+  }
+  delete q;
+  p.queues = nullptr;
 }
 
 }  // namespace sdft

@@ -31,4 +31,10 @@ uint64_t wait_timeout_ns();
 sdft_status launch_plan_f32(const Plan& plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
 sdft_status launch_plan_f64(const Plan& plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
 
+// Strided execution of a multi-level plan through the work-queue kernel, with
+// the queue for this batch size built on first use and cached in the plan.
+sdft_status run_strided_queue(sdft_plan_s* plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
+// Release the cached queues of a plan.
+void free_strided_queues(Plan& p);
+
 }  // namespace sdft

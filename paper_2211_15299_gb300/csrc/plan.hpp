@@ -58,6 +58,8 @@ struct Plan {
   int* d_status = nullptr;        // device status word
   uint64_t device_bytes = 0;
   double tw0[32] = {0};           // level-0 table entries 1..15 (rounded to prec), for kernel params
+  void* queues = nullptr;         // cached work queues of strided multi-level execution (batch.cu)
+  int strategy = SDFT_STRATEGY_LEVELS;
 };
 
 // Host-side planning (plan.cpp). Fills everything except the device fields.

@@ -156,24 +156,6 @@ __device__ __forceinline__ bool dispatch_first_q(int v, char* buf, const QArgs& 
   }
 }
 
-template <class R, int Q = 1>
-__device__ __forceinline__ bool dispatch_later_q(int v, char* buf, const QArgs& a, const QItem& it, uint32_t tid) {
-  constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
-  if constexpr (Q > TB - CB) {
-    return false;
-  } else {
-    if (v == q_variant_later(Q, true)) {
-      run_passes_q<R, TB - Q, TB, true, 32>(buf, a, it, tid);
-      return true;
-    }
-    if (v == q_variant_later(Q, false)) {
-      run_passes_q<R, TB - Q, TB, false, 32>(buf, a, it, tid);
-      return true;
-    }
-    return dispatch_later_q<R, Q + 1>(v, buf, a, it, tid);
-  }
-}
-
 // Small instances: one thread per instance, k <= 16 in registers.
 template <class R, int S>
 __device__ __forceinline__ void small_one(const typename KT<R>::C* __restrict__ in, typename KT<R>::C* __restrict__ out,
@@ -221,6 +203,143 @@ __device__ __forceinline__ void run_small(const QArgs& a, const QItem& it, uint3
   }
 }
 
+// Per-CTA pipeline of the queue kernel (3 tile buffers, round-robin items).
+template <class R>
+struct QPipe {
+  const QParams& prm;
+  char* smem;
+  uint32_t bar0, tid;
+  uint64_t c, G, n;
+  uint32_t phases = 0;        // bit b: parity of the next completion of buffer b
+  uint32_t inflight = 0;      // thread 0: buffers with an issued, unconsumed load
+  uint32_t pending_sig = kNone;
+  bool failed = false;        // thread 0: a dependency wait expired
+  bool aborted = false;
+
+  __device__ __forceinline__ QPipe(const QParams& p, char* sm, uint32_t b0, uint32_t t)
+      : prm(p), smem(sm), bar0(b0), tid(t), c(blockIdx.x), G(gridDim.x) {
+    n = (p.a.n_items > c) ? (p.a.n_items - c + G - 1) / G : 0;
+  }
+  __device__ __forceinline__ const QItem& item(uint64_t j) const { return prm.a.items[c + j * G]; }
+  __device__ __forceinline__ static bool is_tma(const QItem& it) { return it.variant != kVSmall && it.variant != kVNop; }
+
+  __device__ __forceinline__ void issue_load(uint64_t j) {   // thread 0
+    const QItem& it = item(j);
+    if (!is_tma(it)) return;
+    if (it.dep != kNone) {
+      const uint32_t* ctr = prm.a.counters + it.dep;
+      const uint32_t need = it.need + prm.a.need_bias;
+      if (ptx::ld_acquire_gpu(ctr) < need) {
+        const uint64_t t0 = ptx::globaltimer();
+        while (ptx::ld_acquire_gpu(ctr) < need) {
+          if (ptx::globaltimer() - t0 > prm.a.timeout_ns) {
+            failed = true;
+            break;
+          }
+        }
+      }
+      ptx::fence_proxy_async_global();
+    }
+    const uint32_t b = uint32_t(j % kBufs);
+    const uint32_t bar = bar0 + 8 * b;
+    const uint32_t bytes = (it.variant < 16) ? (128u << (it.map / 2)) : kTileBytes;
+    ptx::mbar_arrive_expect_tx(bar, bytes);
+    ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], bar, 0, it.c1, 0, it.c3);
+    inflight |= 1u << b;
+  }
+
+  // Wait for item j's tile; false if the CTA must stop.
+  __device__ __forceinline__ bool begin(uint64_t j, const QItem& it) {
+    const uint32_t b = uint32_t(j % kBufs);
+    bool ok = true;
+    if (is_tma(it)) {
+      ok = ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, prm.a.timeout_ns);
+      if (ok) {
+        phases ^= 1u << b;
+        if (tid == 0) inflight &= ~(1u << b);
+      }
+    }
+    if (__syncthreads_or(!ok || (tid == 0 && failed))) {
+      aborted = true;
+      return false;
+    }
+    return true;
+  }
+
+  // After item j's compute: store, publish the previous store, prefetch j + 2.
+  __device__ __forceinline__ void end(uint64_t j, const QItem& it) {
+    if (tid != 0) return;
+    bool stored = false;
+    if (is_tma(it)) {
+      const uint32_t slot = (it.variant < 16) ? uint32_t(it.map) + 1u : uint32_t(it.map);
+      ptx::tma_store_4d(&prm.maps[slot], ptx::smem_addr(smem + (j % kBufs) * kTileBytes), 0, it.c1, 0, it.c3);
+      ptx::bulk_commit();
+      stored = true;
+    }
+    if (stored) ptx::bulk_wait<1>(); else ptx::bulk_wait<0>();
+    if (pending_sig != kNone) {          // the previous store is complete: publish it
+      ptx::fence_proxy_async_global();
+      ptx::red_add_release_gpu(prm.a.counters + pending_sig, 1u);
+    }
+    pending_sig = stored ? it.sig : kNone;
+    if (j >= 1 && j + 2 < n) issue_load(j + 2);   // into the buffer of item j-1, drained above
+  }
+
+  __device__ __forceinline__ void finish() {
+    if (tid != 0) return;
+    if (aborted || failed) {
+      // Let loads already issued land before the CTA's shared memory is released.
+      for (int b = 0; b < kBufs; ++b)
+        if (inflight >> b & 1u) ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, prm.a.timeout_ns);
+      atomicExch(prm.a.status, int(SDFT_ERR_TIMEOUT));
+    }
+    ptx::bulk_wait<0>();
+    if (!aborted && pending_sig != kNone) {
+      ptx::fence_proxy_async_global();
+      ptx::red_add_release_gpu(prm.a.counters + pending_sig, 1u);
+    }
+  }
+};
+
+// Consecutive items of one single-table variant: the top pass's twiddles stay
+// in registers while the table does not change. Returns the next item index.
+template <class R, int PLO, int PHI, bool LAST>
+__device__ __noinline__ uint64_t loop_single(QPipe<R>& q, uint64_t j, int v) {
+  using C = typename KT<R>::C;
+  constexpr int NREG = reg_twiddles(KT<R>::TB, PLO, PHI);
+  C wreg[NREG > 0 ? NREG : 1];
+  const C* cache = nullptr;
+  const QArgs& a = q.prm.a;
+  for (; j < q.n; ++j) {
+    const QItem it = q.item(j);
+    if (it.variant != v) break;
+    if (!q.begin(j, it)) break;
+    const bool first = v < 16;
+    const C* tab = first ? static_cast<const C*>(a.insts[it.inst].tw) : static_cast<const C*>(it.tw);
+    const R sc = first ? R(a.insts[it.inst].scale) : R(it.scale);
+    if (tab != cache) {
+      load_reg_twiddles<R, PLO, PHI>(tab, q.tid, wreg);
+      cache = tab;
+    }
+    // pass 0 reads entry 2^m1 + u as w0[2^m1 - 1 + u]: w0 = tab + 1
+    run_passes<R, PLO, PHI, LAST>(q.smem + (j % kBufs) * kTileBytes, wreg, tab + 1, tab, q.tid, sc);
+    q.end(j, it);
+  }
+  return j;
+}
+
+template <class R, int Q = 1>
+__device__ __forceinline__ uint64_t dispatch_later_loop(QPipe<R>& q, uint64_t j, int v) {
+  constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
+  if constexpr (Q > TB - CB) {
+    return j + 1;   // unknown variant: skip (cannot happen for host-built lists)
+  } else {
+    if (v == q_variant_later(Q, true)) return loop_single<R, TB - Q, TB, true>(q, j, v);
+    if (v == q_variant_later(Q, false)) return loop_single<R, TB - Q, TB, false>(q, j, v);
+    return dispatch_later_loop<R, Q + 1>(q, j, v);
+  }
+}
+
 template <class R>
 __global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ QParams prm) {
   const QArgs& a = prm.a;
@@ -238,109 +357,34 @@ __global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ 
       return;
     }
   }
-  const uint64_t G = gridDim.x;
-  const uint64_t c = blockIdx.x;
-  if (c >= a.n_items) return;
-  const uint64_t n = (a.n_items - c + G - 1) / G;   // items c, c+G, ... below n_items
-  auto item_at = [&](uint64_t j) -> const QItem& { return a.items[c + j * G]; };
-  auto is_tma = [&](const QItem& it) { return it.variant != kVSmall && it.variant != kVNop; };
-
-  bool failed = false;            // thread 0 only: a dependency wait expired
-  uint32_t inflight = 0;          // thread 0 only: buffers with an issued, unconsumed load
-  auto issue_load = [&](uint64_t j) {
-    const QItem& it = item_at(j);
-    if (!is_tma(it)) return;
-    if (it.dep != kNone) {
-      const uint32_t* ctr = a.counters + it.dep;
-      const uint32_t need = it.need + a.need_bias;
-      if (ptx::ld_acquire_gpu(ctr) < need) {
-        const uint64_t t0 = ptx::globaltimer();
-        while (ptx::ld_acquire_gpu(ctr) < need) {
-          if (ptx::globaltimer() - t0 > a.timeout_ns) {
-            failed = true;
-            break;
-          }
-        }
-      }
-      ptx::fence_proxy_async_global();
-    }
-    const uint32_t b = uint32_t(j % kBufs);
-    const uint32_t bar = bar0 + 8 * b;
-    const bool first_level = it.variant < 16;
-    const uint32_t bytes = first_level ? (128u << (it.map / 2)) : kTileBytes;
-    ptx::mbar_arrive_expect_tx(bar, bytes);
-    ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], bar, 0, it.c1, 0, it.c3);
-    inflight |= 1u << b;
-  };
-
+  QPipe<R> q(prm, smem, bar0, tid);
+  if (q.n == 0) return;
   if (tid == 0) {
     for (int b = 0; b < kBufs; ++b) ptx::mbar_init(bar0 + 8 * b, 1);
     ptx::fence_mbar_init();
-    for (uint64_t j = 0; j < n && j < uint64_t(kBufs); ++j) issue_load(j);
+    for (uint64_t j = 0; j < q.n && j < uint64_t(kBufs); ++j) q.issue_load(j);
   }
   __syncthreads();
-  uint32_t phases = 0;            // bit b: parity of the next completion of buffer b
-  uint32_t pending_sig = kNone;   // thread 0: counter of the last stored item not yet signalled
-  bool aborted = false;
+  constexpr int TB = KT<R>::TB;
   uint64_t j = 0;
-  for (; j < n; ++j) {
-    const QItem it = item_at(j);
-    const uint32_t b = uint32_t(j % kBufs);
-    char* buf = smem + b * kTileBytes;
-    bool ok = true;
-    if (is_tma(it)) {
-      ok = ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, a.timeout_ns);
-      if (ok) {
-        phases ^= 1u << b;
-        if (tid == 0) inflight &= ~(1u << b);
-      }
-    }
-    if (__syncthreads_or(!ok || (tid == 0 && failed))) {
-      aborted = true;
-      break;
-    }
+  while (j < q.n && !q.aborted) {
+    const QItem it = q.item(j);
     const int v = it.variant;
-    if (v == kVNop) {
-      // nothing to do
-    } else if (v == kVSmall) {
-      run_small<R>(a, it, tid);
-    } else if (v == kVFirstChunk) {
-      run_passes_q<R, 0, KT<R>::TB, false, KT<R>::TB>(buf, a, it, tid);
-    } else if (v < 16) {
-      dispatch_first_q<R>(v, buf, a, it, tid);
+    if (v == kVFirstChunk) {
+      j = loop_single<R, 0, TB, false>(q, j, v);
+    } else if (v == q_variant_first(TB)) {
+      j = loop_single<R, 0, TB, true>(q, j, v);
+    } else if (v >= 16 && v != kVNop) {
+      j = dispatch_later_loop<R>(q, j, v);
     } else {
-      dispatch_later_q<R>(v, buf, a, it, tid);
-    }
-    if (tid == 0) {
-      bool stored = false;
-      if (is_tma(it)) {
-        const uint32_t slot = (v < 16) ? uint32_t(it.map) + 1u : uint32_t(it.map);
-        ptx::tma_store_4d(&prm.maps[slot], ptx::smem_addr(buf), 0, it.c1, 0, it.c3);
-        ptx::bulk_commit();
-        stored = true;
-      }
-      if (stored) ptx::bulk_wait<1>(); else ptx::bulk_wait<0>();
-      if (pending_sig != kNone) {           // the previous store is complete: publish it
-        ptx::fence_proxy_async_global();
-        ptx::red_add_release_gpu(a.counters + pending_sig, 1u);
-      }
-      pending_sig = stored ? it.sig : kNone;
-      if (j >= 1 && j + 2 < n) issue_load(j + 2);   // into the buffer of item j-1, drained above
+      if (!q.begin(j, it)) break;
+      if (v == kVSmall) run_small<R>(a, it, tid);
+      else if (v != kVNop) dispatch_first_q<R>(v, smem + (j % kBufs) * kTileBytes, a, it, tid);
+      q.end(j, it);
+      ++j;
     }
   }
-  if (tid == 0) {
-    if (aborted || failed) {
-      // Let loads already issued land before the CTA's shared memory is released.
-      for (int b = 0; b < kBufs; ++b)
-        if (inflight >> b & 1u) ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, a.timeout_ns);
-      atomicExch(a.status, int(SDFT_ERR_TIMEOUT));
-    }
-    ptx::bulk_wait<0>();
-    if (!aborted && pending_sig != kNone) {
-      ptx::fence_proxy_async_global();
-      ptx::red_add_release_gpu(a.counters + pending_sig, 1u);
-    }
-  }
+  q.finish();
 }
 
 }  // namespace sdft

@@ -153,3 +153,41 @@ def test_dependency_wait_times_out_and_recovers():
         ref = p.execute_strided(x[b.offsets[i]:b.offsets[i] + p.k].clone())
         got = y[b.offsets[i]:b.offsets[i] + p.k]
         assert float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref)) < 1e-6
+
+
+@pytest.mark.parametrize("s", [14, 20, 21])
+def test_strided_queue_strategy_matches_oracle(s):
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan
+    rng = np.random.default_rng(4500 + s)
+    inst = _instances(rng, [s])[0]
+    plan = Plan(inst.M, inst.J, 0)
+    Jc = O.canonical_support_by_key(inst.J, inst.pivots)
+    B = 3
+    C = W.complex_gaussian((B, inst.k), rng)
+    F = O.synthesize_levels(inst.M, inst.pivots, Jc, C).astype(np.complex64)
+    x = torch.from_numpy(F).cuda()
+    ref = plan.execute_strided(x).clone()
+    plan.set_strategy("queue")
+    y = plan.execute_strided(x)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    got = y.cpu().numpy().astype(np.complex128)
+    assert rel_l2(got, C) < 1e-5
+    assert float(torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref)) < 1e-6
+
+
+def test_autotune_chooses_a_strategy():
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan
+    rng = np.random.default_rng(4600)
+    inst = _instances(rng, [16])[0]
+    plan = Plan(inst.M, inst.J, 0)
+    x = torch.randn((8, inst.k), dtype=torch.complex64, device="cuda")
+    name, ms_levels, ms_queue = plan.autotune(x.clone(), reps=2)
+    assert name in ("levels", "queue") and ms_levels > 0 and ms_queue > 0
+    y = plan.execute_strided(x)
+    plan.set_strategy("levels")
+    ref = plan.execute_strided(x)
+    torch.cuda.synchronize()
+    assert float(torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref)) < 1e-6
