@@ -194,6 +194,27 @@ sdft_status sdft_batch_info(sdft_batch batch, uint64_t* total, uint64_t* offsets
 sdft_status sdft_batch_execute(sdft_batch batch, const void* d_samples, void* d_coeffs,
                                void* stream);
 
+/*
+ * sdft_batch_execute_noalloc - the same work as sdft_batch_execute, for callers
+ * that must not allocate device memory while they run: for example code that
+ * works under a fixed device-memory budget handed out once at start-up, or a
+ * serving loop where a cudaMalloc could stall every stream on the device. The
+ * paper has no counterpart; this is a property of the library only.
+ * The call itself allocates nothing: the batch (created earlier) supplies its
+ * queue, and the dependency counters come from one fixed array of 65536
+ * 32-bit counters (256 KiB) built into the library, present on every device
+ * that loads it until the process exits. Batches needing more counters (more
+ * than 65536 multi-level instance levels) are rejected with
+ * SDFT_ERR_UNSUPPORTED. The first call on a device looks up that array's
+ * device address (with the device current); make that first call before any
+ * stream capture. All calls share the array and it keeps the last call's
+ * counts, so each call clears the part it uses first; calls whose work
+ * overlaps on the GPU (other streams, other threads) race on it and must be
+ * serialised by the caller. Buffers as for sdft_batch_execute.
+ */
+sdft_status sdft_batch_execute_noalloc(sdft_batch batch, const void* d_samples, void* d_coeffs,
+                                       void* stream);
+
 /* Device status word of a batch (as for plans). */
 sdft_status sdft_batch_device_status(sdft_batch batch, int clear);
 

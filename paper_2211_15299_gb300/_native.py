@@ -59,6 +59,7 @@ SIGNATURES = {
     "sdft_batch_create": (c_int, [ctypes.POINTER(c_vp), c_u64, ctypes.POINTER(c_vp)]),
     "sdft_batch_info": (c_int, [c_vp, P_u64, P_u64]),
     "sdft_batch_execute": (c_int, [c_vp, c_vp, c_vp, c_vp]),
+    "sdft_batch_execute_noalloc": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "sdft_batch_device_status": (c_int, [c_vp, c_int]),
     "sdft_batch_set_wait": (c_int, [c_vp, c_u64, c_u32]),
     "sdft_batch_stats": (c_int, [c_vp, P_u64, P_u64, ctypes.POINTER(c_int)]),
@@ -208,6 +209,11 @@ def sdft_batch_info(batch: int, n: int):
 
 def sdft_batch_execute(batch: int, d_samples, d_coeffs, stream=None) -> None:
     _check(_lib.sdft_batch_execute(batch, _ptr(d_samples), _ptr(d_coeffs), _stream(stream)), "sdft_batch_execute")
+
+
+def sdft_batch_execute_noalloc(batch: int, d_samples, d_coeffs, stream=None) -> None:
+    _check(_lib.sdft_batch_execute_noalloc(batch, _ptr(d_samples), _ptr(d_coeffs), _stream(stream)),
+           "sdft_batch_execute_noalloc")
 
 
 def sdft_batch_device_status(batch: int, clear: bool = False) -> int:

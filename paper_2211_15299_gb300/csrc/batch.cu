@@ -371,6 +371,70 @@ static sdft_status run_batch(Batch& B, const void* in, void* out, cudaStream_t s
   return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, st) : launch_queue_f64(prm, grid, st);
 }
 
+// ---- allocation-free execution ------------------------------------------------
+// Dependency counters for sdft_batch_execute_noalloc live in this fixed array
+// instead of the batch's own allocation. Every device that loads the library
+// holds it (256 KiB) until the process exits; all calls share it.
+constexpr uint64_t kNoAllocCounters = 65536;
+static __device__ __align__(256) uint32_t g_noalloc_counters[kNoAllocCounters];
+
+// Device address of the array for the current device, looked up once per
+// device (cudaGetSymbolAddress needs that device current). In host code the
+// array's name is only a host-side stand-in, so kernels get this address.
+static sdft_status noalloc_counters(uint32_t** out) {
+  static std::mutex mu;
+  static uint32_t* addr[64] = {nullptr};
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= 64) return SDFT_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_counters);
+    if (e != cudaSuccess) return cuda_fail(e);
+    addr[dev] = static_cast<uint32_t*>(p);
+  }
+  *out = addr[dev];
+  return SDFT_OK;
+}
+
+static sdft_status run_batch_noalloc(const Batch& B, const void* in, void* out, cudaStream_t st) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev != B.device) return SDFT_ERR_ARG;
+  if (!in || !out) return SDFT_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return SDFT_ERR_ARG;
+  const uint64_t bytes = B.total * uint64_t(elem_bytes(B.prec));
+  const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
+  if (a != b && a < b + bytes && b < a + bytes) return SDFT_ERR_ARG;
+  if (B.n_counters > kNoAllocCounters) return SDFT_ERR_UNSUPPORTED;
+  if (B.items.empty()) return SDFT_OK;
+  uint32_t* counters = nullptr;
+  sdft_status s = noalloc_counters(&counters);
+  if (s != SDFT_OK) return s;
+  QParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  s = encode_batch_maps(B, in, out, prm);
+  if (s != SDFT_OK) return s;
+  prm.a.items = B.d_items;
+  prm.a.n_items = B.items.size();
+  prm.a.insts = B.d_insts;
+  prm.a.counters = counters;
+  prm.a.in = in;
+  prm.a.out = out;
+  prm.a.status = B.d_status;
+  prm.a.timeout_ns = B.timeout_ns ? B.timeout_ns : wait_timeout_ns();
+  prm.a.need_bias = B.need_bias;
+  if (B.n_counters) {   // the array keeps the previous call's counts
+    e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * B.n_counters, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  const int grid = int(std::min<uint64_t>(uint64_t(B.grid), B.items.size()));
+  return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, st) : launch_queue_f64(prm, grid, st);
+}
+
 // Cached queues of strided multi-level execution, keyed by batch size.
 struct StridedQueues {
   std::mutex mu;
@@ -486,6 +550,12 @@ sdft_status sdft_batch_execute(sdft_batch batch, const void* d_samples, void* d_
   if (!batch) return SDFT_ERR_ARG;
   if (batch->b.device < 0) return SDFT_ERR_NO_DEVICE;
   return sdft::run_batch(batch->b, d_samples, d_coeffs, static_cast<cudaStream_t>(stream));
+}
+
+sdft_status sdft_batch_execute_noalloc(sdft_batch batch, const void* d_samples, void* d_coeffs, void* stream) {
+  if (!batch) return SDFT_ERR_ARG;
+  if (batch->b.device < 0) return SDFT_ERR_NO_DEVICE;
+  return sdft::run_batch_noalloc(batch->b, d_samples, d_coeffs, static_cast<cudaStream_t>(stream));
 }
 
 sdft_status sdft_batch_device_status(sdft_batch batch, int clear) {
