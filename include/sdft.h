@@ -236,6 +236,61 @@ sdft_status sdft_batch_stats(sdft_batch batch, uint64_t* n_items, uint64_t* n_co
 sdft_status sdft_batch_destroy(sdft_batch batch);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of requests under a device-memory budget     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sdft_server_s* sdft_server;
+
+typedef struct {
+  uint64_t submitted;        /* requests accepted by sdft_server_submit          */
+  uint64_t completed;        /* requests whose coefficients are in host memory   */
+  uint64_t failed;           /* requests completed with a non-zero status        */
+  uint64_t micro_batches;    /* work-queue launches                              */
+  uint64_t coeffs;           /* coefficients of the completed requests           */
+  uint64_t inflight;         /* requests admitted and not yet completed          */
+  uint64_t max_inflight;     /* largest `inflight` seen                          */
+  uint64_t arena_bytes;      /* device arena (the admission budget)              */
+  uint64_t arena_peak_bytes; /* largest arena use                                */
+} sdft_server_stats;
+
+/*
+ * sdft_server_create - a serving engine on the current device. `budget_bytes`
+ * (rounded down to a power of two) is allocated once as the arena that holds
+ * the requests' samples and coefficients; a request is admitted when a block of
+ * its size (k x element size, at least 128 bytes) is free. Up to `n_slots`
+ * micro-batches of up to `max_batch` requests run at once, each one
+ * persistent work-queue launch on its own stream, sharing the co-resident CTAs.
+ * A worker thread forms micro-batches in arrival order as slots and memory free
+ * up (continuous batching). Plans stay owned by the caller and must outlive
+ * their requests.
+ */
+sdft_status sdft_server_create(sdft_prec prec, uint64_t budget_bytes, uint32_t n_slots, uint32_t max_batch,
+                               sdft_server* out);
+
+/* Queue one request: transform k = plan's k samples at h_samples into h_coeffs
+ * (host buffers; pinned memory makes the copies asynchronous). The buffers must
+ * stay valid until the request completes. `tag` identifies it in poll. */
+sdft_status sdft_server_submit(sdft_server srv, sdft_plan plan, const void* h_samples, void* h_coeffs,
+                               uint64_t tag);
+
+/* Up to `cap` completed requests since the last poll: tag, latency in seconds
+ * (submit to the completion of the copy-out), status (SDFT_OK, or
+ * SDFT_ERR_BUDGET when a request can never fit the arena). *n_out = count. */
+sdft_status sdft_server_poll(sdft_server srv, uint64_t* tags, double* latency_s, int32_t* status, uint64_t cap,
+                             uint64_t* n_out);
+
+/* Wait until every submitted request has completed (0 = no time limit). */
+sdft_status sdft_server_drain(sdft_server srv, uint64_t timeout_ms);
+
+sdft_status sdft_server_get_stats(sdft_server srv, sdft_server_stats* stats);
+
+/* Device status word of the server's launches (as for plans). */
+sdft_status sdft_server_device_status(sdft_server srv, int clear);
+
+/* Stop accepting requests, finish the queued ones, release everything. */
+sdft_status sdft_server_destroy(sdft_server srv);
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics                                                               */
 /* ------------------------------------------------------------------------ */
 

@@ -40,6 +40,12 @@ STATUS = {
 }
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "submitted", "completed", "failed", "micro_batches", "coeffs", "inflight", "max_inflight",
+        "arena_bytes", "arena_peak_bytes")]
+
+
 # Every symbol declared in include/sdft.h: name -> (restype, argtypes)
 SIGNATURES = {
     "sdft_plan_create": (c_int, [c_u32, P_u64, c_u64, c_int, c_u32, ctypes.POINTER(c_vp)]),
@@ -64,6 +70,13 @@ SIGNATURES = {
     "sdft_batch_set_wait": (c_int, [c_vp, c_u64, c_u32]),
     "sdft_batch_stats": (c_int, [c_vp, P_u64, P_u64, ctypes.POINTER(c_int)]),
     "sdft_batch_destroy": (c_int, [c_vp]),
+    "sdft_server_create": (c_int, [c_int, c_u64, c_u32, c_u32, ctypes.POINTER(c_vp)]),
+    "sdft_server_submit": (c_int, [c_vp, c_vp, c_vp, c_vp, c_u64]),
+    "sdft_server_poll": (c_int, [c_vp, P_u64, P_f64, ctypes.POINTER(ctypes.c_int32), c_u64, P_u64]),
+    "sdft_server_drain": (c_int, [c_vp, c_u64]),
+    "sdft_server_get_stats": (c_int, [c_vp, ctypes.POINTER(ServerStats)]),
+    "sdft_server_device_status": (c_int, [c_vp, c_int]),
+    "sdft_server_destroy": (c_int, [c_vp]),
     "sdft_status_string": (ctypes.c_char_p, [c_int]),
     "sdft_last_cuda_error": (c_int, []),
     "sdft_version": (c_int, []),
@@ -232,6 +245,47 @@ def sdft_batch_stats(batch: int):
 
 def sdft_batch_destroy(batch: int) -> None:
     _check(_lib.sdft_batch_destroy(batch), "sdft_batch_destroy")
+
+
+def sdft_server_create(prec: int, budget_bytes: int, n_slots: int = 2, max_batch: int = 64) -> int:
+    out = c_vp()
+    _check(_lib.sdft_server_create(int(prec), int(budget_bytes), int(n_slots), int(max_batch), ctypes.byref(out)),
+           "sdft_server_create")
+    return int(out.value)
+
+
+def sdft_server_submit(server: int, plan: int, h_samples, h_coeffs, tag: int) -> None:
+    _check(_lib.sdft_server_submit(server, plan, _ptr(h_samples), _ptr(h_coeffs), int(tag)), "sdft_server_submit")
+
+
+def sdft_server_poll(server: int, cap: int = 4096):
+    tags = np.zeros(cap, dtype=np.uint64)
+    lat = np.zeros(cap, dtype=np.float64)
+    st = np.zeros(cap, dtype=np.int32)
+    n = c_u64()
+    _check(_lib.sdft_server_poll(server, tags.ctypes.data_as(P_u64), lat.ctypes.data_as(P_f64),
+                                 st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), cap, ctypes.byref(n)),
+           "sdft_server_poll")
+    k = int(n.value)
+    return tags[:k], lat[:k], st[:k]
+
+
+def sdft_server_drain(server: int, timeout_ms: int = 0) -> None:
+    _check(_lib.sdft_server_drain(server, int(timeout_ms)), "sdft_server_drain")
+
+
+def sdft_server_get_stats(server: int) -> dict:
+    st = ServerStats()
+    _check(_lib.sdft_server_get_stats(server, ctypes.byref(st)), "sdft_server_get_stats")
+    return {n: int(getattr(st, n)) for n, _ in ServerStats._fields_}
+
+
+def sdft_server_device_status(server: int, clear: bool = False) -> int:
+    return int(_lib.sdft_server_device_status(server, int(bool(clear))))
+
+
+def sdft_server_destroy(server: int) -> None:
+    _check(_lib.sdft_server_destroy(server), "sdft_server_destroy")
 
 
 def sdft_status_string(status: int) -> str:

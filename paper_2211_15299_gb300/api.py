@@ -185,3 +185,47 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching serving engine (sdft_server_*).
+
+    Requests carry a Plan and pinned host tensors; the engine copies samples
+    in, runs micro-batches as persistent work-queue launches on a few streams,
+    copies coefficients out and reports per-request latency."""
+
+    def __init__(self, prec="c64", budget_bytes: int = 1 << 30, n_slots: int = 2, max_batch: int = 64):
+        self.prec = _PREC[prec] if isinstance(prec, str) else int(prec)
+        self.handle = N.sdft_server_create(self.prec, budget_bytes, n_slots, max_batch)
+        self._live = {}      # tag -> (plan, h_in, h_out) kept alive until completion
+
+    def submit(self, plan: Plan, h_in, h_out, tag: int):
+        self._live[int(tag)] = (plan, h_in, h_out)
+        N.sdft_server_submit(self.handle, plan.handle, h_in, h_out, tag)
+
+    def poll(self, cap: int = 4096):
+        tags, lat, st = N.sdft_server_poll(self.handle, cap)
+        for t in tags:
+            self._live.pop(int(t), None)
+        return tags, lat, st
+
+    def drain(self, timeout_ms: int = 0):
+        N.sdft_server_drain(self.handle, timeout_ms)
+
+    def stats(self) -> dict:
+        return N.sdft_server_get_stats(self.handle)
+
+    def device_status(self, clear: bool = False) -> int:
+        return N.sdft_server_device_status(self.handle, clear)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.sdft_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

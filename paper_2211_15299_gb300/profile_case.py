@@ -21,7 +21,11 @@ def main() -> int:
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--reps", type=int, default=4)
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--uneven", type=int, default=0,
+                    help="run the uneven workload's recipe with this many instances instead")
     args = ap.parse_args()
+    if args.uneven:
+        return uneven(args)
 
     import torch
 
@@ -40,6 +44,28 @@ def main() -> int:
     torch.cuda.synchronize()
     st = plan.device_status()
     print(f"profile_case log2n={args.log2n} log2k={args.log2k} batch={args.batch} {args.prec} "
+          f"reps={args.reps} device_status={st:#x}", flush=True)
+    return 0 if st == 0 else 3
+
+
+def uneven(args) -> int:
+    import torch
+
+    import workloads as W
+    from paper_2211_15299_gb300 import Batch, Plan
+
+    insts = W.workload_uneven(count=args.uneven)
+    plans = [Plan(i.M, i.J, args.prec) for i in insts]
+    b = Batch(plans)
+    dt = torch.complex64 if args.prec == "c64" else torch.complex128
+    x = torch.randn(b.total, dtype=dt, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(args.reps):
+        b.execute(x, y)
+    torch.cuda.synchronize()
+    st = b.device_status()
+    n_items, n_ctr, grid = b.stats()
+    print(f"profile_case uneven={args.uneven} coeffs={b.total} items={n_items} counters={n_ctr} grid={grid} "
           f"reps={args.reps} device_status={st:#x}", flush=True)
     return 0 if st == 0 else 3
 

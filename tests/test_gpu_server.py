@@ -1,0 +1,94 @@
+"""GPU tests of the serving engine: continuous batching under a memory budget."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def _requests(rng, sizes):
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan
+    reqs = []
+    for s in sizes:
+        M = max(s, 1) + int(rng.integers(0, 8))
+        piv = W.random_pivots(M, s, rng)
+        J = W.homogeneous_support(M, piv, rng)
+        plan = Plan(M, J, 0)
+        Jc = O.canonical_support_by_key(J, piv)
+        c = W.complex_gaussian(1 << s, rng)
+        f = O.synthesize_levels(M, piv, Jc, c).astype(np.complex64)
+        h_in = torch.from_numpy(f).pin_memory()
+        reqs.append((plan, h_in, c, M, piv, Jc))
+    return reqs
+
+
+def _serve(srv, reqs):
+    torch = _torch()
+    outs = []
+    for i, (plan, h_in, *_rest) in enumerate(reqs):
+        h_out = torch.empty_like(h_in).pin_memory()
+        outs.append(h_out)
+        srv.submit(plan, h_in, h_out, i)
+    srv.drain(timeout_ms=60_000)
+    got = {}
+    while len(got) < len(reqs):
+        tags, lat, st = srv.poll()
+        for t, l, s_ in zip(tags, lat, st):
+            got[int(t)] = (float(l), int(s_))
+        if not len(tags):
+            break
+    return outs, got
+
+
+def test_each_result_same_alone_and_in_the_mix():
+    from paper_2211_15299_gb300 import Server
+    rng = np.random.default_rng(5150)
+    sizes = [int(s) for s in rng.permutation([0, 2, 4, 5, 7, 9, 11, 12, 12, 13, 14, 16, 3, 8, 10, 15] * 3)]
+    reqs = _requests(rng, sizes)
+    srv = Server("c64", budget_bytes=64 << 20, n_slots=2, max_batch=8)
+    alone = []
+    for i, r in enumerate(reqs):                       # one request at a time
+        out, got = _serve(srv, [r])
+        assert got[0][1] == 0
+        alone.append(out[0].clone())
+    mixed, got = _serve(srv, reqs)                      # all at once
+    st = srv.stats()
+    assert st["micro_batches"] > len(reqs) and st["max_inflight"] > 1
+    assert srv.device_status() == 0
+    for i, r in enumerate(reqs):
+        plan, h_in, c, M, piv, Jc = r
+        assert got[i][1] == 0 and got[i][0] > 0
+        x = mixed[i].numpy().astype(np.complex128)
+        assert np.array_equal(mixed[i].numpy(), alone[i].numpy()), i
+        ref = O.transform_levels(M, piv, Jc, h_in.numpy().astype(np.complex128))
+        assert rel_l2(x, ref) < 1e-5, (i, plan.s)
+    srv.close()
+
+
+def test_admission_respects_the_budget():
+    torch = _torch()
+    from paper_2211_15299_gb300 import Server
+    rng = np.random.default_rng(5151)
+    reqs = _requests(rng, [16] * 6)                     # 512 KiB each
+    srv = Server("c64", budget_bytes=1 << 20, n_slots=4, max_batch=4)   # room for two
+    outs, got = _serve(srv, reqs)
+    st = srv.stats()
+    assert st["completed"] == 6 and st["arena_peak_bytes"] <= 1 << 20
+    assert st["max_inflight"] <= 2
+    for i, r in enumerate(reqs):
+        assert rel_l2(outs[i].numpy().astype(np.complex128), r[2]) < 1e-5
+    # a request that can never fit is completed with SDFT_ERR_BUDGET
+    big = _requests(rng, [18])
+    outs, got = _serve(srv, big)
+    assert got[0][1] == 7
+    srv.close()
