@@ -252,6 +252,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         extra["uneven"] = run_uneven(args)
         extra["large_k"] = run_large(args)
+        extra["serving"] = run_serving(args)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -372,6 +373,128 @@ def run_uneven(args):
             "launches_per_step": 1}
 
 
+def run_serving(args):
+    """Serving leg: Poisson arrivals (rate, duration) of requests whose supports have
+    N in 2^10..2^26 and k in 2^4..2^18; 80% reuse one of 256 resident plans, 20% bring
+    a new support whose plan is built on arrival (by a pool of planner threads, the
+    planning time counting in the latency); samples start in pinned host memory;
+    a device-memory admission budget bounds the requests in flight."""
+    import concurrent.futures as cf
+    import threading as th
+    import torch
+    from paper_2211_15299_gb300 import Plan, Server, _native as N
+    rng = W.rng_for(5, 9)
+    trace = W.workload_serving(rate=args.serve_rate, duration=args.serve_seconds)
+    n_req = len(trace.arrivals)
+    t0 = time.perf_counter()
+    resident = [Plan(i.M, i.J, "c64") for i in trace.plans[:256]]
+    t_resident = time.perf_counter() - t0
+
+    def pinned(k):
+        return torch.randn(k, dtype=torch.complex64).pin_memory()
+
+    res_in = [pinned(p.k) for p in resident]
+    res_out = [torch.empty(p.k, dtype=torch.complex64).pin_memory() for p in resident]
+    pool = {}                                  # s -> list of free (in, out) pinned pairs
+    pool_mu = th.Lock()
+
+    def take(s):
+        with pool_mu:
+            lst = pool.setdefault(s, [])
+            if lst:
+                return lst.pop()
+        return pinned(1 << s), torch.empty(1 << s, dtype=torch.complex64).pin_memory()
+
+    srv = Server("c64", budget_bytes=args.serve_budget << 20, n_slots=2, max_batch=args.serve_batch)
+    h = srv.handle
+    arrival = np.zeros(n_req)
+    submit_t = np.zeros(n_req)
+    fresh_bufs = {}
+    fresh_plans = {}
+    planner = cf.ThreadPoolExecutor(max_workers=args.serve_planners)
+
+    def fresh(r, inst, t_arr):
+        plan = Plan(inst.M, inst.J, "c64")     # ctypes drops the GIL: plans build in parallel
+        bi, bo = take(plan.s)
+        fresh_bufs[r] = (bi, bo)
+        fresh_plans[r] = plan
+        submit_t[r] = time.perf_counter()
+        N.sdft_server_submit(h, plan.handle, bi.data_ptr(), bo.data_ptr(), r)
+
+    lat = np.zeros(n_req)
+    done = np.zeros(n_req, dtype=bool)
+    status = np.zeros(n_req, dtype=np.int32)
+    stop = th.Event()
+
+    def poller():
+        while not stop.is_set() or not done.all():
+            tags, l, st = N.sdft_server_poll(h, 8192)
+            for t, li, si in zip(tags, l, st):
+                t = int(t)
+                lat[t] = li + (submit_t[t] - arrival[t])
+                status[t] = si
+                done[t] = True
+                if t in fresh_bufs:
+                    with pool_mu:
+                        pool.setdefault(fresh_plans[t].s, []).append(fresh_bufs.pop(t))
+            if not len(tags):
+                time.sleep(0.0002)
+            if stop.is_set() and time.perf_counter() > deadline:
+                break
+
+    deadline = float("inf")
+    pt = th.Thread(target=poller, daemon=True)
+    pt.start()
+    start = time.perf_counter() + 0.05
+    futures = []
+    for r in range(n_req):
+        t_arr = start + trace.arrivals[r]
+        arrival[r] = t_arr
+        while True:
+            now = time.perf_counter()
+            if now >= t_arr:
+                break
+            if t_arr - now > 0.0005:
+                time.sleep(t_arr - now - 0.0003)
+        pid = int(trace.plan_ids[r])
+        if pid < 256:
+            submit_t[r] = time.perf_counter()
+            N.sdft_server_submit(h, resident[pid].handle, res_in[pid].data_ptr(), res_out[pid].data_ptr(), r)
+        else:
+            futures.append(planner.submit(fresh, r, trace.plans[pid], t_arr))
+    for f in futures:
+        f.result()
+    srv.drain(timeout_ms=600_000)
+    end = time.perf_counter()
+    deadline = end + 5.0
+    stop.set()
+    pt.join(timeout=10)
+    planner.shutdown()
+    st = srv.stats()
+    ok = status == 0
+    ks = np.array([(resident[int(p)].k if p < 256 else (1 << trace.plans[int(p)].s)) for p in trace.plan_ids])
+    wall = end - start
+    is_fresh = np.array([p >= 256 for p in trace.plan_ids])
+    split = {}
+    for name, sel in (("resident", ok & ~is_fresh), ("fresh", ok & is_fresh)):
+        if sel.any():
+            split[name] = {"p50_ms": float(np.percentile(lat[sel], 50) * 1e3),
+                           "p99_ms": float(np.percentile(lat[sel], 99) * 1e3), "count": int(sel.sum())}
+    out = {"requests": n_req, "offered_rate": args.serve_rate, "seconds": args.serve_seconds,
+           "by_kind": split,
+           "completed": int(done.sum()), "failed": int((~ok).sum()),
+           "p50_ms": float(np.percentile(lat[ok], 50) * 1e3) if ok.any() else None,
+           "p99_ms": float(np.percentile(lat[ok], 99) * 1e3) if ok.any() else None,
+           "mean_ms": float(lat[ok].mean() * 1e3) if ok.any() else None,
+           "coeffs_per_s": float(ks[ok].sum() / wall), "achieved_rate": float(ok.sum() / wall),
+           "fresh_plans": int(sum(1 for p in trace.plan_ids if p >= 256)),
+           "micro_batches": st["micro_batches"], "max_inflight": st["max_inflight"],
+           "arena_peak_MiB": st["arena_peak_bytes"] / 2**20, "budget_MiB": args.serve_budget,
+           "resident_plan_build_s": t_resident, "device_status": srv.device_status()}
+    srv.close()
+    return out
+
+
 def cpu_baseline(inst, x32, y32, sample):
     """The FP64 oracle's dense solve on `sample` instances of the same input."""
     import oracle as O
@@ -444,7 +567,13 @@ def main():
     ap.add_argument("--large", action="store_true", help="time only the large-k leg (N=2^30, k=2^20)")
     ap.add_argument("--large-batch", type=int, default=64)
     ap.add_argument("--uneven-count", type=int, default=10000)
-    ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and large-k legs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the uneven, large-k and serving legs")
+    ap.add_argument("--serve", action="store_true", help="run only the serving leg")
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-budget", type=int, default=16384, help="admission budget, MiB")
+    ap.add_argument("--serve-batch", type=int, default=64)
+    ap.add_argument("--serve-planners", type=int, default=12)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -452,6 +581,8 @@ def main():
         run_reference(args)
     elif args.large:
         print(json.dumps({"large_k": run_large(args)}), flush=True)
+    elif args.serve:
+        print(json.dumps({"serving": run_serving(args)}), flush=True)
     else:
         run_ours(args)
 
