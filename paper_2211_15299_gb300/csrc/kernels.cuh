@@ -61,21 +61,23 @@ __host__ __device__ constexpr uint32_t xor_part(uint32_t X) {
 }
 
 // ---- butterflies -----------------------------------------------------------------
+// complex64: the twiddle product in scalar FMAs, the two complex sums as packed
+// FP32x2 operations (each lane rounds exactly as the scalar operation would).
 __device__ __forceinline__ void bfly(float2& a, float2& b, const float2 w) {
-  const float tr = fmaf(-w.y, b.y, w.x * b.x);
-  const float ti = fmaf(w.y, b.x, w.x * b.y);
-  b.x = a.x - tr;
-  b.y = a.y - ti;
-  a.x = a.x + tr;
-  a.y = a.y + ti;
+  float2 t;
+  t.x = fmaf(-w.y, b.y, w.x * b.x);
+  t.y = fmaf(w.y, b.x, w.x * b.y);
+  b = __ffma2_rn(t, make_float2(-1.f, -1.f), a);   // a - t
+  a = __fadd2_rn(a, t);
 }
 __device__ __forceinline__ void bfly_scaled(float2& a, float2& b, const float2 w, const float sc) {
-  const float tr = fmaf(-w.y, b.y, w.x * b.x);
-  const float ti = fmaf(w.y, b.x, w.x * b.y);
-  b.x = fmaf(a.x, sc, -tr);
-  b.y = fmaf(a.y, sc, -ti);
-  a.x = fmaf(a.x, sc, tr);
-  a.y = fmaf(a.y, sc, ti);
+  float2 t;
+  t.x = fmaf(-w.y, b.y, w.x * b.x);
+  t.y = fmaf(w.y, b.x, w.x * b.y);
+  const float2 s2 = make_float2(sc, sc);
+  const float2 as = __fmul2_rn(a, s2);                // exact: sc is a power of two
+  b = __ffma2_rn(t, make_float2(-1.f, -1.f), as);
+  a = __fadd2_rn(as, t);
 }
 __device__ __forceinline__ void bfly(double2& a, double2& b, const double2 w) {
   const double tr = fma(-w.y, b.y, w.x * b.x);
@@ -308,16 +310,30 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   if (t0 >= t1) return;
   const uint64_t n = t1 - t0;
 
-  auto coords = [&](uint64_t i, int& c1, int& c3) {
-    const int64_t a = int64_t(i / args.nB), bb = int64_t(i % args.nB);
-    c1 = int(a * args.a_step1 + bb * args.b_step1);
-    c3 = int(bb * args.b_step3);
+  // Tile i = a * nB + b: walk (a, b) incrementally instead of dividing.
+  struct Cursor {
+    uint64_t a, b;
   };
-  auto issue_load = [&](uint64_t j) {  // local tile index j -> buffer j % kBufs
-    const uint32_t b = uint32_t(j % kBufs);
+  auto cursor_at = [&](uint64_t i) { return Cursor{i / args.nB, i % args.nB}; };
+  auto advance = [&](Cursor& c) {
+    if (++c.b == args.nB) {
+      c.b = 0;
+      ++c.a;
+    }
+  };
+  auto coords = [&](const Cursor& c, int& c1, int& c3) {
+    c1 = int(int64_t(c.a) * args.a_step1 + int64_t(c.b) * args.b_step1);
+    c3 = int(int64_t(c.b) * args.b_step3);
+  };
+  Cursor load_cur = cursor_at(t0);     // thread 0: next tile to load
+  uint32_t load_buf = 0;               // thread 0: its buffer (tiles load in order, buffers cycle)
+  auto issue_load = [&]() {
+    const uint32_t b = load_buf;
+    load_buf = (load_buf + 1 == uint32_t(kBufs)) ? 0u : load_buf + 1;
     const uint32_t bar = bar0 + 8 * b;
     int c1, c3;
-    coords(t0 + j, c1, c3);
+    coords(load_cur, c1, c3);
+    advance(load_cur);
     ptx::mbar_arrive_expect_tx(bar, kTileBytes);
     ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &src, bar, 0, c1, 0, c3);
   };
@@ -327,7 +343,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&src);
     ptx::prefetch_tensormap(&dst);
-    for (uint64_t j = 0; j < n && j < uint64_t(kBufs); ++j) issue_load(j);
+    for (uint64_t j = 0; j < n && j < uint64_t(kBufs); ++j) issue_load();
   }
   __syncthreads();
   const R sc = R(args.scale);
@@ -336,17 +352,20 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   const C* twt = tw;
   uint64_t cur_tab = ~0ull;
   bool aborted = false;
+  Cursor cur = cursor_at(t0);          // tile being computed
+  uint32_t b = 0;                      // its buffer
+  uint32_t phases = 0;                 // bit q: parity of buffer q's next completion
   uint64_t j = 0;
-  for (; j < n; ++j) {
-    const uint32_t b = uint32_t(j % kBufs);
+  for (; j < n; ++j, advance(cur), b = (b + 1 == uint32_t(kBufs)) ? 0u : b + 1) {
     char* buf = smem + b * kTileBytes;
-    const uint64_t tab = args.tw_stride ? (t0 + j) / args.nB : 0;
+    const uint64_t tab = args.tw_stride ? cur.a : 0;
     if (tab != cur_tab) {  // uniform across the CTA
       twt = tw + tab * args.tw_stride;
       load_reg_twiddles<R, PLO, PHI>(twt, tid, wreg);
       cur_tab = tab;
     }
-    const bool ok = ptx::mbar_wait_bounded(bar0 + 8 * b, uint32_t((j / kBufs) & 1), args.timeout_ns);
+    const bool ok = ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, args.timeout_ns);
+    phases ^= 1u << b;
     if (__syncthreads_or(!ok)) {
       aborted = true;
       break;
@@ -354,12 +373,12 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     run_passes<R, PLO, PHI, LAST>(buf, wreg, args.tw0, twt, tid, sc);
     if (tid == 0) {
       int c1, c3;
-      coords(t0 + j, c1, c3);
+      coords(cur, c1, c3);
       ptx::tma_store_4d(&dst, ptx::smem_addr(buf), 0, c1, 0, c3);
       ptx::bulk_commit();
       if (j >= 1 && j + 2 < n) {
         ptx::bulk_wait_read<1>();   // the store of tile j-1 has left its buffer
-        issue_load(j + 2);
+        issue_load();               // tile j+2 into that buffer
       }
     }
   }

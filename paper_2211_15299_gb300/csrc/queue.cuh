@@ -246,6 +246,27 @@ struct QPipe {
     ptx::mbar_arrive_expect_tx(bar, bytes);
     ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], bar, 0, it.c1, 0, it.c3);
     inflight |= 1u << b;
+    prefetch_tables(it);
+  }
+
+  // Twiddle tables of an item into L2 while its tile is still in flight.
+  __device__ __forceinline__ void prefetch_tables(const QItem& it) const {
+    constexpr int TB = KT<R>::TB;
+    constexpr uint32_t ES = KT<R>::ES;
+    if (it.variant >= 16) {                        // later level: entries [2^plo, 2^TB)
+      const int Q = (it.variant - 16) / 2 + 1;
+      const uint32_t first = 1u << (TB - Q);
+      ptx::prefetch_l2(static_cast<const char*>(it.tw) + first * ES, ((1u << TB) - first) * ES);
+    } else if (it.variant == kVFirstChunk) {
+      ptx::prefetch_l2(prm.a.insts[it.inst].tw, (1u << TB) * ES);
+    } else {                                       // whole instances of size 2^s
+      const int s = it.variant - 1 + 5;
+      const uint32_t cnt = it.count < 16u ? it.count : 16u;   // bound the work of the issuing thread
+      for (uint32_t g = 0; g < cnt; ++g) {
+        const void* tw = prm.a.insts[it.inst + g].tw;
+        if (tw) ptx::prefetch_l2(tw, (1u << s) * ES);
+      }
+    }
   }
 
   // Wait for item j's tile; false if the CTA must stop.
@@ -313,14 +334,14 @@ __device__ __noinline__ uint64_t loop_single(QPipe<R>& q, uint64_t j, int v) {
   for (; j < q.n; ++j) {
     const QItem it = q.item(j);
     if (it.variant != v) break;
-    if (!q.begin(j, it)) break;
     const bool first = v < 16;
     const C* tab = first ? static_cast<const C*>(a.insts[it.inst].tw) : static_cast<const C*>(it.tw);
     const R sc = first ? R(a.insts[it.inst].scale) : R(it.scale);
-    if (tab != cache) {
+    if (tab != cache) {          // issue the register loads before waiting for the tile
       load_reg_twiddles<R, PLO, PHI>(tab, q.tid, wreg);
       cache = tab;
     }
+    if (!q.begin(j, it)) break;
     // pass 0 reads entry 2^m1 + u as w0[2^m1 - 1 + u]: w0 = tab + 1
     run_passes<R, PLO, PHI, LAST>(q.smem + (j % kBufs) * kTileBytes, wreg, tab + 1, tab, q.tid, sc);
     q.end(j, it);
