@@ -414,7 +414,9 @@ def run_serving(args):
     planner = cf.ThreadPoolExecutor(max_workers=args.serve_planners)
 
     def fresh(r, inst, t_arr):
-        plan = Plan(inst.M, inst.J, "c64")     # ctypes drops the GIL: plans build in parallel
+        # ctypes drops the GIL, so plans build in parallel; the device tables stay on the
+        # host until the server uploads them into its arena with the request
+        plan = Plan(inst.M, inst.J, "c64", defer=True)
         bi, bo = take(plan.s)
         fresh_bufs[r] = (bi, bo)
         fresh_plans[r] = plan

@@ -65,7 +65,11 @@ typedef enum {
 typedef enum { SDFT_C64 = 0, SDFT_C128 = 1 } sdft_prec;
 
 /* Plan flags. */
-#define SDFT_PLAN_HOST_ONLY 0x1u /* build the host tables only; no device upload */
+#define SDFT_PLAN_HOST_ONLY 0x1u    /* build the host tables only; no device upload */
+#define SDFT_PLAN_DEFER_DEVICE 0x2u /* build the device tables in host memory but do not upload:
+                                       the plan can only be used through a server
+                                       (sdft_server_submit), which uploads them into its arena
+                                       per request, so creating it allocates no device memory */
 
 /* Largest log2N and log2 k this build accepts. */
 #define SDFT_MAX_LOG2N 62u
@@ -79,7 +83,7 @@ typedef enum { SDFT_C64 = 0, SDFT_C128 = 1 } sdft_prec;
  *            during the call.
  *   k      : |J|, a power of two, k <= 2^SDFT_MAX_LOG2K.
  *   prec   : arithmetic of the device path (complex64 or complex128 buffers).
- *   flags  : 0 or SDFT_PLAN_HOST_ONLY.
+ *   flags  : 0, SDFT_PLAN_HOST_ONLY or SDFT_PLAN_DEFER_DEVICE.
  *   out    : receives the plan; the caller owns it (sdft_plan_destroy).
  * Pivots: the levels l at which the congruence tree T(J) splits (Definition 8),
  * found as the 2-adic valuations of differences of neighbours in bit-reversed

@@ -31,6 +31,7 @@ P_f64 = ctypes.POINTER(ctypes.c_double)
 SDFT_C64, SDFT_C128 = 0, 1
 SDFT_STRATEGY_LEVELS, SDFT_STRATEGY_QUEUE = 1, 2
 SDFT_PLAN_HOST_ONLY = 0x1
+SDFT_PLAN_DEFER_DEVICE = 0x2
 
 STATUS = {
     0: "SDFT_OK", 1: "SDFT_ERR_ARG", 2: "SDFT_ERR_NOT_POW2", 3: "SDFT_ERR_RANGE",

@@ -135,7 +135,8 @@ sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft
                              sdft_plan* out) {
   if (!out) return SDFT_ERR_ARG;
   *out = nullptr;
-  if (flags & ~SDFT_PLAN_HOST_ONLY) return SDFT_ERR_ARG;
+  if (flags & ~(SDFT_PLAN_HOST_ONLY | SDFT_PLAN_DEFER_DEVICE)) return SDFT_ERR_ARG;
+  if ((flags & SDFT_PLAN_HOST_ONLY) && (flags & SDFT_PLAN_DEFER_DEVICE)) return SDFT_ERR_ARG;
   sdft_plan_s* h = new (std::nothrow) sdft_plan_s();
   if (!h) return SDFT_ERR_NOMEM;
   sdft_status s;
@@ -173,6 +174,13 @@ sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft
       for (int i = 0; i < 30 && size_t(2 + i) < 2 * size_t(p.tw_elems); ++i)
         p.tw0[i] = prec == SDFT_C64 ? double(reinterpret_cast<const float*>(host.data())[2 + i])
                                     : reinterpret_cast<const double*>(host.data())[2 + i];
+    }
+    if (flags & SDFT_PLAN_DEFER_DEVICE) {     // keep the tables on the host for a server
+      p.host_tables.swap(host);
+      p.deferred = true;
+      p.device = dev;
+      *out = h;
+      return SDFT_OK;
     }
     e = cudaMalloc(&p.d_status, 256);
     if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, 256);

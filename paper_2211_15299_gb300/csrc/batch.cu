@@ -507,8 +507,10 @@ sdft_status sdft_batch_create(const sdft_plan* plans, uint64_t n, sdft_batch* ou
   if (!out) return SDFT_ERR_ARG;
   *out = nullptr;
   if (!plans || n == 0 || n > 0xffffffffull) return SDFT_ERR_ARG;
-  for (uint64_t i = 0; i < n; ++i)
+  for (uint64_t i = 0; i < n; ++i) {
     if (!plans[i]) return SDFT_ERR_ARG;
+    if (plans[i]->p.deferred) return SDFT_ERR_NO_DEVICE;   // tables only reach the device via a server
+  }
   // Either every plan is host-only (a batch for inspection) or all live on the current device.
   const bool host_only = plans[0]->p.device < 0;
   int dev = -1;

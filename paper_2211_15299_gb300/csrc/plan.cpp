@@ -27,6 +27,40 @@ inline uint64_t bitrev64(uint64_t x) {
 
 inline int highest_bit(uint64_t x) { return 63 - __builtin_clzll(x); }
 
+// LSD radix sort of `bits`-bit keys in 8-bit digits (stable; tmp is scratch).
+void radix_sort(std::vector<uint64_t>& a, std::vector<uint64_t>& tmp, uint32_t bits) {
+  const size_t n = a.size();
+  tmp.resize(n);
+  for (uint32_t shift = 0; shift < bits; shift += 8) {
+    size_t count[257] = {0};
+    for (size_t i = 0; i < n; ++i) ++count[((a[i] >> shift) & 255u) + 1];
+    for (int d = 0; d < 256; ++d) count[d + 1] += count[d];
+    for (size_t i = 0; i < n; ++i) tmp[count[(a[i] >> shift) & 255u]++] = a[i];
+    a.swap(tmp);
+  }
+}
+
+// Byte lookup tables for a bit gather: out(x) = sum_q bit_{src[q]}(x) << dst[q],
+// evaluated as the OR of one table entry per byte of x.
+struct BitGather {
+  uint32_t nbytes = 0;
+  std::vector<uint64_t> lut;   // nbytes x 256
+  void build(const uint32_t* src, const uint32_t* dst, uint32_t n, uint32_t in_bits) {
+    nbytes = (in_bits + 7) / 8;
+    lut.assign(size_t(nbytes) * 256, 0);
+    for (uint32_t q = 0; q < n; ++q) {
+      const uint32_t byte = src[q] / 8, bit = src[q] % 8;
+      for (uint32_t v = 0; v < 256; ++v)
+        if (v >> bit & 1u) lut[size_t(byte) * 256 + v] |= 1ull << dst[q];
+    }
+  }
+  uint64_t operator()(uint64_t x) const {
+    uint64_t r = 0;
+    for (uint32_t b = 0; b < nbytes; ++b) r |= lut[size_t(b) * 256 + ((x >> (8 * b)) & 255u)];
+    return r;
+  }
+};
+
 // cos(pi x), sin(pi x) for a dyadic x in [0, 1): fold into [0, 1/4] with exact
 // reflections so quarter turns come out exact, then call the C library.
 void cos_sin_pi(double x, double& c, double& s) {
@@ -78,9 +112,10 @@ sdft_status build_plan(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec
   p.prec = prec;
 
   // Pivots from depth-first neighbours of the LSB-first tree.
-  std::vector<uint64_t> rev(k);
+  std::vector<uint64_t> rev(k), tmp;
   for (uint64_t i = 0; i < k; ++i) rev[i] = M ? (bitrev64(J[i]) >> (64 - M)) : 0;
-  std::sort(rev.begin(), rev.end());
+  radix_sort(rev, tmp, M);
+  std::vector<uint64_t>().swap(tmp);
   uint64_t level_mask = 0;
   for (uint64_t i = 0; i + 1 < k; ++i) {
     const uint64_t x = rev[i] ^ rev[i + 1];
@@ -94,22 +129,26 @@ sdft_status build_plan(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec
     if (level_mask >> l & 1) p.pivots.push_back(l);
 
   // Canonical order: coefficient t is the element whose pivot bits spell t.
+  std::vector<uint32_t> qbits(s), ibits(s);
+  for (uint32_t q = 0; q < s; ++q) {
+    qbits[q] = q;
+    ibits[q] = M - 1 - p.pivots[q];
+  }
+  BitGather key_of;
+  key_of.build(p.pivots.data(), qbits.data(), s, M);
   p.Jc.assign(k, ~0ull);
   for (uint64_t i = 0; i < k; ++i) {
-    uint64_t key = 0;
-    for (uint32_t q = 0; q < s; ++q) key |= ((J[i] >> p.pivots[q]) & 1ull) << q;
+    const uint64_t key = key_of(J[i]);
     if (p.Jc[key] != ~0ull) return SDFT_ERR_NOT_HOMOGENEOUS;  // cannot happen once the count matched
     p.Jc[key] = J[i];
   }
 
-  // Pivoted sampling pattern (Definition "r_sampling_pattern"), sample order t.
-  p.I.assign(k, 0);
-  for (uint64_t t = 0; t < k; ++t) {
-    uint64_t i = 0;
-    for (uint32_t q = 0; q < s; ++q)
-      if (t >> q & 1) i |= 1ull << (M - 1 - p.pivots[q]);
-    p.I[t] = i;
-  }
+  // Pivoted sampling pattern (Definition "r_sampling_pattern"), sample order t:
+  // I[t] = sum_q bit_q(t) 2^(M-1-r_{q+1}).
+  BitGather index_of;
+  index_of.build(qbits.data(), ibits.data(), s, s);
+  p.I.resize(k);
+  for (uint64_t t = 0; t < k; ++t) p.I[t] = index_of(t);
 
   // Level schedule.
   p.levels.clear();

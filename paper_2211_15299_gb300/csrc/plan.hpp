@@ -59,6 +59,8 @@ struct Plan {
   uint64_t device_bytes = 0;
   double tw0[32] = {0};           // level-0 table entries 1..15 (rounded to prec), for kernel params
   void* queues = nullptr;         // cached work queues of strided multi-level execution (batch.cu)
+  bool deferred = false;          // device tables not uploaded: host_tables holds them (serving)
+  std::vector<unsigned char> host_tables;
   int strategy = SDFT_STRATEGY_LEVELS;
 };
 

@@ -89,6 +89,10 @@ struct Req {
   Clock::time_point t_submit;
   uint64_t off = 0;      // arena byte offset
   uint32_t order = 0;    // log2 block bytes
+  const void* tw = nullptr;   // device twiddle tables used for this request
+  uint64_t tw_off = 0;        // arena block of a deferred plan's tables
+  uint32_t tw_order = 0;
+  bool own_tw = false;
 };
 
 struct Done {
@@ -189,7 +193,7 @@ sdft_status build_items(Server& S, Slot& sl, size_t& n_items, uint32_t& n_ctr) {
   for (size_t i = 0; i < n; ++i) {
     const Plan& p = *sl.reqs[i].plan;
     QInst& q = sl.h_insts[i];
-    q.tw = p.d_tw;
+    q.tw = sl.reqs[i].tw;
     q.off = sl.reqs[i].off / es;
     q.s = p.s;
     q.pad = 0;
@@ -239,7 +243,8 @@ sdft_status build_items(Server& S, Slot& sl, size_t& n_items, uint32_t& n_ctr) {
         it.sig = sig;
         it.c1 = int32_t(gb << L.lg);
         it.c3 = int32_t(z0 + z);
-        it.tw = static_cast<const char*>(p.d_tw) + (L.tw_off + gb * L.tw_len) * es - (size_t(1) << L.plo) * es;
+        it.tw = static_cast<const char*>(sl.reqs[g.inst].tw) + (L.tw_off + gb * L.tw_len) * es -
+                (size_t(1) << L.plo) * es;
         it.scale = sl.h_insts[g.inst].scale;
         sdft_status s = push(it);
         if (s != SDFT_OK) return s;
@@ -320,6 +325,11 @@ sdft_status launch_slot(Server& S, Slot& sl) {
   if (s != SDFT_OK) return s;
   cudaError_t e = cudaSuccess;
   for (const Req& r : sl.reqs) {
+    if (r.own_tw) {   // a deferred plan's tables go into the arena with its request
+      e = cudaMemcpyAsync(S.d_arena + r.tw_off, r.plan->host_tables.data(), r.plan->host_tables.size(),
+                          cudaMemcpyHostToDevice, sl.stream);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
     e = cudaMemcpyAsync(S.d_arena + r.off, r.h_in, r.plan->k * es, cudaMemcpyHostToDevice, sl.stream);
     if (e != cudaSuccess) return cuda_fail(e);
   }
@@ -365,6 +375,7 @@ void worker_loop(Server* S) {
       if (!sl->busy || !sl->done.load(std::memory_order_acquire)) continue;
       for (const Req& r : sl->reqs) {
         S->buddy.release(r.off, r.order);
+        if (r.own_tw) S->buddy.release(r.tw_off, r.tw_order);
         const double lat = std::chrono::duration<double>(sl->t_done - r.t_submit).count();
         S->done.push_back(Done{r.tag, lat, int32_t(SDFT_OK)});
         ++S->stats.completed;
@@ -392,7 +403,9 @@ void worker_loop(Server* S) {
       while (!S->waiting.empty() && batch.size() < S->max_batch) {
         Req r = S->waiting.front();
         r.order = block_order(*S, *r.plan);
-        if ((1ull << r.order) > S->budget) {        // can never fit
+        const uint64_t tw_bytes = r.plan->deferred ? std::max<uint64_t>(r.plan->host_tables.size(), 128) : 0;
+        r.tw_order = tw_bytes ? uint32_t(64 - __builtin_clzll(tw_bytes - 1)) : 0;
+        if ((1ull << r.order) + (tw_bytes ? (1ull << r.tw_order) : 0) > S->budget) {   // can never fit
           S->waiting.pop_front();
           S->done.push_back(Done{r.tag, 0.0, int32_t(SDFT_ERR_BUDGET)});
           ++S->stats.failed;
@@ -401,6 +414,18 @@ void worker_loop(Server* S) {
         }
         const uint64_t off = S->buddy.alloc(r.order);
         if (off == ~0ull) break;                        // wait for memory to free up
+        if (tw_bytes) {
+          const uint64_t toff = S->buddy.alloc(r.tw_order);
+          if (toff == ~0ull) {
+            S->buddy.release(off, r.order);
+            break;
+          }
+          r.tw_off = toff;
+          r.tw = S->d_arena + toff;
+          r.own_tw = true;
+        } else {
+          r.tw = r.plan->d_tw;
+        }
         r.off = off;
         S->waiting.pop_front();
         batch.push_back(r);
@@ -419,6 +444,7 @@ void worker_loop(Server* S) {
           cudaStreamSynchronize(free_slot->stream);
           for (const Req& r : free_slot->reqs) {
             S->buddy.release(r.off, r.order);
+            if (r.own_tw) S->buddy.release(r.tw_off, r.tw_order);
             S->done.push_back(Done{r.tag, 0.0, int32_t(st)});
             ++S->stats.failed;
           }
@@ -529,6 +555,7 @@ sdft_status sdft_server_submit(sdft_server srv, sdft_plan plan, const void* h_sa
   if (!srv || !plan || !h_samples || !h_coeffs) return SDFT_ERR_ARG;
   Server& S = srv->s;
   if (plan->p.device != S.device) return SDFT_ERR_NO_DEVICE;
+  if (!plan->p.deferred && !plan->p.d_status) return SDFT_ERR_NO_DEVICE;
   if (plan->p.prec != S.prec) return SDFT_ERR_PRECISION;
   Req r;
   r.tag = tag;

@@ -92,3 +92,29 @@ def test_admission_respects_the_budget():
     outs, got = _serve(srv, big)
     assert got[0][1] == 7
     srv.close()
+
+
+def test_deferred_plans_through_the_server():
+    """Plans built with their device tables kept on the host (no device
+    allocation at creation) give the same results through a server as plans
+    uploaded at creation, and cannot run outside a server."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Batch, Plan, SdftError, Server
+    rng = np.random.default_rng(5152)
+    reqs = _requests(rng, [3, 6, 12, 13, 15, 17])
+    srv = Server("c64", budget_bytes=64 << 20, n_slots=2, max_batch=4)
+    ref, _ = _serve(srv, reqs)
+    deferred = []
+    for plan, h_in, c, M, piv, Jc in reqs:
+        J = np.asarray(plan.support_order)
+        deferred.append((Plan(M, J, 0, defer=True), h_in, c, M, piv, Jc))
+    got, status = _serve(srv, deferred)
+    assert all(status[i][1] == 0 for i in range(len(reqs)))
+    for i in range(len(reqs)):
+        assert np.array_equal(got[i].numpy(), ref[i].numpy()), i
+    x = torch.zeros(deferred[0][0].k, dtype=torch.complex64, device="cuda")
+    with pytest.raises(SdftError):
+        deferred[0][0].execute(x)
+    with pytest.raises(SdftError):
+        Batch([deferred[0][0]])
+    srv.close()
