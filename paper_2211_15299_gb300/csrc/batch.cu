@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
@@ -77,11 +78,12 @@ void free_batch(Batch& b) {
 int log2u(uint64_t x) { return 63 - __builtin_clzll(x); }
 
 // Invariants of an item list: every dependency refers to a counter signalled
-// only by items earlier in the list, reaches its target exactly, and sits at
-// least 4 x grid positions back; level-0 tiles cover aligned rows.
+// only by items earlier in the list, reaches its target exactly, and its last
+// producer sits at least 3 x grid positions back (then a CTA never waits on an
+// item whose store it has not yet published, and no two CTAs wait on each other).
 sdft_status check_items(const Batch& B) {
   std::vector<uint64_t> sig_count(B.n_counters, 0), sig_last(B.n_counters, 0);
-  const uint64_t lag = 4ull * uint64_t(B.grid);
+  const uint64_t lag = 3ull * uint64_t(B.grid);
   for (uint64_t p = 0; p < B.items.size(); ++p) {
     const QItem& it = B.items[p];
     if (it.dep != kNone) {
@@ -97,13 +99,6 @@ sdft_status check_items(const Batch& B) {
   }
   return SDFT_OK;
 }
-
-struct Group {            // later-level tiles of one instance, waiting to be emitted
-  uint64_t ready;         // emit once this many items exist
-  std::vector<QItem> items;
-  int64_t next_inst = -1; // instance whose next level follows this group (-1: none)
-  size_t next_level = 0;
-};
 
 }  // namespace
 
@@ -160,13 +155,19 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
     return int(slot);
   };
 
-  const uint64_t lag = 4ull * uint64_t(B.grid);
-  std::vector<QItem>& items = B.items;
-  items.clear();
-  std::deque<Group> pending;
+  // Phase 1: units of work. A unit is one instance's levels (stage 0 = its
+  // level-0 chunks, stage j = its level-j tiles, each stage waiting on the
+  // previous one's counter), a tile of whole same-size instances, or a range of
+  // k <= 16 instances. cost = coefficients touched.
+  struct Unit {
+    std::vector<std::vector<QItem>> stages;
+    uint64_t cost = 0;
+  };
+  std::vector<Unit> units;
   uint32_t n_ctr = 0;
-
-  auto later_group = [&](uint64_t q, size_t level, uint32_t dep, uint32_t need, Group& g) -> sdft_status {
+  const size_t es = size_t(elem_bytes(prec));
+  auto later_stage = [&](uint64_t q, size_t level, uint32_t dep, uint32_t need, std::vector<QItem>& out,
+                         uint32_t& sig_out) -> sdft_status {
     const Plan& p = plans[order[q]]->p;
     const Level& L = p.levels[level];
     const int slot = slot_for(L);
@@ -175,8 +176,7 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
     const uint64_t z0 = insts[q].off >> L.hi;
     if (z0 + zs > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
     const bool more = level + 1 < p.levels.size();
-    const uint32_t sig = more ? n_ctr++ : kNone;
-    const size_t es = size_t(elem_bytes(prec));
+    sig_out = more ? n_ctr++ : kNone;
     for (uint64_t gb = 0; gb < L.n_gb; ++gb)
       for (uint64_t z = 0; z < zs; ++z) {
         QItem it{};
@@ -186,36 +186,13 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
         it.inst = uint32_t(q);
         it.dep = dep;
         it.need = need;
-        it.sig = sig;
+        it.sig = sig_out;
         it.c1 = int32_t(gb << L.lg);
         it.c3 = int32_t(z0 + z);
         it.tw = static_cast<const char*>(p.d_tw) + (L.tw_off + gb * L.tw_len) * es - (size_t(1) << L.plo) * es;
         it.scale = insts[q].scale;
-        g.items.push_back(it);
+        out.push_back(it);
       }
-    if (more) {
-      g.next_inst = int64_t(q);
-      g.next_level = level + 1;
-    }
-    return SDFT_OK;
-  };
-
-  auto emit = [&](const QItem& it) -> sdft_status {
-    items.push_back(it);
-    while (!pending.empty() && pending.front().ready <= items.size()) {
-      Group g = std::move(pending.front());
-      pending.pop_front();
-      const uint32_t sig = g.items.empty() ? kNone : g.items.front().sig;
-      const uint32_t cnt = uint32_t(g.items.size());
-      for (const QItem& x : g.items) items.push_back(x);
-      if (g.next_inst >= 0) {
-        Group h;
-        h.ready = items.size() + lag;
-        sdft_status s = later_group(uint64_t(g.next_inst), g.next_level, sig, cnt, h);
-        if (s != SDFT_OK) return s;
-        pending.push_back(std::move(h));
-      }
-    }
     return SDFT_OK;
   };
 
@@ -223,16 +200,15 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
   while (q < n) {
     const uint32_t s = insts[q].s;
     if (s <= kSmallMax) {                       // one thread per instance
-      uint64_t cnt = 0;
-      while (q + cnt < n && insts[q + cnt].s <= kSmallMax && cnt < NT) ++cnt;
+      uint64_t cnt = 0, cost = 0;
+      while (q + cnt < n && insts[q + cnt].s <= kSmallMax && cnt < NT) cost += 1ull << insts[q + cnt++].s;
       QItem it{};
       it.variant = uint16_t(kVSmall);
       it.count = uint32_t(cnt);
       it.inst = uint32_t(q);
       it.dep = kNone;
       it.sig = kNone;
-      sdft_status st = emit(it);
-      if (st != SDFT_OK) return st;
+      units.push_back(Unit{{{it}}, cost});
       q += cnt;
     } else if (s <= TB) {                       // whole instances per tile
       uint64_t run = 0;
@@ -253,8 +229,7 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
         it.sig = kNone;
         it.c1 = int32_t(row0);
         it.c3 = 0;
-        sdft_status st = emit(it);
-        if (st != SDFT_OK) return st;
+        units.push_back(Unit{{{it}}, cnt << s});
         q += cnt;
         left -= cnt;
       }
@@ -264,6 +239,8 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
       const uint32_t sig = n_ctr++;
       const uint64_t row0 = insts[q].off >> CB;
       if (row0 + (chunks << (TB - CB)) > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
+      Unit u;
+      u.stages.emplace_back();
       for (uint64_t ch = 0; ch < chunks; ++ch) {
         QItem it{};
         it.variant = uint16_t(kVFirstChunk);
@@ -274,28 +251,107 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
         it.sig = sig;
         it.c1 = int32_t(row0 + (ch << (TB - CB)));
         it.c3 = 0;
-        sdft_status st = emit(it);
-        if (st != SDFT_OK) return st;
+        u.stages[0].push_back(it);
       }
-      Group g;
-      g.ready = items.size() + lag;
-      sdft_status st = later_group(q, 1, sig, uint32_t(chunks), g);
-      if (st != SDFT_OK) return st;
-      pending.push_back(std::move(g));
-      (void)p;
+      uint32_t dep = sig, need = uint32_t(chunks);
+      for (size_t level = 1; level < p.levels.size(); ++level) {
+        u.stages.emplace_back();
+        uint32_t next = kNone;
+        sdft_status st = later_stage(q, level, dep, need, u.stages.back(), next);
+        if (st != SDFT_OK) return st;
+        need = uint32_t(u.stages.back().size());
+        dep = next;
+      }
+      for (const auto& st : u.stages) u.cost += uint64_t(st.size()) << TB;
+      units.push_back(std::move(u));
       ++q;
     }
   }
-  // Tail: pad with no-op items so every dependency keeps its distance.
-  while (!pending.empty()) {
-    QItem nop{};
-    nop.variant = uint16_t(kVNop);
-    nop.dep = kNone;
-    nop.sig = kNone;
-    sdft_status st = emit(nop);
-    if (st != SDFT_OK) return st;
-  }
   B.n_counters = n_ctr;
+
+  // Phase 2: order the items. Every dependency must sit at least 3 x grid list
+  // positions behind the item that waits on it (CTA c takes positions c, c + G,
+  // ...; a CTA issues item j's load after publishing item j - 3's store).
+  QItem nop{};
+  nop.variant = uint16_t(kVNop);
+  nop.dep = kNone;
+  nop.sig = kNone;
+  std::vector<QItem>& items = B.items;
+  items.clear();
+  const uint64_t G = uint64_t(B.grid);
+  struct Pending {
+    uint64_t ready;
+    size_t unit, stage;
+  };
+  if (units.size() >= 2 * G) {
+    // Lanes: a unit runs entirely in one CTA (its tables stay in registers and
+    // L1, its intermediate in L2); units go to the least-loaded lane, largest
+    // first, and a unit's next stage follows 3 lane positions after its last item.
+    std::vector<size_t> by_cost(units.size());
+    for (size_t u = 0; u < units.size(); ++u) by_cost[u] = u;
+    std::stable_sort(by_cost.begin(), by_cost.end(),
+                     [&](size_t a, size_t b) { return units[a].cost > units[b].cost; });
+    std::vector<std::vector<size_t>> lane_units(G);
+    std::vector<std::pair<uint64_t, uint64_t>> heap;   // (load, lane), min-heap
+    for (uint64_t l = 0; l < G; ++l) heap.push_back({0, l});
+    auto cmp = [](const std::pair<uint64_t, uint64_t>& a, const std::pair<uint64_t, uint64_t>& b) {
+      return a > b;
+    };
+    for (size_t u : by_cost) {
+      std::pop_heap(heap.begin(), heap.end(), cmp);
+      auto& top = heap.back();
+      lane_units[top.second].push_back(u);
+      top.first += units[u].cost;
+      std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    std::vector<std::vector<QItem>> lanes(G);
+    size_t longest = 0;
+    for (uint64_t l = 0; l < G; ++l) {
+      std::vector<QItem>& lane = lanes[l];
+      std::deque<Pending> pend;
+      std::function<void(const QItem&)> put = [&](const QItem& it) {
+        lane.push_back(it);
+        while (!pend.empty() && pend.front().ready <= lane.size()) {
+          const Pending pd = pend.front();
+          pend.pop_front();
+          const auto& st = units[pd.unit].stages[pd.stage];
+          for (const QItem& x : st) lane.push_back(x);
+          if (pd.stage + 1 < units[pd.unit].stages.size())
+            pend.push_back(Pending{lane.size() + 3, pd.unit, pd.stage + 1});
+        }
+      };
+      for (size_t u : lane_units[l]) {
+        for (const QItem& it : units[u].stages[0]) put(it);
+        if (units[u].stages.size() > 1) pend.push_back(Pending{lane.size() + 3, u, 1});
+      }
+      while (!pend.empty()) put(nop);
+      longest = std::max(longest, lane.size());
+    }
+    items.resize(longest * G, nop);
+    for (uint64_t l = 0; l < G; ++l)
+      for (size_t idx = 0; idx < lanes[l].size(); ++idx) items[idx * G + l] = lanes[l][idx];
+    while (!items.empty() && items.back().variant == kVNop) items.pop_back();
+  } else {
+    // Round robin in unit order: a unit's next stage is held back until 4 x grid
+    // more items exist (consecutive items go to consecutive CTAs).
+    const uint64_t lag = 4ull * G;
+    std::deque<Pending> pend;
+    std::function<void(const QItem&)> put = [&](const QItem& it) {
+      items.push_back(it);
+      while (!pend.empty() && pend.front().ready <= items.size()) {
+        const Pending pd = pend.front();
+        pend.pop_front();
+        for (const QItem& x : units[pd.unit].stages[pd.stage]) items.push_back(x);
+        if (pd.stage + 1 < units[pd.unit].stages.size())
+          pend.push_back(Pending{items.size() + lag, pd.unit, pd.stage + 1});
+      }
+    };
+    for (size_t u = 0; u < units.size(); ++u) {
+      for (const QItem& it : units[u].stages[0]) put(it);
+      if (units[u].stages.size() > 1) pend.push_back(Pending{items.size() + lag, u, 1});
+    }
+    while (!pend.empty()) put(nop);
+  }
   if (B.device < 0) return SDFT_OK;
 
   // Device arrays.

@@ -230,6 +230,24 @@ __device__ __forceinline__ void load_reg_twiddles(const typename KT<R>::C* __res
   }
 }
 
+// Prefetch into L1 the entries a thread will read in every pass that takes
+// its twiddles from memory (register-held top pass and L1-read middle pass).
+template <class R, int PLO, int PHI, int P = 0>
+__device__ __forceinline__ void prefetch_twiddles(const typename KT<R>::C* __restrict__ tw, uint32_t tid) {
+  constexpr int TB = KT<R>::TB;
+  if constexpr (P < n_passes(TB, PLO, PHI)) {
+    constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
+    if constexpr (B > 0) {
+      const typename KT<R>::C* base = tw + (tid & ((1u << B) - 1u));
+#pragma unroll
+      for (int m1 = SLO; m1 < SHI; ++m1)
+#pragma unroll
+        for (int v = 0; v < (1 << (m1 - B)); ++v) ptx::prefetch_l1(base + (1u << m1) + (uint32_t(v) << B));
+    }
+    prefetch_twiddles<R, PLO, PHI, P + 1>(tw, tid);
+  }
+}
+
 template <class R, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0>
 __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* wreg, const typename KT<R>::C* w0,
                                            const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc) {

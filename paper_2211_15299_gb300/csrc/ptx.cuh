@@ -99,6 +99,10 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<uint64_t>(p)));
+}
+
 // Bring `bytes` (a multiple of 16, 16-byte aligned address) into L2 without
 // waiting for it.
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {

@@ -57,6 +57,15 @@ struct QArgs {
   uint32_t need_bias;       // added to every dependency target (0; non-zero only to test timeouts)
 };
 
+// Item metadata resolved by the issuing thread when it starts the item's load
+// (two items ahead), kept in shared memory per tile buffer.
+struct QMeta {            // 64 bytes
+  QItem it;
+  const void* tab;        // the item's (first) twiddle table, absolute-indexed
+  double scale;           // N/k for the final stage
+};
+constexpr uint32_t kQueueSmem = kBufs * kTileBytes + 64 + kBufs * sizeof(QMeta) + 1024;
+
 // Kernel parameters: the arguments and the tensor maps over the packed buffers
 // (maps in parameter space are baked into a captured CUDA graph).
 struct QParams {
@@ -223,8 +232,24 @@ struct QPipe {
   __device__ __forceinline__ const QItem& item(uint64_t j) const { return prm.a.items[c + j * G]; }
   __device__ __forceinline__ static bool is_tma(const QItem& it) { return it.variant != kVSmall && it.variant != kVNop; }
 
+  __device__ __forceinline__ QMeta& meta(uint64_t j) const {
+    return reinterpret_cast<QMeta*>(smem + kBufs * kTileBytes + 64)[j % kBufs];
+  }
+
   __device__ __forceinline__ void issue_load(uint64_t j) {   // thread 0
     const QItem& it = item(j);
+    QMeta& m = meta(j);             // read by all threads once a barrier has passed
+    m.it = it;
+    if (it.variant >= 16 && it.variant != kVNop) {
+      m.tab = it.tw;
+      m.scale = it.scale;
+    } else if (it.variant != kVNop && it.variant != kVSmall) {
+      m.tab = prm.a.insts[it.inst].tw;
+      m.scale = prm.a.insts[it.inst].scale;
+    } else {
+      m.tab = nullptr;
+      m.scale = 0.0;
+    }
     if (!is_tma(it)) return;
     if (it.dep != kNone) {
       const uint32_t* ctr = prm.a.counters + it.dep;
@@ -322,42 +347,37 @@ struct QPipe {
   }
 };
 
-// Consecutive items of one single-table variant: the top pass's twiddles stay
-// in registers while the table does not change. Returns the next item index.
+// A single-table item (a 2^TB chunk, a one-instance tile, a later-level group
+// block): the passes of k_level with the top pass's twiddles loaded into
+// registers for this item (the previous item prefetched them into L1).
 template <class R, int PLO, int PHI, bool LAST>
-__device__ __noinline__ uint64_t loop_single(QPipe<R>& q, uint64_t j, int v) {
+__device__ __forceinline__ void run_single(char* buf, const typename KT<R>::C* tab, R sc, uint32_t tid) {
   using C = typename KT<R>::C;
   constexpr int NREG = reg_twiddles(KT<R>::TB, PLO, PHI);
   C wreg[NREG > 0 ? NREG : 1];
-  const C* cache = nullptr;
-  const QArgs& a = q.prm.a;
-  for (; j < q.n; ++j) {
-    const QItem it = q.item(j);
-    if (it.variant != v) break;
-    const bool first = v < 16;
-    const C* tab = first ? static_cast<const C*>(a.insts[it.inst].tw) : static_cast<const C*>(it.tw);
-    const R sc = first ? R(a.insts[it.inst].scale) : R(it.scale);
-    if (tab != cache) {          // issue the register loads before waiting for the tile
-      load_reg_twiddles<R, PLO, PHI>(tab, q.tid, wreg);
-      cache = tab;
-    }
-    if (!q.begin(j, it)) break;
-    // pass 0 reads entry 2^m1 + u as w0[2^m1 - 1 + u]: w0 = tab + 1
-    run_passes<R, PLO, PHI, LAST>(q.smem + (j % kBufs) * kTileBytes, wreg, tab + 1, tab, q.tid, sc);
-    q.end(j, it);
-  }
-  return j;
+  load_reg_twiddles<R, PLO, PHI>(tab, tid, wreg);
+  // pass 0 reads entry 2^m1 + u as w0[2^m1 - 1 + u]: w0 = tab + 1
+  run_passes<R, PLO, PHI, LAST>(buf, wreg, tab + 1, tab, tid, sc);
 }
 
 template <class R, int Q = 1>
-__device__ __forceinline__ uint64_t dispatch_later_loop(QPipe<R>& q, uint64_t j, int v) {
+__device__ __forceinline__ void dispatch_later_single(int v, char* buf, const typename KT<R>::C* tab, R sc,
+                                                      uint32_t tid) {
   constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
-  if constexpr (Q > TB - CB) {
-    return j + 1;   // unknown variant: skip (cannot happen for host-built lists)
-  } else {
-    if (v == q_variant_later(Q, true)) return loop_single<R, TB - Q, TB, true>(q, j, v);
-    if (v == q_variant_later(Q, false)) return loop_single<R, TB - Q, TB, false>(q, j, v);
-    return dispatch_later_loop<R, Q + 1>(q, j, v);
+  if constexpr (Q <= TB - CB) {
+    if (v == q_variant_later(Q, true)) return run_single<R, TB - Q, TB, true>(buf, tab, sc, tid);
+    if (v == q_variant_later(Q, false)) return run_single<R, TB - Q, TB, false>(buf, tab, sc, tid);
+    dispatch_later_single<R, Q + 1>(v, buf, tab, sc, tid);
+  }
+}
+
+template <class R, int Q = 1>
+__device__ __forceinline__ void dispatch_later_prefetch(int v, const typename KT<R>::C* tab, uint32_t tid) {
+  constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
+  if constexpr (Q <= TB - CB) {
+    if (v == q_variant_later(Q, true) || v == q_variant_later(Q, false))
+      return prefetch_twiddles<R, TB - Q, TB>(tab, tid);
+    dispatch_later_prefetch<R, Q + 1>(v, tab, tid);
   }
 }
 
@@ -369,7 +389,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ 
   const uint32_t bar0 = ptx::smem_addr(smem + kBufs * kTileBytes);
   const uint32_t tid = threadIdx.x;
   {
-    const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 8 * kBufs;
+    const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 64 + kBufs * uint32_t(sizeof(QMeta));
     int bad = 0;
     if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
     else if (reinterpret_cast<uintptr_t>(&prm.maps[0]) & 63u) bad = kBadMap;
@@ -386,24 +406,39 @@ __global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ 
     for (uint64_t j = 0; j < q.n && j < uint64_t(kBufs); ++j) q.issue_load(j);
   }
   __syncthreads();
+  using C = typename KT<R>::C;
   constexpr int TB = KT<R>::TB;
-  uint64_t j = 0;
-  while (j < q.n && !q.aborted) {
-    const QItem it = q.item(j);
+  for (uint64_t j = 0; j < q.n; ++j) {
+    const QMeta& m = q.meta(j);
+    const QItem it = m.it;
     const int v = it.variant;
-    if (v == kVFirstChunk) {
-      j = loop_single<R, 0, TB, false>(q, j, v);
+    const C* tab = static_cast<const C*>(m.tab);
+    const R sc = R(m.scale);
+    if (!q.begin(j, it)) break;
+    char* buf = smem + (j % kBufs) * kTileBytes;
+    if (v == kVNop) {
+      // nothing to do
+    } else if (v == kVSmall) {
+      run_small<R>(a, it, tid);
+    } else if (v == kVFirstChunk) {
+      run_single<R, 0, TB, false>(buf, tab, sc, tid);
     } else if (v == q_variant_first(TB)) {
-      j = loop_single<R, 0, TB, true>(q, j, v);
-    } else if (v >= 16 && v != kVNop) {
-      j = dispatch_later_loop<R>(q, j, v);
+      run_single<R, 0, TB, true>(buf, tab, sc, tid);
+    } else if (v >= 16) {
+      dispatch_later_single<R>(v, buf, tab, sc, tid);
     } else {
-      if (!q.begin(j, it)) break;
-      if (v == kVSmall) run_small<R>(a, it, tid);
-      else if (v != kVNop) dispatch_first_q<R>(v, smem + (j % kBufs) * kTileBytes, a, it, tid);
-      q.end(j, it);
-      ++j;
+      dispatch_first_q<R>(v, buf, a, it, tid);   // several instances per tile
     }
+    if (j + 1 < q.n) {   // the next item's register and L1 twiddles, while this store drains
+      const QMeta& nx = q.meta(j + 1);
+      const int nv = nx.it.variant;
+      const C* nt = static_cast<const C*>(nx.tab);
+      if (nt && nt != tab) {
+        if (nv == kVFirstChunk || nv == q_variant_first(TB)) prefetch_twiddles<R, 0, TB>(nt, tid);
+        else if (nv >= 16 && nv != kVNop) dispatch_later_prefetch<R>(nv, nt, tid);
+      }
+    }
+    q.end(j, it);
   }
   q.finish();
 }
@@ -422,21 +457,21 @@ int queue_grid_f64();
 template <class R>
 int queue_grid() {
   auto fn = k_queue<R>;
-  if (ensure_smem(reinterpret_cast<const void*>(fn), int(kLevelSmem)) != SDFT_OK) return 0;
+  if (ensure_smem(reinterpret_cast<const void*>(fn), int(kQueueSmem)) != SDFT_OK) return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, KT<R>::NT, kLevelSmem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, KT<R>::NT, kQueueSmem) != cudaSuccess) return 0;
   return per_sm * sm_count();
 }
 
 template <class R>
 sdft_status launch_queue(const QParams& prm, int grid, cudaStream_t st) {
   auto fn = k_queue<R>;
-  sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(kLevelSmem));
+  sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(kQueueSmem));
   if (s != SDFT_OK) return s;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
   cfg.blockDim = dim3(KT<R>::NT);
-  cfg.dynamicSmemBytes = kLevelSmem;
+  cfg.dynamicSmemBytes = kQueueSmem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs resident: dependency waits make progress

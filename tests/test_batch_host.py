@@ -48,3 +48,15 @@ def test_host_only_batch_cannot_execute():
     with pytest.raises(SdftError) as ei:
         N.sdft_batch_execute(b.handle, 16, 16, None)
     assert ei.value.name == "SDFT_ERR_NO_DEVICE"
+
+
+def test_lane_schedule_invariants_full_uneven_workload():
+    # 10,000 instances give far more units than CTAs: the lane schedule is used
+    from paper_2211_15299_gb300 import Batch
+    insts = W.workload_uneven(count=10000)
+    plans = _plans(insts)
+    b = Batch(plans)
+    n_items, n_ctr, grid = b.stats()        # raises if a dependency is closer than 3 x grid
+    multi = sum(1 for p in plans if p.s > 12)
+    assert n_ctr == multi
+    assert n_items >= sum(max(1, p.k >> 12) for p in plans if p.s > 12)
