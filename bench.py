@@ -61,7 +61,7 @@ class ClockSampler:
         self.lines = []
 
     def __enter__(self):
-        if os.environ.get("CUDA_INJECTION64_PATH"):
+        if os.environ.get("CUDA_INJECTION64_PATH") or os.environ.get("SDFT_NO_CLOCKS"):
             return self          # under a profiler: do not poll the GPU through NVML
         try:
             self.proc = subprocess.Popen(

@@ -13,6 +13,7 @@
 // remain. Consecutive items go to consecutive CTAs, so list order is roughly
 // time order and the intermediate of a multi-level instance is read back from L2.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <functional>
@@ -283,7 +284,14 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
     uint64_t ready;
     size_t unit, stage;
   };
-  if (units.size() >= 2 * G) {
+  // SDFT_BATCH_SCHEDULE=rr|lanes overrides the choice (both satisfy the invariant).
+  static const int forced = [] {
+    const char* e = std::getenv("SDFT_BATCH_SCHEDULE");
+    if (!e) return 0;
+    return std::strcmp(e, "lanes") == 0 ? 1 : (std::strcmp(e, "rr") == 0 ? 2 : 0);
+  }();
+  const bool use_lanes = forced ? forced == 1 : units.size() >= 2 * G;
+  if (use_lanes) {
     // Lanes: a unit runs entirely in one CTA (its tables stay in registers and
     // L1, its intermediate in L2); units go to the least-loaded lane, largest
     // first, and a unit's next stage follows 3 lane positions after its last item.
