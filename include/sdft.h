@@ -160,7 +160,8 @@ sdft_status sdft_plan_autotune(sdft_plan plan, uint64_t batch, const void* d_sam
 /* Device status word of a plan: SDFT_OK, SDFT_ERR_TIMEOUT, or a launch
  * self-check code above 0xff (0x101: dynamic shared memory smaller than the
  * kernel's layout; 0x102: tensor-map parameter not 64-byte aligned; 0x103:
- * twiddle table not 16-byte aligned; the kernel did no work). Synchronises the
+ * twiddle table, or a batch's item list, not 16-byte aligned; the kernel did
+ * no work). Synchronises the
  * device; clears the word when `clear` is non-zero. */
 sdft_status sdft_plan_device_status(sdft_plan plan, int clear);
 

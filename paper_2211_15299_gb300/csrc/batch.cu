@@ -80,11 +80,13 @@ int log2u(uint64_t x) { return 63 - __builtin_clzll(x); }
 
 // Invariants of an item list: every dependency refers to a counter signalled
 // only by items earlier in the list, reaches its target exactly, and its last
-// producer sits at least 3 x grid positions back (then a CTA never waits on an
-// item whose store it has not yet published, and no two CTAs wait on each other).
+// producer sits at least 4 x grid positions back. A CTA publishes item j's
+// counter at the end of item j+2 and before the dependency wait of item j+4,
+// so then a CTA never waits on an item whose counter it has not yet
+// published, and no two CTAs wait on each other.
 sdft_status check_items(const Batch& B) {
   std::vector<uint64_t> sig_count(B.n_counters, 0), sig_last(B.n_counters, 0);
-  const uint64_t lag = 3ull * uint64_t(B.grid);
+  const uint64_t lag = 4ull * uint64_t(B.grid);
   for (uint64_t p = 0; p < B.items.size(); ++p) {
     const QItem& it = B.items[p];
     if (it.dep != kNone) {
@@ -230,6 +232,8 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
         it.sig = kNone;
         it.c1 = int32_t(row0);
         it.c3 = 0;
+        it.tw = insts[q].tw;
+        it.scale = insts[q].scale;
         units.push_back(Unit{{{it}}, cnt << s});
         q += cnt;
         left -= cnt;
@@ -252,6 +256,8 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
         it.sig = sig;
         it.c1 = int32_t(row0 + (ch << (TB - CB)));
         it.c3 = 0;
+        it.tw = insts[q].tw;
+        it.scale = insts[q].scale;
         u.stages[0].push_back(it);
       }
       uint32_t dep = sig, need = uint32_t(chunks);
@@ -270,9 +276,9 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
   }
   B.n_counters = n_ctr;
 
-  // Phase 2: order the items. Every dependency must sit at least 3 x grid list
+  // Phase 2: order the items. Every dependency must sit at least 4 x grid list
   // positions behind the item that waits on it (CTA c takes positions c, c + G,
-  // ...; a CTA issues item j's load after publishing item j - 3's store).
+  // ...; a CTA issues item j's load after publishing item j - 4's store).
   QItem nop{};
   nop.variant = uint16_t(kVNop);
   nop.dep = kNone;
@@ -294,7 +300,7 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
   if (use_lanes) {
     // Lanes: a unit runs entirely in one CTA (its tables stay in registers and
     // L1, its intermediate in L2); units go to the least-loaded lane, largest
-    // first, and a unit's next stage follows 3 lane positions after its last item.
+    // first, and a unit's next stage starts 4 lane positions after its last item.
     std::vector<size_t> by_cost(units.size());
     for (size_t u = 0; u < units.size(); ++u) by_cost[u] = u;
     std::stable_sort(by_cost.begin(), by_cost.end(),

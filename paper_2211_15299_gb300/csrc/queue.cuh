@@ -31,8 +31,9 @@ struct QItem {            // 48 bytes
   uint32_t need;          // value the counter must reach
   uint32_t sig;           // counter to increment once the item's store is complete, or kNone
   int32_t c1, c3;         // TMA coordinates of the tile
-  const void* tw;         // later levels: the group block's table, absolute-indexed
-  double scale;           // later levels: N/k of the instance
+  const void* tw;         // twiddle table, absolute-indexed: level 0 the (first) instance's
+                          // plan table, later levels the group block's table
+  double scale;           // N/k of the (first) instance
 };
 
 struct QInst {            // 32 bytes
@@ -57,14 +58,11 @@ struct QArgs {
   uint32_t need_bias;       // added to every dependency target (0; non-zero only to test timeouts)
 };
 
-// Item metadata resolved by the issuing thread when it starts the item's load
-// (two items ahead), kept in shared memory per tile buffer.
-struct QMeta {            // 64 bytes
-  QItem it;
-  const void* tab;        // the item's (first) twiddle table, absolute-indexed
-  double scale;           // N/k for the final stage
-};
-constexpr uint32_t kQueueSmem = kBufs * kTileBytes + 64 + kBufs * sizeof(QMeta) + 1024;
+// Item records are copied into a shared-memory ring kMetaSlots items ahead of
+// use, so the issuing thread never waits on a global load of a record.
+constexpr int kMetaSlots = 6;
+static_assert(sizeof(QItem) % 16 == 0, "items are copied in 16-byte pieces");
+constexpr uint32_t kQueueSmem = kBufs * kTileBytes + 64 + kMetaSlots * sizeof(QItem) + 1024;
 
 // Kernel parameters: the arguments and the tensor maps over the packed buffers
 // (maps in parameter space are baked into a captured CUDA graph).
@@ -221,7 +219,7 @@ struct QPipe {
   uint64_t c, G, n;
   uint32_t phases = 0;        // bit b: parity of the next completion of buffer b
   uint32_t inflight = 0;      // thread 0: buffers with an issued, unconsumed load
-  uint32_t pending_sig = kNone;
+  uint32_t sig1 = kNone, sig2 = kNone;   // signals of items j-1 and j-2, not yet published
   bool failed = false;        // thread 0: a dependency wait expired
   bool aborted = false;
 
@@ -229,27 +227,28 @@ struct QPipe {
       : prm(p), smem(sm), bar0(b0), tid(t), c(blockIdx.x), G(gridDim.x) {
     n = (p.a.n_items > c) ? (p.a.n_items - c + G - 1) / G : 0;
   }
-  __device__ __forceinline__ const QItem& item(uint64_t j) const { return prm.a.items[c + j * G]; }
   __device__ __forceinline__ static bool is_tma(const QItem& it) { return it.variant != kVSmall && it.variant != kVNop; }
 
-  __device__ __forceinline__ QMeta& meta(uint64_t j) const {
-    return reinterpret_cast<QMeta*>(smem + kBufs * kTileBytes + 64)[j % kBufs];
+  // Record of item j in the ring; valid for all threads once thread 0 has
+  // waited for its copy and a barrier has passed.
+  __device__ __forceinline__ const QItem& meta(uint64_t j) const {
+    return reinterpret_cast<const QItem*>(smem + kBufs * kTileBytes + 64)[j % kMetaSlots];
   }
 
-  __device__ __forceinline__ void issue_load(uint64_t j) {   // thread 0
-    const QItem& it = item(j);
-    QMeta& m = meta(j);             // read by all threads once a barrier has passed
-    m.it = it;
-    if (it.variant >= 16 && it.variant != kVNop) {
-      m.tab = it.tw;
-      m.scale = it.scale;
-    } else if (it.variant != kVNop && it.variant != kVSmall) {
-      m.tab = prm.a.insts[it.inst].tw;
-      m.scale = prm.a.insts[it.inst].scale;
-    } else {
-      m.tab = nullptr;
-      m.scale = 0.0;
+  // Thread 0: start copying item j's record into its ring slot (one cp.async
+  // group per call, empty past the end of the CTA's items).
+  __device__ __forceinline__ void fetch_record(uint64_t j) const {
+    if (j < n) {
+      const char* src = reinterpret_cast<const char*>(&prm.a.items[c + j * G]);
+      const uint32_t dst = ptx::smem_addr(&meta(j));
+#pragma unroll
+      for (uint32_t o = 0; o < sizeof(QItem); o += 16) ptx::cp_async_16(dst + o, src + o);
     }
+    ptx::cp_async_commit();
+  }
+
+  __device__ __forceinline__ void issue_load(uint64_t j) {   // thread 0; record j has landed
+    const QItem& it = meta(j);
     if (!is_tma(it)) return;
     if (it.dep != kNone) {
       const uint32_t* ctr = prm.a.counters + it.dep;
@@ -283,14 +282,12 @@ struct QPipe {
       const uint32_t first = 1u << (TB - Q);
       ptx::prefetch_l2(static_cast<const char*>(it.tw) + first * ES, ((1u << TB) - first) * ES);
     } else if (it.variant == kVFirstChunk) {
-      ptx::prefetch_l2(prm.a.insts[it.inst].tw, (1u << TB) * ES);
+      ptx::prefetch_l2(it.tw, (1u << TB) * ES);
     } else {                                       // whole instances of size 2^s
+      // The first instance's table here; the others' two items ahead, by the
+      // threads of warps 1.. (see the kernel loop).
       const int s = it.variant - 1 + 5;
-      const uint32_t cnt = it.count < 16u ? it.count : 16u;   // bound the work of the issuing thread
-      for (uint32_t g = 0; g < cnt; ++g) {
-        const void* tw = prm.a.insts[it.inst + g].tw;
-        if (tw) ptx::prefetch_l2(tw, (1u << s) * ES);
-      }
+      ptx::prefetch_l2(it.tw, (1u << s) * ES);
     }
   }
 
@@ -312,27 +309,37 @@ struct QPipe {
     return true;
   }
 
-  // After item j's compute: store, publish the previous store, prefetch j + 2.
+  // After item j's compute: store it, publish item j-2, prefetch item j + 2.
+  // Every item commits one bulk group (empty if it stores nothing), so group g
+  // is item g. A counter is released two items after its store was issued,
+  // once that store is complete; the buffer of item j-1 is reused as soon as
+  // its store has read shared memory. A consumer therefore sits at least four
+  // items after its producer in the producing CTA (4 x grid list positions).
   __device__ __forceinline__ void end(uint64_t j, const QItem& it) {
     if (tid != 0) return;
-    bool stored = false;
     if (is_tma(it)) {
       const uint32_t slot = (it.variant < 16) ? uint32_t(it.map) + 1u : uint32_t(it.map);
       ptx::tma_store_4d(&prm.maps[slot], ptx::smem_addr(smem + (j % kBufs) * kTileBytes), 0, it.c1, 0, it.c3);
-      ptx::bulk_commit();
-      stored = true;
     }
-    if (stored) ptx::bulk_wait<1>(); else ptx::bulk_wait<0>();
-    if (pending_sig != kNone) {          // the previous store is complete: publish it
+    ptx::bulk_commit();
+    if (sig2 != kNone) {                 // store of item j-2 complete: publish it
+      ptx::bulk_wait<2>();
       ptx::fence_proxy_async_global();
-      ptx::red_add_release_gpu(prm.a.counters + pending_sig, 1u);
+      ptx::red_add_release_gpu(prm.a.counters + sig2, 1u);
     }
-    pending_sig = stored ? it.sig : kNone;
-    if (j >= 1 && j + 2 < n) issue_load(j + 2);   // into the buffer of item j-1, drained above
+    sig2 = sig1;
+    sig1 = is_tma(it) ? it.sig : kNone;
+    ptx::cp_async_wait<2>();             // records up to j + 3 have landed
+    if (j >= 1 && j + 2 < n) {           // into the buffer of item j-1
+      ptx::bulk_wait_read<1>();
+      issue_load(j + 2);
+    }
+    fetch_record(j + kMetaSlots);        // into the slot of item j, read by all threads already
   }
 
   __device__ __forceinline__ void finish() {
     if (tid != 0) return;
+    ptx::cp_async_wait<0>();
     if (aborted || failed) {
       // Let loads already issued land before the CTA's shared memory is released.
       for (int b = 0; b < kBufs; ++b)
@@ -340,9 +347,10 @@ struct QPipe {
       atomicExch(prm.a.status, int(SDFT_ERR_TIMEOUT));
     }
     ptx::bulk_wait<0>();
-    if (!aborted && pending_sig != kNone) {
+    if (!aborted) {
       ptx::fence_proxy_async_global();
-      ptx::red_add_release_gpu(prm.a.counters + pending_sig, 1u);
+      if (sig2 != kNone) ptx::red_add_release_gpu(prm.a.counters + sig2, 1u);
+      if (sig1 != kNone) ptx::red_add_release_gpu(prm.a.counters + sig1, 1u);
     }
   }
 };
@@ -389,10 +397,11 @@ __global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ 
   const uint32_t bar0 = ptx::smem_addr(smem + kBufs * kTileBytes);
   const uint32_t tid = threadIdx.x;
   {
-    const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 64 + kBufs * uint32_t(sizeof(QMeta));
+    const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 64 + kMetaSlots * uint32_t(sizeof(QItem));
     int bad = 0;
     if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
     else if (reinterpret_cast<uintptr_t>(&prm.maps[0]) & 63u) bad = kBadMap;
+    else if (reinterpret_cast<uintptr_t>(a.items) & 15u) bad = kBadTable;
     if (bad) {
       if (tid == 0) atomicCAS(a.status, 0, bad);
       return;
@@ -403,17 +412,18 @@ __global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ 
   if (tid == 0) {
     for (int b = 0; b < kBufs; ++b) ptx::mbar_init(bar0 + 8 * b, 1);
     ptx::fence_mbar_init();
+    for (int j = 0; j < kMetaSlots; ++j) q.fetch_record(uint64_t(j));
+    ptx::cp_async_wait<kMetaSlots - kBufs>();     // records 0 .. kBufs-1
     for (uint64_t j = 0; j < q.n && j < uint64_t(kBufs); ++j) q.issue_load(j);
   }
   __syncthreads();
   using C = typename KT<R>::C;
   constexpr int TB = KT<R>::TB;
   for (uint64_t j = 0; j < q.n; ++j) {
-    const QMeta& m = q.meta(j);
-    const QItem it = m.it;
+    const QItem it = q.meta(j);
     const int v = it.variant;
-    const C* tab = static_cast<const C*>(m.tab);
-    const R sc = R(m.scale);
+    const C* tab = static_cast<const C*>(it.tw);
+    const R sc = R(it.scale);
     if (!q.begin(j, it)) break;
     char* buf = smem + (j % kBufs) * kTileBytes;
     if (v == kVNop) {
@@ -430,12 +440,20 @@ __global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ 
       dispatch_first_q<R>(v, buf, a, it, tid);   // several instances per tile
     }
     if (j + 1 < q.n) {   // the next item's register and L1 twiddles, while this store drains
-      const QMeta& nx = q.meta(j + 1);
-      const int nv = nx.it.variant;
-      const C* nt = static_cast<const C*>(nx.tab);
+      const QItem& nx = q.meta(j + 1);
+      const int nv = nx.variant;
+      const C* nt = static_cast<const C*>(nx.tw);
       if (nt && nt != tab) {
         if (nv == kVFirstChunk || nv == q_variant_first(TB)) prefetch_twiddles<R, 0, TB>(nt, tid);
         else if (nv >= 16 && nv != kVNop) dispatch_later_prefetch<R>(nv, nt, tid);
+      }
+    }
+    if (j + 2 < q.n && tid >= 32) {   // tables of a multi-instance tile two items ahead, into L2
+      const QItem& n2 = q.meta(j + 2);
+      const uint32_t g = tid - 32;
+      if (n2.variant >= 1 && n2.variant < q_variant_first(TB) && g < n2.count) {
+        const void* t2 = a.insts[n2.inst + g].tw;
+        if (t2) ptx::prefetch_l2(t2, (1u << (n2.variant - 1 + 5)) * KT<R>::ES);
       }
     }
     q.end(j, it);

@@ -285,6 +285,8 @@ sdft_status build_items(Server& S, Slot& sl, size_t& n_items, uint32_t& n_ctr) {
       it.dep = kNone;
       it.sig = kNone;
       it.c1 = int32_t(row0);
+      it.tw = sl.h_insts[i].tw;
+      it.scale = sl.h_insts[i].scale;
       sdft_status s = emit(it);
       if (s != SDFT_OK) return s;
     } else {
@@ -299,6 +301,8 @@ sdft_status build_items(Server& S, Slot& sl, size_t& n_items, uint32_t& n_ctr) {
         it.dep = kNone;
         it.sig = sig;
         it.c1 = int32_t(row0 + (ch << (TB - CB)));
+        it.tw = sl.h_insts[i].tw;
+        it.scale = sl.h_insts[i].scale;
         sdft_status s = emit(it);
         if (s != SDFT_OK) return s;
       }

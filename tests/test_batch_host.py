@@ -56,7 +56,7 @@ def test_lane_schedule_invariants_full_uneven_workload():
     insts = W.workload_uneven(count=10000)
     plans = _plans(insts)
     b = Batch(plans)
-    n_items, n_ctr, grid = b.stats()        # raises if a dependency is closer than 3 x grid
+    n_items, n_ctr, grid = b.stats()        # raises if a dependency is closer than 4 x grid
     multi = sum(1 for p in plans if p.s > 12)
     assert n_ctr == multi
     assert n_items >= sum(max(1, p.k >> 12) for p in plans if p.s > 12)
