@@ -221,6 +221,18 @@ def run_ours(args):
 
     tpi = time_device_steps(step64_per_instance, 3, 1, flush, stream)
     fp64_per_instance = n_pi * k / statistics.mean(tpi)
+    # context only: a library batched k-point C2C FFT (cuFFT through torch.fft)
+    # over the same batch moves the same bytes with a regular twiddle pattern
+    yfft = torch.empty_like(x32)
+
+    def step_fft():
+        torch.fft.fft(x32, dim=1, out=yfft)
+
+    tf = time_device_steps(step_fft, max(3, args.steps // 4), 3, flush, stream)
+    fft_ceiling = {"what": f"torch.fft.fft batch {batch} x {k} complex64 (cuFFT library call)",
+                   "coeffs_per_s": coeffs_per_step / statistics.mean(tf),
+                   "GB_per_s": 16 * coeffs_per_step / statistics.mean(tf) / 1e9}
+    del yfft
     # accuracy of the FP32 path against the FP64 path on the same input
     step()
     step64()
@@ -269,6 +281,7 @@ def run_ours(args):
         "fp64": {"batched_coeffs_per_s": fp64_batched, "per_instance_coeffs_per_s": fp64_per_instance,
                  "per_instance_sample": n_pi, "fp32_speedup_vs_per_instance": value / ws / fp64_per_instance},
         "rel_l2_fp32_vs_fp64": rel_fp32_vs_fp64,
+        "fft_ceiling": fft_ceiling,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }

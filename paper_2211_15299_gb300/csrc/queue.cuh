@@ -268,7 +268,9 @@ struct QPipe {
     const uint32_t bar = bar0 + 8 * b;
     const uint32_t bytes = (it.variant < 16) ? (128u << (it.map / 2)) : kTileBytes;
     ptx::mbar_arrive_expect_tx(bar, bytes);
-    ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], bar, 0, it.c1, 0, it.c3);
+    // Samples and intermediates are read once: first out of L2.
+    ptx::tma_load_4d_hint(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], bar, 0, it.c1, 0, it.c3,
+                          ptx::policy_evict_first());
     inflight |= 1u << b;
     prefetch_tables(it);
   }
@@ -319,7 +321,11 @@ struct QPipe {
     if (tid != 0) return;
     if (is_tma(it)) {
       const uint32_t slot = (it.variant < 16) ? uint32_t(it.map) + 1u : uint32_t(it.map);
-      ptx::tma_store_4d(&prm.maps[slot], ptx::smem_addr(smem + (j % kBufs) * kTileBytes), 0, it.c1, 0, it.c3);
+      // An intermediate (a later level reads it back) stays in L2 ahead of
+      // streaming data; a final result leaves first.
+      const uint64_t pol = (it.sig != kNone) ? ptx::policy_evict_last() : ptx::policy_evict_first();
+      ptx::tma_store_4d_hint(&prm.maps[slot], ptx::smem_addr(smem + (j % kBufs) * kTileBytes), 0, it.c1, 0, it.c3,
+                             pol);
     }
     ptx::bulk_commit();
     if (sig2 != kNone) {                 // store of item j-2 complete: publish it
