@@ -257,7 +257,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(inst, x32, y32, args.cpu_sample)
+        cpu = cpu_baseline(inst, x32, y32, min(args.cpu_sample, batch))
     extra = {}
     if not args.no_extra:
         del x64, y64, h_in, h_out, d_in, d_out
@@ -372,6 +372,12 @@ def run_uneven(args):
     x = torch.randn(b.total, dtype=torch.complex64, device=dev, generator=g)
     y = torch.empty_like(x)
 
+    # autotune the queue shape (item order x CTAs) on these buffers, then capture
+    t0 = time.perf_counter()
+    schedule, grid, ms_tuned = b.autotune(x, y, reps=3)
+    t_tune = time.perf_counter() - t0
+    n_items, n_ctr, grid = b.stats()
+
     def step(s=None):
         b.execute(x, y, stream=(s or stream).cuda_stream)
 
@@ -383,16 +389,16 @@ def run_uneven(args):
             "ms_per_step": 1e3 * mean, "alg_GBps": (16 * total + tw_bytes) / mean / 1e9,
             "alg_bytes_per_step": 16 * total + tw_bytes, "work_items": n_items,
             "dependency_counters": n_ctr, "grid": grid, "plan_build_s": t_plan,
-            "launches_per_step": 1}
+            "autotune": {"schedule": schedule, "grid": grid, "ms_per_run": ms_tuned, "seconds": t_tune},
+            "launches_per_step": 1, "graph": "one CUDA graph replay per step"}
 
 
 def run_serving(args):
     """Serving leg: Poisson arrivals (rate, duration) of requests whose supports have
     N in 2^10..2^26 and k in 2^4..2^18; 80% reuse one of 256 resident plans, 20% bring
-    a new support whose plan is built on arrival (by a pool of planner threads, the
+    a new support planned on arrival by the engine's own planner threads (the
     planning time counting in the latency); samples start in pinned host memory;
     a device-memory admission budget bounds the requests in flight."""
-    import concurrent.futures as cf
     import threading as th
     import torch
     from paper_2211_15299_gb300 import Plan, Server, _native as N
@@ -418,40 +424,37 @@ def run_serving(args):
                 return lst.pop()
         return pinned(1 << s), torch.empty(1 << s, dtype=torch.complex64).pin_memory()
 
-    srv = Server("c64", budget_bytes=args.serve_budget << 20, n_slots=2, max_batch=args.serve_batch)
+    # fresh supports are planned by the engine's own planner threads (deferred
+    # plans: tables built on the host, uploaded into the arena with the request)
+    srv = Server("c64", budget_bytes=args.serve_budget << 20, n_slots=2, max_batch=args.serve_batch,
+                 n_planners=args.serve_planners)
     h = srv.handle
     arrival = np.zeros(n_req)
     submit_t = np.zeros(n_req)
     fresh_bufs = {}
-    fresh_plans = {}
-    planner = cf.ThreadPoolExecutor(max_workers=args.serve_planners)
-
-    def fresh(r, inst, t_arr):
-        # ctypes drops the GIL, so plans build in parallel; the device tables stay on the
-        # host until the server uploads them into its arena with the request
-        plan = Plan(inst.M, inst.J, "c64", defer=True)
-        bi, bo = take(plan.s)
-        fresh_bufs[r] = (bi, bo)
-        fresh_plans[r] = plan
-        submit_t[r] = time.perf_counter()
-        N.sdft_server_submit(h, plan.handle, bi.data_ptr(), bo.data_ptr(), r)
+    fresh_s = {}
+    fresh_J = {pid: np.ascontiguousarray(np.asarray(trace.plans[pid].J, dtype=np.uint64))
+               for pid in set(int(p) for p in trace.plan_ids if p >= 256)}
 
     lat = np.zeros(n_req)
     done = np.zeros(n_req, dtype=bool)
     status = np.zeros(n_req, dtype=np.int32)
     stop = th.Event()
 
+    lat_srv = np.zeros(n_req)
+
     def poller():
         while not stop.is_set() or not done.all():
             tags, l, st = N.sdft_server_poll(h, 8192)
             for t, li, si in zip(tags, l, st):
                 t = int(t)
+                lat_srv[t] = li
                 lat[t] = li + (submit_t[t] - arrival[t])
                 status[t] = si
                 done[t] = True
                 if t in fresh_bufs:
                     with pool_mu:
-                        pool.setdefault(fresh_plans[t].s, []).append(fresh_bufs.pop(t))
+                        pool.setdefault(fresh_s.pop(t), []).append(fresh_bufs.pop(t))
             if not len(tags):
                 time.sleep(0.0002)
             if stop.is_set() and time.perf_counter() > deadline:
@@ -461,7 +464,6 @@ def run_serving(args):
     pt = th.Thread(target=poller, daemon=True)
     pt.start()
     start = time.perf_counter() + 0.05
-    futures = []
     for r in range(n_req):
         t_arr = start + trace.arrivals[r]
         arrival[r] = t_arr
@@ -476,15 +478,18 @@ def run_serving(args):
             submit_t[r] = time.perf_counter()
             N.sdft_server_submit(h, resident[pid].handle, res_in[pid].data_ptr(), res_out[pid].data_ptr(), r)
         else:
-            futures.append(planner.submit(fresh, r, trace.plans[pid], t_arr))
-    for f in futures:
-        f.result()
+            inst = trace.plans[pid]
+            s_ = int(inst.s)
+            bi, bo = take(s_)
+            fresh_bufs[r] = (bi, bo)
+            fresh_s[r] = s_
+            submit_t[r] = time.perf_counter()
+            N.sdft_server_submit_support(h, inst.M, fresh_J[pid], bi.data_ptr(), bo.data_ptr(), r)
     srv.drain(timeout_ms=600_000)
     end = time.perf_counter()
     deadline = end + 5.0
     stop.set()
     pt.join(timeout=10)
-    planner.shutdown()
     st = srv.stats()
     ok = status == 0
     ks = np.array([(resident[int(p)].k if p < 256 else (1 << trace.plans[int(p)].s)) for p in trace.plan_ids])
@@ -493,8 +498,15 @@ def run_serving(args):
     split = {}
     for name, sel in (("resident", ok & ~is_fresh), ("fresh", ok & is_fresh)):
         if sel.any():
+            pre = submit_t[sel] - arrival[sel]
             split[name] = {"p50_ms": float(np.percentile(lat[sel], 50) * 1e3),
-                           "p99_ms": float(np.percentile(lat[sel], 99) * 1e3), "count": int(sel.sum())}
+                           "p99_ms": float(np.percentile(lat[sel], 99) * 1e3), "count": int(sel.sum()),
+                           # arrival -> submit (client dispatch, and planning for fresh supports)
+                           "client_p50_ms": float(np.percentile(pre, 50) * 1e3),
+                           "client_p99_ms": float(np.percentile(pre, 99) * 1e3),
+                           # submit -> completion stamp inside the server
+                           "server_p50_ms": float(np.percentile(lat_srv[sel], 50) * 1e3),
+                           "server_p99_ms": float(np.percentile(lat_srv[sel], 99) * 1e3)}
     out = {"requests": n_req, "offered_rate": args.serve_rate, "seconds": args.serve_seconds,
            "by_kind": split,
            "completed": int(done.sum()), "failed": int((~ok).sum()),
@@ -502,7 +514,8 @@ def run_serving(args):
            "p99_ms": float(np.percentile(lat[ok], 99) * 1e3) if ok.any() else None,
            "mean_ms": float(lat[ok].mean() * 1e3) if ok.any() else None,
            "coeffs_per_s": float(ks[ok].sum() / wall), "achieved_rate": float(ok.sum() / wall),
-           "fresh_plans": int(sum(1 for p in trace.plan_ids if p >= 256)),
+           "fresh_plans": int(sum(1 for p in trace.plan_ids if p >= 256)), "planned_by_server": st["planned"],
+           "planner_threads": args.serve_planners,
            "micro_batches": st["micro_batches"], "max_inflight": st["max_inflight"],
            "arena_peak_MiB": st["arena_peak_bytes"] / 2**20, "budget_MiB": args.serve_budget,
            "resident_plan_build_s": t_resident, "device_status": srv.device_status()}
@@ -521,9 +534,19 @@ def cpu_baseline(inst, x32, y32, sample):
     dt = time.perf_counter() - t0
     got = y32[:sample].cpu().numpy().astype(np.complex128)
     rel = float(np.linalg.norm(got - C) / np.linalg.norm(C))
+    # the oracle's Algorithm 1 (unrolled by levels, numpy, vectorised over instances)
+    # on the whole batch: the O(k log k) CPU method beside the dense definition
+    Fa = x32.cpu().numpy().astype(np.complex128)
+    t0 = time.perf_counter()
+    Ca = O.transform_levels(inst.M, inst.pivots, Jc, Fa)
+    da = time.perf_counter() - t0
+    rel_a = float(np.linalg.norm(y32.cpu().numpy().astype(np.complex128) - Ca) / np.linalg.norm(Ca))
     return {"value": sample * inst.k / dt, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
             "sample": f"{sample} of the batch's instances, dense k x k LU solve (one factorisation)",
-            "seconds": dt, "rel_l2_gpu_fp32_vs_oracle": rel}
+            "seconds": dt, "rel_l2_gpu_fp32_vs_oracle": rel,
+            "alg1": {"value": Fa.shape[0] * inst.k / da, "unit": UNIT, "kind": "oracle",
+                     "sample": f"all {Fa.shape[0]} instances, Algorithm 1 by levels (numpy FP64, one thread)",
+                     "seconds": da, "rel_l2_gpu_fp32_vs_oracle": rel_a}}
 
 
 def _blas_threads():
@@ -544,7 +567,7 @@ def run_reference(args):
     rng = W.rng_for(2, 555)
     Jc = O.canonical_support_by_key(inst.J, inst.pivots)
     I = O.sample_set(inst.M, inst.pivots)
-    sample = args.cpu_sample
+    sample = args.ref_sample
     F = W.complex_gaussian((sample, inst.k), rng)
     for _ in range(max(1, min(args.warmup, 1))):
         O.solve(M, Jc, I, F[:8])
@@ -576,19 +599,22 @@ def main():
     ap.add_argument("--log2n", type=int, default=20)
     ap.add_argument("--log2k", type=int, default=12)
     ap.add_argument("--batch", type=int, default=4096)
-    ap.add_argument("--cpu-sample", type=int, default=256)
+    ap.add_argument("--cpu-sample", type=int, default=4096,
+                    help="instances in the oracle dense-solve baseline (at most the batch; about 10 s of CPU work)")
+    ap.add_argument("--ref-sample", type=int, default=256, help="instances per step of --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only-fp32", action="store_true", help="time the complex64 leg only (profiling)")
     ap.add_argument("--large", action="store_true", help="time only the large-k leg (N=2^30, k=2^20)")
     ap.add_argument("--large-batch", type=int, default=64)
     ap.add_argument("--uneven-count", type=int, default=10000)
+    ap.add_argument("--uneven", action="store_true", help="time only the uneven-batch leg")
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven, large-k and serving legs")
     ap.add_argument("--serve", action="store_true", help="run only the serving leg")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-budget", type=int, default=16384, help="admission budget, MiB")
     ap.add_argument("--serve-batch", type=int, default=64)
-    ap.add_argument("--serve-planners", type=int, default=12)
+    ap.add_argument("--serve-planners", type=int, default=8, help="the engine's planner threads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -598,6 +624,8 @@ def main():
         print(json.dumps({"large_k": run_large(args)}), flush=True)
     elif args.serve:
         print(json.dumps({"serving": run_serving(args)}), flush=True)
+    elif args.uneven:
+        print(json.dumps({"uneven": run_uneven(args)}), flush=True)
     else:
         run_ours(args)
 

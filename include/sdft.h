@@ -230,6 +230,35 @@ sdft_status sdft_batch_device_status(sdft_batch batch, int clear);
  * that path. */
 sdft_status sdft_batch_set_wait(sdft_batch batch, uint64_t timeout_ns, uint32_t need_bias);
 
+/* Order of a batch's work items (see sdft_batch_set_schedule). No paper
+ * counterpart: scheduling of many instances is a property of this library. */
+typedef enum {
+  SDFT_SCHEDULE_AUTO = 0,         /* lanes when there are at least 2 x grid units, else round robin */
+  SDFT_SCHEDULE_LANES = 1,        /* each instance's levels in one CTA, largest first to the least-loaded CTA */
+  SDFT_SCHEDULE_ROUND_ROBIN = 2   /* instances in packed order over consecutive CTAs */
+} sdft_schedule;
+
+/*
+ * sdft_batch_set_schedule - rebuild the batch's work queue with the given item
+ * order on `grid` CTAs (0: every co-resident CTA; larger values are clamped to
+ * that). Offsets, buffers and results do not change: every instance runs the
+ * same arithmetic in any order, so results are bit-identical. The device item
+ * list is reallocated: synchronise work using the batch first, and re-capture
+ * any CUDA graph holding it. SDFT_ERR_ARG for an unknown schedule.
+ */
+sdft_status sdft_batch_set_schedule(sdft_batch batch, sdft_schedule schedule, uint32_t grid);
+
+/*
+ * sdft_batch_autotune - time the batch under four queue shapes (lanes or round
+ * robin, on all co-resident CTAs or on half of them; one warm-up and `reps`
+ * timed runs each, CUDA events on `stream`, the buffers overwritten), keep the
+ * fastest and report it (any output may be NULL; `ms_best` is the mean time of
+ * one run). Synchronises `stream`. As for sdft_batch_set_schedule, graphs
+ * captured before must be re-captured.
+ */
+sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d_coeffs, void* stream, int reps,
+                                sdft_schedule* chosen, uint32_t* chosen_grid, float* ms_best);
+
 /* Work items, dependency counters and grid size (co-resident CTAs) of a batch;
  * returns SDFT_ERR_ARG if the item list breaks its ordering invariants (every
  * dependency target reached exactly, by items at least 4 x grid positions
@@ -256,6 +285,7 @@ typedef struct {
   uint64_t max_inflight;     /* largest `inflight` seen                          */
   uint64_t arena_bytes;      /* device arena (the admission budget)              */
   uint64_t arena_peak_bytes; /* largest arena use                                */
+  uint64_t planned;          /* supports planned by the server's planner threads */
 } sdft_server_stats;
 
 /*
@@ -267,10 +297,12 @@ typedef struct {
  * persistent work-queue launch on its own stream, sharing the co-resident CTAs.
  * A worker thread forms micro-batches in arrival order as slots and memory free
  * up (continuous batching). Plans stay owned by the caller and must outlive
- * their requests.
+ * their requests. `n_planners` threads (0..64) plan the supports submitted
+ * with sdft_server_submit_support. No paper counterpart: serving is a property
+ * of this library. SDFT_ERR_ARG for out-of-range arguments.
  */
 sdft_status sdft_server_create(sdft_prec prec, uint64_t budget_bytes, uint32_t n_slots, uint32_t max_batch,
-                               sdft_server* out);
+                               uint32_t n_planners, sdft_server* out);
 
 /* Queue one request: transform k = plan's k samples at h_samples into h_coeffs
  * (host buffers; pinned memory makes the copies asynchronous). The buffers must
@@ -278,9 +310,27 @@ sdft_status sdft_server_create(sdft_prec prec, uint64_t budget_bytes, uint32_t n
 sdft_status sdft_server_submit(sdft_server srv, sdft_plan plan, const void* h_samples, void* h_coeffs,
                                uint64_t tag);
 
+/*
+ * sdft_server_submit_support - queue one request that brings its support
+ * instead of a plan: J (k frequencies in [0, 2^log2N), copied during the call)
+ * is planned by one of the server's planner threads (as sdft_plan_create with
+ * SDFT_PLAN_DEFER_DEVICE: Definitions 8, 9 and the pivoted sampling pattern
+ * of Section VII), the request then enters the admission FIFO, and the plan is
+ * released when it completes. Planning time counts in the latency. h_samples
+ * holds f at the support's sample set I_r in sample order, h_coeffs receives
+ * the coefficients in the support's canonical order (the orders
+ * sdft_plan_sample_indices / sdft_plan_support_order report for a plan of the
+ * same J). A support that fails validation completes with that status
+ * (e.g. SDFT_ERR_NOT_HOMOGENEOUS). SDFT_ERR_UNSUPPORTED if the server has no
+ * planner threads. Buffers as for sdft_server_submit.
+ */
+sdft_status sdft_server_submit_support(sdft_server srv, uint32_t log2N, const uint64_t* J, uint64_t k,
+                                       const void* h_samples, void* h_coeffs, uint64_t tag);
+
 /* Up to `cap` completed requests since the last poll: tag, latency in seconds
- * (submit to the completion of the copy-out), status (SDFT_OK, or
- * SDFT_ERR_BUDGET when a request can never fit the arena). *n_out = count. */
+ * (submit to the completion of the copy-out), status (SDFT_OK; SDFT_ERR_BUDGET
+ * when a request can never fit the arena; a plan-creation status for a support
+ * that failed validation). *n_out = count. */
 sdft_status sdft_server_poll(sdft_server srv, uint64_t* tags, double* latency_s, int32_t* status, uint64_t cap,
                              uint64_t* n_out);
 

@@ -30,6 +30,7 @@ P_f64 = ctypes.POINTER(ctypes.c_double)
 
 SDFT_C64, SDFT_C128 = 0, 1
 SDFT_STRATEGY_LEVELS, SDFT_STRATEGY_QUEUE = 1, 2
+SDFT_SCHEDULE_AUTO, SDFT_SCHEDULE_LANES, SDFT_SCHEDULE_ROUND_ROBIN = 0, 1, 2
 SDFT_PLAN_HOST_ONLY = 0x1
 SDFT_PLAN_DEFER_DEVICE = 0x2
 
@@ -44,7 +45,7 @@ STATUS_CODE = {v: k for k, v in STATUS.items()}
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "submitted", "completed", "failed", "micro_batches", "coeffs", "inflight", "max_inflight",
-        "arena_bytes", "arena_peak_bytes")]
+        "arena_bytes", "arena_peak_bytes", "planned")]
 
 
 # Every symbol declared in include/sdft.h: name -> (restype, argtypes)
@@ -69,10 +70,14 @@ SIGNATURES = {
     "sdft_batch_execute_noalloc": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "sdft_batch_device_status": (c_int, [c_vp, c_int]),
     "sdft_batch_set_wait": (c_int, [c_vp, c_u64, c_u32]),
+    "sdft_batch_set_schedule": (c_int, [c_vp, c_int, c_u32]),
+    "sdft_batch_autotune": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, ctypes.POINTER(c_int), P_u32,
+                                    ctypes.POINTER(ctypes.c_float)]),
     "sdft_batch_stats": (c_int, [c_vp, P_u64, P_u64, ctypes.POINTER(c_int)]),
     "sdft_batch_destroy": (c_int, [c_vp]),
-    "sdft_server_create": (c_int, [c_int, c_u64, c_u32, c_u32, ctypes.POINTER(c_vp)]),
+    "sdft_server_create": (c_int, [c_int, c_u64, c_u32, c_u32, c_u32, ctypes.POINTER(c_vp)]),
     "sdft_server_submit": (c_int, [c_vp, c_vp, c_vp, c_vp, c_u64]),
+    "sdft_server_submit_support": (c_int, [c_vp, c_u32, P_u64, c_u64, c_vp, c_vp, c_u64]),
     "sdft_server_poll": (c_int, [c_vp, P_u64, P_f64, ctypes.POINTER(ctypes.c_int32), c_u64, P_u64]),
     "sdft_server_drain": (c_int, [c_vp, c_u64]),
     "sdft_server_get_stats": (c_int, [c_vp, ctypes.POINTER(ServerStats)]),
@@ -238,6 +243,18 @@ def sdft_batch_set_wait(batch: int, timeout_ns: int = 0, need_bias: int = 0) -> 
     _check(_lib.sdft_batch_set_wait(batch, int(timeout_ns), int(need_bias)), "sdft_batch_set_wait")
 
 
+def sdft_batch_set_schedule(batch: int, schedule: int = SDFT_SCHEDULE_AUTO, grid: int = 0) -> None:
+    _check(_lib.sdft_batch_set_schedule(batch, int(schedule), int(grid)), "sdft_batch_set_schedule")
+
+
+def sdft_batch_autotune(batch: int, d_samples, d_coeffs, stream=None, reps: int = 3):
+    """Returns (chosen schedule, chosen grid, ms per run of the chosen shape)."""
+    ch, g, ms = c_int(), c_u32(), ctypes.c_float()
+    _check(_lib.sdft_batch_autotune(batch, _ptr(d_samples), _ptr(d_coeffs), _stream(stream), int(reps),
+                                    ctypes.byref(ch), ctypes.byref(g), ctypes.byref(ms)), "sdft_batch_autotune")
+    return int(ch.value), int(g.value), float(ms.value)
+
+
 def sdft_batch_stats(batch: int):
     ni, nc, g = c_u64(), c_u64(), c_int()
     _check(_lib.sdft_batch_stats(batch, ctypes.byref(ni), ctypes.byref(nc), ctypes.byref(g)), "sdft_batch_stats")
@@ -248,15 +265,22 @@ def sdft_batch_destroy(batch: int) -> None:
     _check(_lib.sdft_batch_destroy(batch), "sdft_batch_destroy")
 
 
-def sdft_server_create(prec: int, budget_bytes: int, n_slots: int = 2, max_batch: int = 64) -> int:
+def sdft_server_create(prec: int, budget_bytes: int, n_slots: int = 2, max_batch: int = 64,
+                       n_planners: int = 4) -> int:
     out = c_vp()
-    _check(_lib.sdft_server_create(int(prec), int(budget_bytes), int(n_slots), int(max_batch), ctypes.byref(out)),
-           "sdft_server_create")
+    _check(_lib.sdft_server_create(int(prec), int(budget_bytes), int(n_slots), int(max_batch), int(n_planners),
+                                   ctypes.byref(out)), "sdft_server_create")
     return int(out.value)
 
 
 def sdft_server_submit(server: int, plan: int, h_samples, h_coeffs, tag: int) -> None:
     _check(_lib.sdft_server_submit(server, plan, _ptr(h_samples), _ptr(h_coeffs), int(tag)), "sdft_server_submit")
+
+
+def sdft_server_submit_support(server: int, log2N: int, J, h_samples, h_coeffs, tag: int) -> None:
+    Ja = np.ascontiguousarray(np.asarray(J, dtype=np.uint64))
+    _check(_lib.sdft_server_submit_support(server, int(log2N), Ja.ctypes.data_as(P_u64), int(Ja.size),
+                                           _ptr(h_samples), _ptr(h_coeffs), int(tag)), "sdft_server_submit_support")
 
 
 def sdft_server_poll(server: int, cap: int = 4096):

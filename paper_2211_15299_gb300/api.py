@@ -152,6 +152,24 @@ class Batch:
     def set_wait(self, timeout_ns: int = 0, need_bias: int = 0):
         N.sdft_batch_set_wait(self.handle, timeout_ns, need_bias)
 
+    _SCHEDULES = {"auto": N.SDFT_SCHEDULE_AUTO, "lanes": N.SDFT_SCHEDULE_LANES,
+                  "round_robin": N.SDFT_SCHEDULE_ROUND_ROBIN}
+
+    def set_schedule(self, schedule: str = "auto", grid: int = 0):
+        """Item order ("auto", "lanes", "round_robin") on `grid` CTAs (0: all co-resident)."""
+        N.sdft_batch_set_schedule(self.handle, self._SCHEDULES[schedule], grid)
+
+    def autotune(self, samples, coeffs=None, stream=None, reps: int = 3):
+        """Time the queue shapes on these buffers, keep the fastest; returns
+        (schedule name, grid, ms per run)."""
+        _check_tensor(samples, self.dtype, self.total, "samples")
+        if coeffs is None:
+            coeffs = _torch().empty_like(samples)
+        _check_tensor(coeffs, self.dtype, self.total, "coeffs")
+        ch, g, ms = N.sdft_batch_autotune(self.handle, samples, coeffs, _current_stream(stream), reps)
+        name = {v: k for k, v in self._SCHEDULES.items()}[ch]
+        return name, g, ms
+
     def pack(self, per_instance):
         """Host-side helper: place per-instance numpy arrays at their offsets."""
         out = np.zeros(self.total, dtype=np.complex128)
@@ -192,18 +210,27 @@ class Batch:
 class Server:
     """Continuous-batching serving engine (sdft_server_*).
 
-    Requests carry a Plan and pinned host tensors; the engine copies samples
-    in, runs micro-batches as persistent work-queue launches on a few streams,
-    copies coefficients out and reports per-request latency."""
+    Requests carry a Plan (or a support, planned by the engine's own planner
+    threads) and pinned host tensors; the engine copies samples in, runs
+    micro-batches as persistent work-queue launches on a few streams, copies
+    coefficients out and reports per-request latency."""
 
-    def __init__(self, prec="c64", budget_bytes: int = 1 << 30, n_slots: int = 2, max_batch: int = 64):
+    def __init__(self, prec="c64", budget_bytes: int = 1 << 30, n_slots: int = 2, max_batch: int = 64,
+                 n_planners: int = 4):
         self.prec = _PREC[prec] if isinstance(prec, str) else int(prec)
-        self.handle = N.sdft_server_create(self.prec, budget_bytes, n_slots, max_batch)
+        self.handle = N.sdft_server_create(self.prec, budget_bytes, n_slots, max_batch, n_planners)
         self._live = {}      # tag -> (plan, h_in, h_out) kept alive until completion
 
     def submit(self, plan: Plan, h_in, h_out, tag: int):
         self._live[int(tag)] = (plan, h_in, h_out)
         N.sdft_server_submit(self.handle, plan.handle, h_in, h_out, tag)
+
+    def submit_support(self, log2N: int, J, h_in, h_out, tag: int):
+        """A request with its own support: planned inside the engine; h_in holds
+        the samples at the support's sample set (sample order), h_out receives
+        the coefficients in canonical order."""
+        self._live[int(tag)] = (None, h_in, h_out)
+        N.sdft_server_submit_support(self.handle, log2N, J, h_in, h_out, tag)
 
     def poll(self, cap: int = 4096):
         tags, lat, st = N.sdft_server_poll(self.handle, cap)

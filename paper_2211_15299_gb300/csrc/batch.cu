@@ -13,7 +13,6 @@
 // remain. Consecutive items go to consecutive CTAs, so list order is roughly
 // time order and the intermediate of a multi-level instance is read back from L2.
 #include <algorithm>
-#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <functional>
@@ -54,6 +53,9 @@ struct Batch {
   uint64_t timeout_ns = 0;           // 0: library default
   uint32_t need_bias = 0;            // diagnostics: added to every dependency target
   int* d_status_shared = nullptr;    // if set, report into this word instead of d_status
+  std::vector<sdft_plan> plans;      // caller's order (the plans outlive the batch)
+  int schedule = SDFT_SCHEDULE_AUTO; // item order (sdft_schedule)
+  int grid_req = 0;                  // CTAs requested (0: every co-resident CTA)
 };
 
 }  // namespace sdft
@@ -115,8 +117,10 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
   if (B.device >= 0) {
     B.grid = prec == SDFT_C64 ? queue_grid_f32() : queue_grid_f64();
     if (B.grid <= 0) return SDFT_ERR_CUDA;
+    if (B.grid_req > 0 && B.grid_req < B.grid) B.grid = B.grid_req;
   } else {
     B.grid = kHostOnlyGrid;     // host-only batches: item list for inspection only
+    if (B.grid_req > 0 && B.grid_req < B.grid) B.grid = B.grid_req;
   }
 
   // Pack by decreasing k (stable).
@@ -285,18 +289,15 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
   nop.sig = kNone;
   std::vector<QItem>& items = B.items;
   items.clear();
+  items.clear();
   const uint64_t G = uint64_t(B.grid);
   struct Pending {
     uint64_t ready;
     size_t unit, stage;
   };
-  // SDFT_BATCH_SCHEDULE=rr|lanes overrides the choice (both satisfy the invariant).
-  static const int forced = [] {
-    const char* e = std::getenv("SDFT_BATCH_SCHEDULE");
-    if (!e) return 0;
-    return std::strcmp(e, "lanes") == 0 ? 1 : (std::strcmp(e, "rr") == 0 ? 2 : 0);
-  }();
-  const bool use_lanes = forced ? forced == 1 : units.size() >= 2 * G;
+  // The batch's schedule setting overrides the default (both satisfy the invariant).
+  const bool use_lanes = B.schedule == SDFT_SCHEDULE_AUTO ? units.size() >= 2 * G
+                                                          : B.schedule == SDFT_SCHEDULE_LANES;
   if (use_lanes) {
     // Lanes: a unit runs entirely in one CTA (its tables stay in registers and
     // L1, its intermediate in L2); units go to the least-loaded lane, largest
@@ -598,6 +599,7 @@ sdft_status sdft_batch_create(const sdft_plan* plans, uint64_t n, sdft_batch* ou
   h->b.device = dev;
   sdft_status s;
   try {
+    h->b.plans.assign(plans, plans + n);
     s = sdft::build_batch(h->b, plans, n);
   } catch (const std::bad_alloc&) {
     s = SDFT_ERR_NOMEM;
@@ -654,6 +656,86 @@ sdft_status sdft_batch_stats(sdft_batch batch, uint64_t* n_items, uint64_t* n_co
   if (n_counters) *n_counters = batch->b.n_counters;
   if (grid) *grid = batch->b.grid;
   return sdft::check_items(batch->b);
+}
+
+// Rebuild the item list and device arrays with the batch's current schedule
+// and grid settings (offsets and tensor maps do not change).
+static sdft_status rebuild_batch(sdft::Batch& B) {
+  sdft::free_batch(B);
+  try {
+    return sdft::build_batch(B, B.plans.data(), B.n);
+  } catch (const std::bad_alloc&) {
+    return SDFT_ERR_NOMEM;
+  }
+}
+
+sdft_status sdft_batch_set_schedule(sdft_batch batch, sdft_schedule schedule, uint32_t grid) {
+  if (!batch) return SDFT_ERR_ARG;
+  if (schedule != SDFT_SCHEDULE_AUTO && schedule != SDFT_SCHEDULE_LANES && schedule != SDFT_SCHEDULE_ROUND_ROBIN)
+    return SDFT_ERR_ARG;
+  if (grid > (1u << 20)) return SDFT_ERR_ARG;
+  sdft::Batch& B = batch->b;
+  if (B.schedule == int(schedule) && B.grid_req == int(grid) && B.d_items) return SDFT_OK;
+  B.schedule = int(schedule);
+  B.grid_req = int(grid);
+  return rebuild_batch(B);
+}
+
+sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d_coeffs, void* stream, int reps,
+                                sdft_schedule* chosen, uint32_t* chosen_grid, float* ms_best) {
+  if (!batch || reps <= 0) return SDFT_ERR_ARG;
+  sdft::Batch& B = batch->b;
+  if (B.device < 0) return SDFT_ERR_NO_DEVICE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int full = B.prec == SDFT_C64 ? sdft::queue_grid_f32() : sdft::queue_grid_f64();
+  if (full <= 0) return SDFT_ERR_CUDA;
+  struct Cand {
+    int schedule, grid;
+  };
+  // Item order x CTAs: every co-resident CTA, or half of them (fewer
+  // intermediates in flight, more L1 per resident CTA).
+  const Cand cands[4] = {{SDFT_SCHEDULE_LANES, 0},
+                         {SDFT_SCHEDULE_ROUND_ROBIN, 0},
+                         {SDFT_SCHEDULE_LANES, full / 2},
+                         {SDFT_SCHEDULE_ROUND_ROBIN, full / 2}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return sdft::cuda_fail(e);
+  }
+  sdft_status s = SDFT_OK;
+  float best = -1.f;
+  Cand pick = cands[0];
+  for (const Cand& c : cands) {
+    s = sdft_batch_set_schedule(batch, sdft_schedule(c.schedule), uint32_t(c.grid));
+    if (s != SDFT_OK) break;
+    s = sdft::run_batch(B, d_samples, d_coeffs, st);     // warm-up
+    if (s != SDFT_OK) break;
+    e = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && s == SDFT_OK && e == cudaSuccess; ++r) s = sdft::run_batch(B, d_samples, d_coeffs, st);
+    if (s == SDFT_OK && e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (s == SDFT_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (s == SDFT_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess && s == SDFT_OK) s = sdft::cuda_fail(e);
+    if (s != SDFT_OK) break;
+    ms /= float(reps);
+    if (best < 0.f || ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != SDFT_OK) return s;
+  s = sdft_batch_set_schedule(batch, sdft_schedule(pick.schedule), uint32_t(pick.grid));
+  if (s != SDFT_OK) return s;
+  if (chosen) *chosen = sdft_schedule(pick.schedule);
+  if (chosen_grid) *chosen_grid = uint32_t(B.grid);
+  if (ms_best) *ms_best = best;
+  return SDFT_OK;
 }
 
 sdft_status sdft_batch_destroy(sdft_batch batch) {

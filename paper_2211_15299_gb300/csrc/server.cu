@@ -10,7 +10,11 @@
 // callback stamps the completion. Requests that arrive while slots are busy are
 // admitted as soon as a slot and memory free up, and the launches of different
 // slots overlap on the device (each slot's grid is its share of the co-resident
-// CTAs, so in-flight launches never wait on each other).
+// CTAs, so in-flight launches never wait on each other). Requests that bring a
+// support instead of a plan are planned by the server's own planner threads
+// (a deferred plan: tables built in host memory, uploaded into the arena with
+// the request) and enter the FIFO once planned; the plan is released when the
+// request completes.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -93,6 +97,16 @@ struct Req {
   uint64_t tw_off = 0;        // arena block of a deferred plan's tables
   uint32_t tw_order = 0;
   bool own_tw = false;
+  sdft_plan own_plan = nullptr;   // planned by the server for this request
+};
+
+struct PlanJob {
+  uint64_t tag;
+  uint32_t M;
+  std::vector<uint64_t> J;
+  const void* h_in;
+  void* h_out;
+  Clock::time_point t_submit;
 };
 
 struct Done {
@@ -138,6 +152,11 @@ struct Server {
   std::thread worker;
   bool stop = false;
   sdft_status worker_error = SDFT_OK;
+  // planner pool for requests that bring their own support
+  std::vector<std::thread> planners;
+  std::deque<PlanJob> plan_jobs;
+  std::condition_variable plan_cv;
+  uint64_t planning = 0;         // jobs queued or being planned
 };
 
 namespace {
@@ -384,13 +403,14 @@ void worker_loop(Server* S) {
         S->done.push_back(Done{r.tag, lat, int32_t(SDFT_OK)});
         ++S->stats.completed;
         S->stats.coeffs += r.plan->k;
+        if (r.own_plan) sdft_plan_destroy(r.own_plan);   // host tables only: no device work
       }
       S->stats.inflight -= sl->reqs.size();
       sl->reqs.clear();
       sl->busy = false;
       progressed = true;
     }
-    if (S->stop && S->waiting.empty()) {
+    if (S->stop && S->waiting.empty() && S->planning == 0) {
       bool idle = true;
       for (Slot* sl : S->slots) idle = idle && !sl->busy;
       if (idle) break;
@@ -413,6 +433,7 @@ void worker_loop(Server* S) {
           S->waiting.pop_front();
           S->done.push_back(Done{r.tag, 0.0, int32_t(SDFT_ERR_BUDGET)});
           ++S->stats.failed;
+          if (r.own_plan) sdft_plan_destroy(r.own_plan);
           progressed = true;
           continue;
         }
@@ -451,6 +472,7 @@ void worker_loop(Server* S) {
             if (r.own_tw) S->buddy.release(r.tw_off, r.tw_order);
             S->done.push_back(Done{r.tag, 0.0, int32_t(st)});
             ++S->stats.failed;
+            if (r.own_plan) sdft_plan_destroy(r.own_plan);
           }
           S->stats.inflight -= free_slot->reqs.size();
           free_slot->reqs.clear();
@@ -461,6 +483,41 @@ void worker_loop(Server* S) {
       }
     }
     if (!progressed) S->cv.wait_for(lk, std::chrono::microseconds(50));
+  }
+}
+
+// Planner thread: plan queued supports (deferred plans), then queue the
+// request for admission; a support that fails validation completes at once
+// with its plan-creation status.
+void planner_loop(Server* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (true) {
+    while (!S->stop && S->plan_jobs.empty()) S->plan_cv.wait(lk);
+    if (S->plan_jobs.empty()) break;     // stopping, nothing left to plan
+    PlanJob job = std::move(S->plan_jobs.front());
+    S->plan_jobs.pop_front();
+    lk.unlock();
+    sdft_plan h = nullptr;
+    const sdft_status st = sdft_plan_create(job.M, job.J.data(), job.J.size(), S->prec, SDFT_PLAN_DEFER_DEVICE, &h);
+    lk.lock();
+    --S->planning;
+    if (st != SDFT_OK) {
+      const double lat = std::chrono::duration<double>(Clock::now() - job.t_submit).count();
+      S->done.push_back(Done{job.tag, lat, int32_t(st)});
+      ++S->stats.failed;
+      continue;
+    }
+    Req r;
+    r.tag = job.tag;
+    r.plan = &h->p;
+    r.h_in = job.h_in;
+    r.h_out = job.h_out;
+    r.t_submit = job.t_submit;
+    r.own_plan = h;
+    S->waiting.push_back(r);
+    ++S->stats.planned;
+    S->cv.notify_one();
   }
 }
 
@@ -489,12 +546,12 @@ struct sdft_server_s {
 extern "C" {
 
 sdft_status sdft_server_create(sdft_prec prec, uint64_t budget_bytes, uint32_t n_slots, uint32_t max_batch,
-                               sdft_server* out) {
+                               uint32_t n_planners, sdft_server* out) {
   using namespace sdft;
   if (!out) return SDFT_ERR_ARG;
   *out = nullptr;
   if ((prec != SDFT_C64 && prec != SDFT_C128) || n_slots == 0 || n_slots > 16 || max_batch == 0 ||
-      budget_bytes < 4096)
+      budget_bytes < 4096 || n_planners > 64)
     return SDFT_ERR_ARG;
   sdft_server_s* h = new (std::nothrow) sdft_server_s();
   if (!h) return SDFT_ERR_NOMEM;
@@ -549,6 +606,7 @@ sdft_status sdft_server_create(sdft_prec prec, uint64_t budget_bytes, uint32_t n
   }
   S.stats.arena_bytes = S.budget;
   S.worker = std::thread(worker_loop, &S);
+  for (uint32_t i = 0; i < n_planners; ++i) S.planners.emplace_back(planner_loop, &S);
   *out = h;
   return SDFT_OK;
 }
@@ -577,6 +635,34 @@ sdft_status sdft_server_submit(sdft_server srv, sdft_plan plan, const void* h_sa
   return SDFT_OK;
 }
 
+sdft_status sdft_server_submit_support(sdft_server srv, uint32_t log2N, const uint64_t* J, uint64_t k,
+                                       const void* h_samples, void* h_coeffs, uint64_t tag) {
+  using namespace sdft;
+  if (!srv || !J || !h_samples || !h_coeffs || k == 0 || k > (1ull << SDFT_MAX_LOG2K)) return SDFT_ERR_ARG;
+  Server& S = srv->s;
+  PlanJob job;
+  job.tag = tag;
+  job.M = log2N;
+  job.h_in = h_samples;
+  job.h_out = h_coeffs;
+  job.t_submit = Clock::now();
+  try {
+    job.J.assign(J, J + k);
+  } catch (const std::bad_alloc&) {
+    return SDFT_ERR_NOMEM;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    if (S.stop) return SDFT_ERR_ARG;
+    if (S.planners.empty()) return SDFT_ERR_UNSUPPORTED;
+    S.plan_jobs.push_back(std::move(job));
+    ++S.planning;
+    ++S.stats.submitted;
+  }
+  S.plan_cv.notify_one();
+  return SDFT_OK;
+}
+
 sdft_status sdft_server_poll(sdft_server srv, uint64_t* tags, double* latency_s, int32_t* status, uint64_t cap,
                              uint64_t* n_out) {
   if (!srv || !n_out || (cap && (!tags || !latency_s || !status))) return SDFT_ERR_ARG;
@@ -600,7 +686,7 @@ sdft_status sdft_server_drain(sdft_server srv, uint64_t timeout_ms) {
   while (true) {
     {
       std::lock_guard<std::mutex> lk(S.mu);
-      if (S.waiting.empty() && S.stats.inflight == 0) return S.worker_error;
+      if (S.waiting.empty() && S.stats.inflight == 0 && S.planning == 0) return S.worker_error;
     }
     if (timeout_ms && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
       return SDFT_ERR_TIMEOUT;
@@ -633,6 +719,9 @@ sdft_status sdft_server_destroy(sdft_server srv) {
     std::lock_guard<std::mutex> lk(S.mu);
     S.stop = true;
   }
+  S.plan_cv.notify_all();
+  for (std::thread& t : S.planners)
+    if (t.joinable()) t.join();
   S.cv.notify_one();
   if (S.worker.joinable()) S.worker.join();
   cudaDeviceSynchronize();

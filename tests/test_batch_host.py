@@ -60,3 +60,27 @@ def test_lane_schedule_invariants_full_uneven_workload():
     multi = sum(1 for p in plans if p.s > 12)
     assert n_ctr == multi
     assert n_items >= sum(max(1, p.k >> 12) for p in plans if p.s > 12)
+
+
+@pytest.mark.parametrize("schedule", ["lanes", "round_robin", "auto"])
+@pytest.mark.parametrize("grid", [0, 152, 7])
+def test_schedules_keep_invariants(schedule, grid):
+    # every queue shape the autotuner may pick satisfies the ordering invariants
+    from paper_2211_15299_gb300 import Batch
+    insts = W.workload_uneven(count=600, salt=11)
+    b = Batch(_plans(insts))
+    _, n_ctr0, _ = b.stats()
+    b.set_schedule(schedule, grid)
+    n_items, n_ctr, g = b.stats()             # raises if a dependency is closer than 4 x grid
+    assert n_ctr == n_ctr0
+    assert g == (grid if grid else 304)
+    multi_items = sum(max(1, p.k >> 12) for p in b.plans if p.s > 12)
+    assert n_items >= 2 * multi_items
+
+
+def test_unknown_schedule_rejected():
+    from paper_2211_15299_gb300 import Batch, SdftError, _native as N
+    b = Batch(_plans(W.workload_uneven(count=5, salt=9)))
+    with pytest.raises(SdftError) as ei:
+        N.sdft_batch_set_schedule(b.handle, 7, 0)
+    assert ei.value.name == "SDFT_ERR_ARG"

@@ -191,3 +191,31 @@ def test_autotune_chooses_a_strategy():
     ref = plan.execute_strided(x)
     torch.cuda.synchronize()
     assert float(torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref)) < 1e-6
+
+
+def test_queue_shapes_bit_identical_and_autotune():
+    """Every item order and grid the autotuner may choose gives the same bits;
+    the autotuned batch still matches the oracle."""
+    torch = _torch()
+    rng = np.random.default_rng(5151)
+    insts = W.workload_uneven(count=300, salt=13)
+    b, plans, st, got, f_in, Jcs, Cs = _run_batch(insts, 0, rng)
+    assert st == 0
+    x = torch.from_numpy(b.pack(f_in).astype(np.complex64)).cuda()
+    ref = b.execute(x).clone()
+    full = b.stats()[2]
+    for schedule, grid in (("lanes", 0), ("round_robin", 0), ("lanes", full // 2), ("round_robin", 37)):
+        b.set_schedule(schedule, grid)
+        y = b.execute(x)
+        torch.cuda.synchronize()
+        assert b.device_status() == 0
+        assert b.stats()[2] == (grid if grid else full)
+        assert torch.equal(y.view(torch.float32), ref.view(torch.float32)), (schedule, grid)
+    name, grid, ms = b.autotune(x, reps=2)
+    assert name in ("lanes", "round_robin") and grid in (full, full // 2) and ms > 0
+    y = b.execute(x)
+    torch.cuda.synchronize()
+    assert torch.equal(y.view(torch.float32), ref.view(torch.float32))
+    out = b.unpack(y.cpu().numpy().astype(np.complex128))
+    worst = max(rel_l2(out[i], Cs[i]) for i in range(len(insts)))
+    assert worst < 1e-5

@@ -118,3 +118,40 @@ def test_deferred_plans_through_the_server():
     with pytest.raises(SdftError):
         Batch([deferred[0][0]])
     srv.close()
+
+
+def test_requests_that_bring_their_support():
+    """Supports planned by the engine's planner threads give the same bits as
+    caller-built plans of the same support; an invalid support completes with
+    its validation status."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Server
+    rng = np.random.default_rng(5153)
+    reqs = _requests(rng, [0, 4, 7, 12, 13, 16, 17])
+    srv = Server("c64", budget_bytes=64 << 20, n_slots=2, max_batch=4, n_planners=3)
+    ref, _ = _serve(srv, reqs)
+    outs = []
+    for i, (plan, h_in, c, M, piv, Jc) in enumerate(reqs):
+        h_out = torch.empty_like(h_in).pin_memory()
+        outs.append(h_out)
+        # the caller's support in its own (shuffled) order
+        J = np.asarray(plan.support_order)[rng.permutation(plan.k)]
+        srv.submit_support(M, J, h_in, h_out, 100 + i)
+    bad_in = torch.zeros(4, dtype=torch.complex64).pin_memory()
+    bad_out = torch.empty_like(bad_in).pin_memory()
+    srv.submit_support(6, np.array([0, 1, 2, 4], dtype=np.uint64), bad_in, bad_out, 999)   # 3 pivots, k = 4
+    srv.drain(timeout_ms=60_000)
+    got = {}
+    for _ in range(100):
+        tags, lat, st = srv.poll()
+        for t, l, s_ in zip(tags, lat, st):
+            got[int(t)] = (float(l), int(s_))
+        if len(got) == len(reqs) + 1:
+            break
+    assert got[999][1] == 5                                # SDFT_ERR_NOT_HOMOGENEOUS
+    for i in range(len(reqs)):
+        assert got[100 + i][1] == 0 and got[100 + i][0] > 0
+        assert np.array_equal(outs[i].numpy(), ref[i].numpy()), i
+    st = srv.stats()
+    assert st["planned"] == len(reqs) and st["failed"] == 1
+    srv.close()
