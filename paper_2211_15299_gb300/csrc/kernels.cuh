@@ -45,7 +45,10 @@ constexpr int kBadSmem = 0x101;   // less dynamic shared memory than the layout 
 constexpr int kBadMap = 0x102;    // tensor map parameter not 64-byte aligned
 constexpr int kBadTable = 0x103;  // twiddle table not 16-byte aligned
 constexpr int kBufs = 3;                                             // tiles in flight per CTA
-constexpr uint32_t kLevelSmem = kBufs * kTileBytes + 64 + 1024;     // tiles, barriers, alignment slack
+// Shared-memory copy of the middle pass's table region (entries [16, 256),
+// absolute-indexed) for the level kernel.
+constexpr uint32_t kMidTwBytes = 256 * 16;
+constexpr uint32_t kLevelSmem = kBufs * kTileBytes + 64 + kMidTwBytes + 1024;   // tiles, barriers, table, slack
 
 // ---- swizzled tile addressing -------------------------------------------------
 // byte(T) = (T >> CB) * 128 + ((col_chunk(T) ^ (row(T) & 7)) << 4) + sub(T) * ES.
@@ -130,8 +133,9 @@ constexpr int pass_ntw(int B, int SLO, int SHI) {
 // Twiddle sources per pass: a B = 0 pass (the same 15 entries for every thread)
 // reads kernel parameters; the top pass (B = TB - 4, the largest table region)
 // holds its entries in registers across tiles; any other pass reads its small
-// table region through the L1 cache.
-enum TwSrc { kTwParam = 0, kTwReg = 1, kTwGlobal = 2 };
+// table region through the L1 cache, or (level kernel) from a shared-memory
+// copy made when the table changes.
+enum TwSrc { kTwParam = 0, kTwReg = 1, kTwGlobal = 2, kTwShared = 3 };
 constexpr int pass_src(int TB, int B) { return B == 0 ? kTwParam : (B == TB - 4 ? kTwReg : kTwGlobal); }
 constexpr int reg_twiddles(int TB, int PLO, int PHI) {
   int n = 0;
@@ -142,6 +146,35 @@ constexpr int reg_twiddles(int TB, int PLO, int PHI) {
   return n;
 }
 
+// One complex value from shared memory (byte address).
+template <class R>
+__device__ __forceinline__ typename KT<R>::C ld_shared_c(uint32_t addr);
+template <>
+__device__ __forceinline__ float2 ld_shared_c<float>(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+template <>
+__device__ __forceinline__ double2 ld_shared_c<double>(uint32_t addr) {
+  double2 v;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
+// Stage range [lo, hi) of the pass that reads its twiddles from memory
+// (neither kernel parameters nor registers); {0, 0} if there is none.
+constexpr int mid_pass_lo(int TB, int PLO, int PHI) {
+  for (int p = 0; p < n_passes(TB, PLO, PHI); ++p)
+    if (pass_src(TB, pass_b(TB, PLO, PHI, p)) == kTwGlobal) return pass_done(TB, PLO, PHI, p);
+  return 0;
+}
+constexpr int mid_pass_hi(int TB, int PLO, int PHI) {
+  for (int p = 0; p < n_passes(TB, PLO, PHI); ++p)
+    if (pass_src(TB, pass_b(TB, PLO, PHI, p)) == kTwGlobal) return pass_shi(TB, PLO, PHI, p);
+  return 0;
+}
+
 // ---- one pass: stages with stage bits [SLO, SHI) on 16 elements per thread --------
 // The thread covers tile-index bits [B, B+4); its other bits (F) come from tid.
 // Stage bit m1 on the element pair (e, e | 2^q), q = m1 - B, uses the table
@@ -149,9 +182,11 @@ constexpr int reg_twiddles(int TB, int PLO, int PHI) {
 // those entries in order (m1 ascending, then e mod 2^q).
 // SRC = kTwParam / kTwReg: `w` holds exactly the pass's entries in order
 // (m1 ascending, then e mod 2^q). SRC = kTwGlobal: `w` is the absolute-indexed
-// table in global memory.
+// table in global memory. SRC = kTwShared: `wsm` is the shared-memory address of
+// the absolute-indexed table region.
 template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SRC>
-__device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc) {
+__device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc,
+                                          uint32_t wsm = 0) {
   using C = typename KT<R>::C;
   static_assert(B >= 0 && B + 4 <= KT<R>::TB, "pass bits out of tile");
   static_assert(SLO >= B && SHI <= B + 4 && SLO < SHI, "stage bits out of pass");
@@ -184,6 +219,8 @@ __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w,
       C wt;
       if constexpr (SRC == kTwGlobal)
         wt = __ldg(w + (1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B));
+      else if constexpr (SRC == kTwShared)
+        wt = ld_shared_c<R>(wsm + ((1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B)) * KT<R>::ES);
       else
         wt = w[off + (e & ((1 << q) - 1))];
       if (SCALE && m1 == SHI - 1)
@@ -248,9 +285,12 @@ __device__ __forceinline__ void prefetch_twiddles(const typename KT<R>::C* __res
   }
 }
 
-template <class R, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0>
+// MIDSM: the memory-read pass takes its twiddles from the shared-memory copy
+// at `wsm` instead of global memory.
+template <class R, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0, bool MIDSM = false>
 __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* wreg, const typename KT<R>::C* w0,
-                                           const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc) {
+                                           const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc,
+                                           uint32_t wsm = 0) {
   constexpr int TB = KT<R>::TB;
   if constexpr (P < n_passes(TB, PLO, PHI)) {
     constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
@@ -258,13 +298,16 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
     constexpr int SRC = pass_src(TB, B);
     if constexpr (SRC == kTwParam) {
       tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, w0, tid, sc);
-      run_passes<R, PLO, PHI, LAST, P + 1, ROFF>(buf, wreg, w0, twg, tid, sc);
+      run_passes<R, PLO, PHI, LAST, P + 1, ROFF, MIDSM>(buf, wreg, w0, twg, tid, sc, wsm);
     } else if constexpr (SRC == kTwGlobal) {
-      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, twg, tid, sc);
-      run_passes<R, PLO, PHI, LAST, P + 1, ROFF>(buf, wreg, w0, twg, tid, sc);
+      if constexpr (MIDSM)
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared>(buf, twg, tid, sc, wsm);
+      else
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, twg, tid, sc);
+      run_passes<R, PLO, PHI, LAST, P + 1, ROFF, MIDSM>(buf, wreg, w0, twg, tid, sc, wsm);
     } else {
       tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, wreg + ROFF, tid, sc);
-      run_passes<R, PLO, PHI, LAST, P + 1, ROFF + pass_ntw(B, SLO, SHI)>(buf, wreg, w0, twg, tid, sc);
+      run_passes<R, PLO, PHI, LAST, P + 1, ROFF + pass_ntw(B, SLO, SHI), MIDSM>(buf, wreg, w0, twg, tid, sc, wsm);
     }
   }
 }
@@ -312,7 +355,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   // dynamic shared memory for the aligned layout, tensor maps 64-byte aligned,
   // twiddle tables 16-byte aligned. A failed check records a status and exits.
   {
-    const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 8 * kBufs;
+    const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 64 + kMidTwBytes;
     int bad = 0;
     if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
     else if ((reinterpret_cast<uintptr_t>(&src) | reinterpret_cast<uintptr_t>(&dst)) & 63u) bad = kBadMap;
@@ -367,6 +410,11 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   const R sc = R(args.scale);
   const C* tw = static_cast<const C*>(args.tw) - args.tw_first;
   C wreg[NREG > 0 ? NREG : 1];
+  constexpr int MLO = mid_pass_lo(KT<R>::TB, PLO, PHI), MHI = mid_pass_hi(KT<R>::TB, PLO, PHI);
+  // a middle pass whose region fits the shared copy reads it from there
+  constexpr bool MIDSM = MLO < MHI && (1u << MHI) * sizeof(C) <= kMidTwBytes;
+  C* midtw = reinterpret_cast<C*>(smem + kBufs * kTileBytes + 64);
+  const uint32_t midtw_addr = ptx::smem_addr(midtw);
   const C* twt = tw;
   uint64_t cur_tab = ~0ull;
   bool aborted = false;
@@ -377,9 +425,12 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   for (; j < n; ++j, advance(cur), b = (b + 1 == uint32_t(kBufs)) ? 0u : b + 1) {
     char* buf = smem + b * kTileBytes;
     const uint64_t tab = args.tw_stride ? cur.a : 0;
-    if (tab != cur_tab) {  // uniform across the CTA
+    if (tab != cur_tab) {  // uniform across the CTA; the previous tile's passes are done
       twt = tw + tab * args.tw_stride;
       load_reg_twiddles<R, PLO, PHI>(twt, tid, wreg);
+      if constexpr (MIDSM) {   // the middle pass's entries into shared memory (barrier below)
+        for (uint32_t e = (1u << MLO) + tid; e < (1u << MHI); e += KT<R>::NT) midtw[e] = twt[e];
+      }
       cur_tab = tab;
     }
     const bool ok = ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, args.timeout_ns);
@@ -388,7 +439,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
       aborted = true;
       break;
     }
-    run_passes<R, PLO, PHI, LAST>(buf, wreg, args.tw0, twt, tid, sc);
+    run_passes<R, PLO, PHI, LAST, 0, 0, MIDSM>(buf, wreg, args.tw0, twt, tid, sc, midtw_addr);
     if (tid == 0) {
       int c1, c3;
       coords(cur, c1, c3);
