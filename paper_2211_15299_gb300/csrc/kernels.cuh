@@ -285,12 +285,17 @@ __device__ __forceinline__ void prefetch_twiddles(const typename KT<R>::C* __res
   }
 }
 
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // MIDSM: the memory-read pass takes its twiddles from the shared-memory copy
-// at `wsm` instead of global memory.
-template <class R, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0, bool MIDSM = false>
+// at `wsm` instead of global memory. `hook` runs after the first pass's
+// barrier (the level kernel issues its next load there).
+template <class R, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0, bool MIDSM = false, class Hook = NoHook>
 __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* wreg, const typename KT<R>::C* w0,
                                            const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc,
-                                           uint32_t wsm = 0) {
+                                           uint32_t wsm = 0, const Hook& hook = Hook()) {
   constexpr int TB = KT<R>::TB;
   if constexpr (P < n_passes(TB, PLO, PHI)) {
     constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
@@ -298,17 +303,17 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
     constexpr int SRC = pass_src(TB, B);
     if constexpr (SRC == kTwParam) {
       tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, w0, tid, sc);
-      run_passes<R, PLO, PHI, LAST, P + 1, ROFF, MIDSM>(buf, wreg, w0, twg, tid, sc, wsm);
     } else if constexpr (SRC == kTwGlobal) {
       if constexpr (MIDSM)
         tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared>(buf, twg, tid, sc, wsm);
       else
         tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, twg, tid, sc);
-      run_passes<R, PLO, PHI, LAST, P + 1, ROFF, MIDSM>(buf, wreg, w0, twg, tid, sc, wsm);
     } else {
       tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, wreg + ROFF, tid, sc);
-      run_passes<R, PLO, PHI, LAST, P + 1, ROFF + pass_ntw(B, SLO, SHI), MIDSM>(buf, wreg, w0, twg, tid, sc, wsm);
     }
+    if constexpr (P == 0) hook();
+    constexpr int RNEXT = (SRC == kTwReg) ? ROFF + pass_ntw(B, SLO, SHI) : ROFF;
+    run_passes<R, PLO, PHI, LAST, P + 1, RNEXT, MIDSM, Hook>(buf, wreg, w0, twg, tid, sc, wsm, hook);
   }
 }
 
@@ -337,10 +342,10 @@ __device__ __forceinline__ char* align1024(char* p) {
 }
 
 // Pipeline per CTA (kBufs = 3 tile buffers): tile j waits on full[j % 3], runs
-// its passes in place, and leaves through a TMA store issued by thread 0. The
-// buffer of tile j-1 is refilled with tile j+2 once its store has finished
-// reading shared memory (wait_group.read 1 leaves only tile j's store pending),
-// so two loads stay in flight behind the tile being computed.
+// its passes in place, and leaves through a TMA store issued by thread 0. After
+// tile j's first pass, the buffer of tile j-1 is refilled with tile j+2 once its
+// store has finished reading shared memory, so up to two loads stay in flight
+// behind the tile being computed.
 template <class R, int PLO, int PHI, bool LAST>
 __global__ void __launch_bounds__(KT<R>::NT, 2)
     k_level(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap dst,
@@ -439,16 +444,21 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
       aborted = true;
       break;
     }
-    run_passes<R, PLO, PHI, LAST, 0, 0, MIDSM>(buf, wreg, args.tw0, twt, tid, sc, midtw_addr);
+    // After the first pass: once the store of tile j-1 (the latest one issued)
+    // has left its buffer, load tile j+2 into it, two thirds of a tile earlier
+    // than at the end of this tile.
+    auto refill = [&]() {
+      if (tid == 0 && j >= 1 && j + 2 < n) {
+        ptx::bulk_wait_read<0>();
+        issue_load();
+      }
+    };
+    run_passes<R, PLO, PHI, LAST, 0, 0, MIDSM>(buf, wreg, args.tw0, twt, tid, sc, midtw_addr, refill);
     if (tid == 0) {
       int c1, c3;
       coords(cur, c1, c3);
       ptx::tma_store_4d(&dst, ptx::smem_addr(buf), 0, c1, 0, c3);
       ptx::bulk_commit();
-      if (j >= 1 && j + 2 < n) {
-        ptx::bulk_wait_read<1>();   // the store of tile j-1 has left its buffer
-        issue_load();               // tile j+2 into that buffer
-      }
     }
   }
   if (tid == 0) {
