@@ -270,6 +270,69 @@ sdft_status sdft_batch_stats(sdft_batch batch, uint64_t* n_items, uint64_t* n_co
 sdft_status sdft_batch_destroy(sdft_batch batch);
 
 /* ------------------------------------------------------------------------ */
+/* Shift-and-Sample: supports that are not homogeneous                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sdft_sas_s* sdft_sas;
+
+/*
+ * sdft_sas_create - plan Shift-and-Sample (Algorithm "shift-sample", Section
+ * "balanced partly homogeneous families") for an arbitrary support J of k
+ * distinct frequencies in [0, 2^log2N) (k need not be a power of two).
+ *   R     : number of pivots; the pivots are the first R split levels of the
+ *           congruence tree T(J), so J is part-homogeneous for them (Definition
+ *           "part-H-tree"). 0 chooses R: the smallest operation count of
+ *           Lemma "computation_shift_sample" (1.5 R 2^R mu* + 6 sum_v mu(v)^2)
+ *           among R whose class systems have 1-norm condition <= 32
+ *           (complex64) or <= 1000 (complex128), else the best-conditioned R.
+ *   flags : 0, or SDFT_PLAN_HOST_ONLY (planning only; cannot execute).
+ * The classes of J modulo 2^(r_max+1) hold mu(v) <= mu* <= 64 members. The
+ * instance needs mu* x 2^R samples: row a (a < mu*) is f at I_r + a (mod N)
+ * (sdft_sas_sample_indices). The plan owns a virtual homogeneous plan with
+ * pivots r and, per class, the inverse of its Vandermonde matrix
+ * [exp(2 pi i a l / N)] (a < mu(v), l its members; eq. "alg1_system"),
+ * computed in FP64 and rounded once to the precision of `prec`.
+ * Errors: SDFT_ERR_RANGE (j >= N), SDFT_ERR_DUPLICATE, SDFT_ERR_ARG (R larger
+ * than the number of split levels or than 24), SDFT_ERR_UNSUPPORTED (no R
+ * keeps mu* <= 64, or a singular class system), SDFT_ERR_NOMEM, SDFT_ERR_CUDA.
+ */
+sdft_status sdft_sas_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft_prec prec, uint32_t R,
+                            uint32_t flags, sdft_sas* out);
+
+/* R, mu*, samples per instance (mu* x 2^R), classes J occupies, and the largest
+ * 1-norm condition number of the class systems (any output may be NULL). */
+sdft_status sdft_sas_info(sdft_sas sas, uint32_t* R, uint32_t* mu_star, uint64_t* samples_per_instance,
+                          uint32_t* occupied_classes, double* max_cond);
+
+/* The R pivots (ascending). */
+sdft_status sdft_sas_pivots(sdft_sas sas, uint32_t* r);
+
+/* mu* x 2^R sample indices, row-major by shift a: the order of one instance's
+ * samples in the execute buffer. */
+sdft_status sdft_sas_sample_indices(sdft_sas sas, uint64_t* idx);
+
+/* The k frequencies in output order (by class, then by value). */
+sdft_status sdft_sas_support_order(sdft_sas sas, uint64_t* J);
+
+/* Device workspace that sdft_sas_execute needs for `batch` instances. */
+sdft_status sdft_sas_workspace_bytes(sdft_sas sas, uint64_t batch, uint64_t* bytes);
+
+/*
+ * sdft_sas_execute - coefficients of `batch` instances: d_samples holds
+ * batch x mu* x 2^R values (sample_indices order), d_coeffs receives batch x k
+ * (support_order), d_work is the workspace (it may be d_samples itself, which
+ * is then overwritten; it must not overlap d_coeffs). Stage 1 runs the virtual
+ * plan over the batch x mu* shifted sample sets (Algorithm 1); stage 2 solves
+ * each class with its precomputed inverse. Device buffers 16-byte aligned;
+ * asynchronous on `stream`. SDFT_ERR_NO_DEVICE for host-only plans.
+ */
+sdft_status sdft_sas_execute(sdft_sas sas, uint64_t batch, const void* d_samples, void* d_work, void* d_coeffs,
+                             void* stream);
+
+/* Release the plan (synchronise work using it first). */
+sdft_status sdft_sas_destroy(sdft_sas sas);
+
+/* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of requests under a device-memory budget     */
 /* ------------------------------------------------------------------------ */
 

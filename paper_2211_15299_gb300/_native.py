@@ -75,6 +75,14 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_float)]),
     "sdft_batch_stats": (c_int, [c_vp, P_u64, P_u64, ctypes.POINTER(c_int)]),
     "sdft_batch_destroy": (c_int, [c_vp]),
+    "sdft_sas_create": (c_int, [c_u32, P_u64, c_u64, c_int, c_u32, c_u32, ctypes.POINTER(c_vp)]),
+    "sdft_sas_info": (c_int, [c_vp, P_u32, P_u32, P_u64, P_u32, P_f64]),
+    "sdft_sas_pivots": (c_int, [c_vp, P_u32]),
+    "sdft_sas_sample_indices": (c_int, [c_vp, P_u64]),
+    "sdft_sas_support_order": (c_int, [c_vp, P_u64]),
+    "sdft_sas_workspace_bytes": (c_int, [c_vp, c_u64, P_u64]),
+    "sdft_sas_execute": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp]),
+    "sdft_sas_destroy": (c_int, [c_vp]),
     "sdft_server_create": (c_int, [c_int, c_u64, c_u32, c_u32, c_u32, ctypes.POINTER(c_vp)]),
     "sdft_server_submit": (c_int, [c_vp, c_vp, c_vp, c_vp, c_u64]),
     "sdft_server_submit_support": (c_int, [c_vp, c_u32, P_u64, c_u64, c_vp, c_vp, c_u64]),
@@ -263,6 +271,55 @@ def sdft_batch_stats(batch: int):
 
 def sdft_batch_destroy(batch: int) -> None:
     _check(_lib.sdft_batch_destroy(batch), "sdft_batch_destroy")
+
+
+def sdft_sas_create(log2N: int, J, prec: int = SDFT_C64, R: int = 0, flags: int = 0) -> int:
+    arr = np.ascontiguousarray(np.asarray(J, dtype=np.uint64))
+    out = c_vp()
+    _check(_lib.sdft_sas_create(int(log2N), arr.ctypes.data_as(P_u64), int(arr.size), int(prec), int(R), int(flags),
+                                ctypes.byref(out)), "sdft_sas_create")
+    return int(out.value)
+
+
+def sdft_sas_info(sas: int):
+    """Returns (R, mu*, samples per instance, occupied classes, largest class condition number)."""
+    R, mu, ns, occ, cond = c_u32(), c_u32(), c_u64(), c_u32(), ctypes.c_double()
+    _check(_lib.sdft_sas_info(sas, ctypes.byref(R), ctypes.byref(mu), ctypes.byref(ns), ctypes.byref(occ),
+                              ctypes.byref(cond)), "sdft_sas_info")
+    return int(R.value), int(mu.value), int(ns.value), int(occ.value), float(cond.value)
+
+
+def sdft_sas_pivots(sas: int, R: int) -> np.ndarray:
+    out = np.zeros(max(R, 1), dtype=np.uint32)
+    _check(_lib.sdft_sas_pivots(sas, out.ctypes.data_as(P_u32)), "sdft_sas_pivots")
+    return out[:R]
+
+
+def sdft_sas_sample_indices(sas: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.uint64)
+    _check(_lib.sdft_sas_sample_indices(sas, out.ctypes.data_as(P_u64)), "sdft_sas_sample_indices")
+    return out
+
+
+def sdft_sas_support_order(sas: int, k: int) -> np.ndarray:
+    out = np.zeros(k, dtype=np.uint64)
+    _check(_lib.sdft_sas_support_order(sas, out.ctypes.data_as(P_u64)), "sdft_sas_support_order")
+    return out
+
+
+def sdft_sas_workspace_bytes(sas: int, batch: int) -> int:
+    out = c_u64()
+    _check(_lib.sdft_sas_workspace_bytes(sas, int(batch), ctypes.byref(out)), "sdft_sas_workspace_bytes")
+    return int(out.value)
+
+
+def sdft_sas_execute(sas: int, batch: int, d_samples, d_work, d_coeffs, stream=None) -> None:
+    _check(_lib.sdft_sas_execute(sas, int(batch), _ptr(d_samples), _ptr(d_work), _ptr(d_coeffs), _stream(stream)),
+           "sdft_sas_execute")
+
+
+def sdft_sas_destroy(sas: int) -> None:
+    _check(_lib.sdft_sas_destroy(sas), "sdft_sas_destroy")
 
 
 def sdft_server_create(prec: int, budget_bytes: int, n_slots: int = 2, max_batch: int = 64,

@@ -207,6 +207,62 @@ class Batch:
             pass
 
 
+class Sas:
+    """Shift-and-Sample for an arbitrary support (sdft_sas_*): mu* transforms of
+    a homogeneous virtual support over shifted sample sets, then one small
+    Vandermonde solve per class."""
+
+    def __init__(self, log2N: int, J: Sequence[int], prec="c64", R: int = 0, host_only: bool = False):
+        self.prec = _PREC[prec] if isinstance(prec, str) else int(prec)
+        J = np.asarray(J, dtype=np.uint64)
+        self.log2N, self.k = int(log2N), int(J.size)
+        self.handle = N.sdft_sas_create(log2N, J, self.prec, R, N.SDFT_PLAN_HOST_ONLY if host_only else 0)
+        self.R, self.mu_star, self.n_samples, self.occupied, self.max_cond = N.sdft_sas_info(self.handle)
+
+    @property
+    def pivots(self) -> np.ndarray:
+        return N.sdft_sas_pivots(self.handle, self.R)
+
+    @property
+    def sample_indices(self) -> np.ndarray:
+        """(mu*, 2^R): row a is the sample set shifted by a."""
+        return N.sdft_sas_sample_indices(self.handle, self.n_samples).reshape(self.mu_star, 1 << self.R)
+
+    @property
+    def support_order(self) -> np.ndarray:
+        return N.sdft_sas_support_order(self.handle, self.k)
+
+    @property
+    def dtype(self):
+        return _dtype(self.prec)
+
+    def execute(self, samples, coeffs=None, work=None, stream=None):
+        """samples: (batch, mu* x 2^R) or (mu* x 2^R,) device tensor; returns (batch, k)."""
+        torch = _torch()
+        x = samples.reshape(-1, self.n_samples)
+        batch = x.shape[0]
+        _check_tensor(x, self.dtype, batch * self.n_samples, "samples")
+        if coeffs is None:
+            coeffs = torch.empty((batch, self.k), dtype=x.dtype, device=x.device)
+        _check_tensor(coeffs, self.dtype, batch * self.k, "coeffs")
+        if work is None:
+            work = torch.empty_like(x)
+        _check_tensor(work, self.dtype, batch * self.n_samples, "work")
+        N.sdft_sas_execute(self.handle, batch, x, work, coeffs, _current_stream(stream))
+        return coeffs
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.sdft_sas_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Server:
     """Continuous-batching serving engine (sdft_server_*).
 

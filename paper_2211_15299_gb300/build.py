@@ -24,7 +24,8 @@ LIB = os.path.join(LIBDIR, "libsdft.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["plan.cpp", "api.cu", "batch.cu", "level_f32.cu", "level_f64.cu", "queue_f32.cu", "queue_f64.cu", "server.cu"]
+SOURCES = ["plan.cpp", "api.cu", "batch.cu", "level_f32.cu", "level_f64.cu", "queue_f32.cu", "queue_f64.cu", "server.cu",
+           "sas.cu"]
 
 
 def _nvcc() -> str:

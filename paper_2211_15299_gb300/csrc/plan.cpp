@@ -240,6 +240,24 @@ sdft_status build_plan(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec
   return SDFT_OK;
 }
 
+sdft_status split_levels(uint32_t M, const uint64_t* J, uint64_t k, uint64_t& level_mask) {
+  level_mask = 0;
+  if (!J || k == 0) return SDFT_ERR_ARG;
+  if (M > SDFT_MAX_LOG2N) return SDFT_ERR_RANGE;
+  const uint64_t N = 1ull << M;
+  for (uint64_t i = 0; i < k; ++i)
+    if (J[i] >= N) return SDFT_ERR_RANGE;
+  std::vector<uint64_t> rev(k), tmp;
+  for (uint64_t i = 0; i < k; ++i) rev[i] = M ? (bitrev64(J[i]) >> (64 - M)) : 0;
+  radix_sort(rev, tmp, M);
+  for (uint64_t i = 0; i + 1 < k; ++i) {
+    const uint64_t x = rev[i] ^ rev[i + 1];
+    if (x == 0) return SDFT_ERR_DUPLICATE;
+    level_mask |= 1ull << (M - 1 - highest_bit(x));
+  }
+  return SDFT_OK;
+}
+
 template <class T>
 void fill_device_tables(const Plan& p, T* out) {
   if (p.tw_elems == 0) return;

@@ -71,6 +71,11 @@ sdft_status build_plan(uint32_t log2N, const uint64_t* J, uint64_t k, sdft_prec 
 // exp(-2 pi i (Jc[u] mod 2^r_m) / 2^(r_m+1)).
 void twiddle_f64(const Plan& p, uint32_t m, uint64_t u, double& re, double& im);
 
+// Every level at which the congruence tree of an arbitrary set J splits (bit l
+// of level_mask), from depth-first neighbours; SDFT_ERR_DUPLICATE /
+// SDFT_ERR_RANGE for repeated or out-of-range elements.
+sdft_status split_levels(uint32_t M, const uint64_t* J, uint64_t k, uint64_t& level_mask);
+
 // Device-table layout (rounded to the plan's precision, final stage scaled by
 // N/k) written into `out` as interleaved pairs of `T`.
 template <class T> void fill_device_tables(const Plan& p, T* out);

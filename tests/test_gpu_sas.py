@@ -1,0 +1,93 @@
+"""GPU parity of Shift-and-Sample against the FP64 oracle (oracle/sas.py)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def _tol(prec, cond):
+    # stage 1 carries the transform's rounding (about 2e-7 relative for complex64,
+    # 1e-15 for complex128); each class system amplifies it by at most its condition
+    return (2e-6 if prec == "c64" else 1e-12) * max(1.0, cond)
+
+
+def _case(M, J, prec, R, batch, rng):
+    """Plan, draw `batch` coefficient vectors, synthesise the shifted samples by
+    the direct sum, run on the GPU; returns (plan, got, c in output order,
+    the FP64 oracle on the same rounded samples)."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Sas
+    J = [int(j) for j in J]
+    p = Sas(M, J, prec, R=R)
+    order = [int(j) for j in p.support_order]
+    r = [int(x) for x in p.pivots]
+    assert r == O.sas_pivots(J, M, p.R)
+    idx = p.sample_indices
+    C = W.complex_gaussian((batch, len(J)), rng)
+    F = np.stack([O.sas_samples_direct(M, order, C[b], idx) for b in range(batch)])
+    np_dt = np.complex64 if prec == "c64" else np.complex128
+    x = torch.from_numpy(F.reshape(batch, -1).astype(np_dt)).cuda()
+    y = p.execute(x)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.complex128)
+    f_in = x.cpu().numpy().astype(np.complex128).reshape(batch, p.mu_star, -1)
+    ref = np.stack([O.sas_transform(M, order, r, f_in[b]) for b in range(batch)])
+    return p, got, C, ref
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_paper_example(prec):
+    rng = np.random.default_rng(61)
+    p, got, C, ref = _case(10, [0, 512, 1, 6, 7], prec, 2, 3, rng)
+    assert p.mu_star == 2 and p.n_samples == 8
+    assert rel_l2(got, ref) < _tol(prec, p.max_cond)
+    assert rel_l2(got, C) < _tol(prec, p.max_cond)
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("seed", range(4))
+def test_arbitrary_sets(prec, seed):
+    rng = np.random.default_rng(700 + seed)
+    M = int(rng.integers(8, 17))
+    k = int(rng.integers(5, 600))
+    J = sorted(int(x) for x in rng.choice(1 << M, size=k, replace=False))
+    p, got, C, ref = _case(M, J, prec, 0, 2, rng)
+    assert rel_l2(got, ref) < _tol(prec, p.max_cond), (p.R, p.mu_star, p.max_cond)
+    assert rel_l2(got, C) < _tol(prec, p.max_cond)
+
+
+@pytest.mark.parametrize("kind", ["ap", "subset"])
+def test_workloads_reduced(kind):
+    # the bench's supports (N = 2^20, k = 3000) on a few instances
+    rng = np.random.default_rng(62)
+    J = W.workload_sas(kind)
+    p, got, C, ref = _case(20, J, "c64", 0, 2, rng)
+    assert rel_l2(got, C) < 1e-5 and rel_l2(got, ref) < 1e-5
+
+
+def test_batch_rows_are_independent():
+    torch = _torch()
+    from paper_2211_15299_gb300 import Sas
+    J = W.workload_sas("subset", M=16, k=500, salt=3)
+    p = Sas(16, J, "c64")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    x = torch.randn((37, p.n_samples), dtype=torch.complex64, device="cuda", generator=g)
+    y = p.execute(x)
+    for b in (0, 17, 36):
+        assert torch.equal(p.execute(x[b:b + 1].clone())[0], y[b])
+    # in place: the samples buffer as workspace
+    x2 = x.clone()
+    y2 = p.execute(x2, work=x2)
+    torch.cuda.synchronize()
+    assert torch.equal(y2, y)

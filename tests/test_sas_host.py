@@ -1,0 +1,90 @@
+"""CPU checks of the Shift-and-Sample planner (host-only plans) against the
+oracle: pivots, classes, sample sets, output order, the choice of R."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+
+def _sas(M, J, R=0):
+    from paper_2211_15299_gb300 import Sas
+    return Sas(M, J, "c64", R=R, host_only=True)
+
+
+def _sets(rng, n):
+    out = [(10, [0, 512, 1, 6, 7]), (10, [0, 256, 1, 6, 7])]
+    for _ in range(n):
+        M = int(rng.integers(4, 13))
+        k = int(rng.integers(1, min(200, 1 << M) + 1))
+        out.append((M, sorted(int(x) for x in rng.choice(1 << M, size=k, replace=False))))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_planner_matches_oracle(seed):
+    rng = np.random.default_rng(40 + seed)
+    for M, J in _sets(rng, 25):
+        levels = O.split_levels(J, M)
+        for R in sorted({1, len(levels) // 2, len(levels)} & set(range(1, len(levels) + 1))):
+            r = O.sas_pivots(J, M, R)
+            mu = O.sas_mu(J, r)
+            if max(mu.values()) > 64:              # beyond the decoder's class size
+                from paper_2211_15299_gb300 import SdftError
+                with pytest.raises(SdftError) as ei:
+                    _sas(M, J, R)
+                assert ei.value.name == "SDFT_ERR_UNSUPPORTED"
+                continue
+            p = _sas(M, J, R)
+            assert list(p.pivots) == r
+            assert p.mu_star == max(mu.values()) and p.occupied == len(mu)
+            assert np.array_equal(p.sample_indices, O.sas_sample_sets(M, r, p.mu_star))
+            want = sorted(J, key=lambda j: (O.node_key(j, r), j))
+            assert [int(x) for x in p.support_order] == want
+            assert p.max_cond >= 1.0 - 1e-12
+            if p.mu_star == 1:
+                assert abs(p.max_cond - 1.0) < 1e-12
+
+
+def test_automatic_R_minimises_the_lemma_cost():
+    # the cheapest R (Lemma "computation_shift_sample") among those whose
+    # class systems are well conditioned (1-norm condition <= 32 for complex64)
+    rng = np.random.default_rng(9)
+    for M, J in _sets(rng, 30):
+        levels = O.split_levels(J, M)
+        if not levels:
+            continue
+        p = _sas(M, J, 0)
+        lk = int(np.ceil(np.log2(len(J)))) if len(J) > 1 else 0
+        cands = [c for c in range(max(0, lk - 4), min(len(levels), lk + 2, 24) + 1)
+                 if max(O.sas_mu(J, levels[:c]).values()) <= 64]
+        cond = {c: (_sas(M, J, c).max_cond if c else 1.0) for c in cands}
+        ok = [c for c in cands if cond[c] <= 32.0]
+        if ok:
+            cost = {c: O.sas_cost(c, O.sas_mu(J, levels[:c])) for c in ok}
+            best = min(cost.values())
+            assert p.R == min(c for c in ok if cost[c] == best), (M, len(J))
+        else:
+            assert p.R == min(cands, key=lambda c: (cond[c], c))
+
+
+def test_homogeneous_set_gives_one_shift():
+    rng = np.random.default_rng(4)
+    M, s = 16, 9
+    piv = W.random_pivots(M, s, rng)
+    J = W.homogeneous_support(M, piv, rng)
+    p = _sas(M, J, s)
+    assert p.mu_star == 1 and p.occupied == 1 << s and list(p.pivots) == [int(x) for x in piv]
+
+
+def test_sas_errors():
+    from paper_2211_15299_gb300 import SdftError
+    with pytest.raises(SdftError) as ei:
+        _sas(4, [1, 2, 2])
+    assert ei.value.name == "SDFT_ERR_DUPLICATE"
+    with pytest.raises(SdftError) as ei:
+        _sas(4, [1, 16])
+    assert ei.value.name == "SDFT_ERR_RANGE"
+    with pytest.raises(SdftError) as ei:
+        _sas(6, [0, 1, 2, 3], R=5)               # only 2 split levels
+    assert ei.value.name == "SDFT_ERR_ARG"

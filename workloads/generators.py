@@ -189,3 +189,38 @@ def workload_serving(rate: float = 20000.0, duration: float = 10.0, pool: int = 
             plans.append(draw())
             ids[r] = len(plans) - 1
     return ServingTrace(arrivals, ids, plans)
+
+
+# ---------------------------------------------------------------------------
+# Supports that are not homogeneous (Shift-and-Sample)
+# ---------------------------------------------------------------------------
+
+
+def arithmetic_progression(M: int, k: int, d: int, rng: np.random.Generator) -> np.ndarray:
+    """{a + n d mod N : 0 <= n < k} with a uniform start a (Corollary "AP")."""
+    N = 1 << M
+    a = int(rng.integers(0, N))
+    J = (a + np.arange(k, dtype=np.uint64) * np.uint64(d)) % np.uint64(N)
+    if np.unique(J).size != k:
+        raise ValueError("progression wraps onto itself")
+    return J
+
+
+def random_subset_of_homogeneous(M: int, s_h: int, k: int, rng: np.random.Generator) -> np.ndarray:
+    """k elements drawn without replacement from a homogeneous set with s_h
+    random pivots (the random-subset family, Theorem "hom_rand_subset")."""
+    piv = random_pivots(M, s_h, rng)
+    H = homogeneous_support(M, piv, rng)
+    return np.sort(rng.choice(H, size=k, replace=False)).astype(np.uint64)
+
+
+def workload_sas(kind: str = "subset", M: int = 20, k: int = 3000, batch: int = 1024, config: int = 6,
+                 salt: int = 0) -> np.ndarray:
+    """Supports for the Shift-and-Sample path: an arithmetic progression with
+    odd difference ("ap"), or a random subset of a homogeneous set with
+    ceil(log2 k) + 2 pivots ("subset")."""
+    rng = rng_for(config, salt)
+    if kind == "ap":
+        return arithmetic_progression(M, k, 2 * int(rng.integers(0, 1 << (M - 2))) + 1, rng)
+    s_h = int(np.ceil(np.log2(k))) + 2
+    return random_subset_of_homogeneous(M, s_h, k, rng)
