@@ -265,6 +265,7 @@ def run_ours(args):
         extra["uneven"] = run_uneven(args)
         extra["large_k"] = run_large(args)
         extra["serving"] = run_serving(args)
+        extra["sas"] = run_sas(args)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -391,6 +392,42 @@ def run_uneven(args):
             "dependency_counters": n_ctr, "grid": grid, "plan_build_s": t_plan,
             "autotune": {"schedule": schedule, "grid": grid, "ms_per_run": ms_tuned, "seconds": t_tune},
             "launches_per_step": 1, "graph": "one CUDA graph replay per step"}
+
+
+def run_sas(args):
+    """Shift-and-Sample leg: supports that are not homogeneous (N = 2^20,
+    k = 3000): an arithmetic progression (complete isolation, mu* = 1) and a
+    random subset of a homogeneous set (mu* shifted transforms and per-class
+    solves); complex64, a batch of instances sharing the support."""
+    import torch
+    from paper_2211_15299_gb300 import Sas
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for kind in ("ap", "subset"):
+        J = W.workload_sas(kind)
+        t0 = time.perf_counter()
+        p = Sas(20, J, "c64")
+        t_plan = time.perf_counter() - t0
+        g = torch.Generator(device=dev)
+        g.manual_seed(W.BASE_SEED + 6)
+        x = torch.randn((args.sas_batch, p.n_samples), dtype=torch.complex64, device=dev, generator=g)
+        w = torch.empty_like(x)
+        y = torch.empty((args.sas_batch, p.k), dtype=torch.complex64, device=dev)
+
+        def step(s=None):
+            p.execute(x, y, work=w, stream=(s or stream).cuda_stream)
+
+        t = time_graph(step, args.steps, args.warmup, flush, stream)
+        mean = statistics.mean(t)
+        coeffs = args.sas_batch * p.k
+        alg = 8 * args.sas_batch * (p.n_samples + p.k)        # samples in, coefficients out
+        res[kind] = {"k": p.k, "R": p.R, "mu_star": p.mu_star, "samples_per_instance": p.n_samples,
+                     "max_cond": p.max_cond, "batch": args.sas_batch, "coeffs_per_s": coeffs / mean,
+                     "ms_per_step": 1e3 * mean, "alg_GBps": alg / mean / 1e9, "plan_s": t_plan,
+                     "launches_per_step": 2 + (1 if p.R > 12 else 0)}
+    return res
 
 
 def run_serving(args):
@@ -613,6 +650,8 @@ def main():
     ap.add_argument("--large-batch", type=int, default=64)
     ap.add_argument("--uneven-count", type=int, default=10000)
     ap.add_argument("--uneven", action="store_true", help="time only the uneven-batch leg")
+    ap.add_argument("--sas", action="store_true", help="time only the Shift-and-Sample leg")
+    ap.add_argument("--sas-batch", type=int, default=1024)
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven, large-k and serving legs")
     ap.add_argument("--serve", action="store_true", help="run only the serving leg")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
@@ -631,6 +670,8 @@ def main():
         print(json.dumps({"serving": run_serving(args)}), flush=True)
     elif args.uneven:
         print(json.dumps({"uneven": run_uneven(args)}), flush=True)
+    elif args.sas:
+        print(json.dumps({"sas": run_sas(args)}), flush=True)
     else:
         run_ours(args)
 

@@ -263,6 +263,7 @@ sdft_status build_sas(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec,
   for (uint64_t t = 0; t < nk; ++t) {
     const uint32_t m = mu[t];
     if (!m) continue;
+    if (S.winv.size() + size_t(m) * m > 0xffffffffull) return SDFT_ERR_UNSUPPORTED;
     const uint32_t woff = uint32_t(S.winv.size());
     S.winv.resize(S.winv.size() + size_t(m) * m);
     const double cond = vandermonde_inverse(M, &S.order[first[t]], m, &S.winv[woff]);

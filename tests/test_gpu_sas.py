@@ -59,7 +59,7 @@ def test_paper_example(prec):
 def test_arbitrary_sets(prec, seed):
     rng = np.random.default_rng(700 + seed)
     M = int(rng.integers(8, 17))
-    k = int(rng.integers(5, 600))
+    k = int(rng.integers(5, min(600, 1 << M)))
     J = sorted(int(x) for x in rng.choice(1 << M, size=k, replace=False))
     p, got, C, ref = _case(M, J, prec, 0, 2, rng)
     assert rel_l2(got, ref) < _tol(prec, p.max_cond), (p.R, p.mu_star, p.max_cond)
