@@ -91,3 +91,17 @@ def test_batch_rows_are_independent():
     y2 = p.execute(x2, work=x2)
     torch.cuda.synchronize()
     assert torch.equal(y2, y)
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_random_subset_at_the_theorems_pivot_count(prec):
+    # Theorem "hom_rand_subset": n = floor(log2 k - log2 log2 k) pivots of K
+    log2k = 10
+    rng = W.rng_for(0, 4321)
+    J, piv = W.bernoulli_subset_of_homogeneous(18, log2k + 3, 1 << log2k, rng)
+    n = int(np.floor(log2k - np.log2(log2k)))
+    p, got, C, ref = _case(18, [int(j) for j in J], prec, n, 2, np.random.default_rng(8))
+    assert [int(x) for x in p.pivots] == [int(x) for x in piv[:n]]
+    assert p.mu_star < (4 + 3 * np.log(2)) * log2k
+    assert rel_l2(got, ref) < _tol(prec, p.max_cond), p.max_cond
+    assert rel_l2(got, C) < _tol(prec, p.max_cond)

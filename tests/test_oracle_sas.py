@@ -161,3 +161,30 @@ def test_sample_complexity_is_mu_star_times_2R():
         idx = O.sas_sample_sets(M, r, max(mu.values()))
         assert idx.shape == (max(mu.values()), 1 << R)
         assert sum(mu.values()) == len(J)
+
+
+@pytest.mark.parametrize("log2k", [8, 10, 12])
+def test_random_subsets_alias_at_most_c_log_k(log2k):
+    # Lemma "bound_mu_r_star" / Theorem "hom_rand_subset": keep every element of
+    # a homogeneous K independently with probability k/|K|; with the first n
+    # pivots of K, n = floor(log2 k - log2 log2 k), the largest class stays
+    # below c log2 k, c = 4 + 3 ln 2, and SAS recovers the coefficients
+    k = 1 << log2k
+    c_const = 4 + 3 * np.log(2)
+    for seed in range(3):
+        rng = W.rng_for(0, 900 + 10 * log2k + seed)
+        M = log2k + 8
+        J, piv = W.bernoulli_subset_of_homogeneous(M, log2k + 3, k, rng)
+        J = [int(j) for j in J]
+        n = int(np.floor(log2k - np.log2(log2k)))
+        r = O.sas_pivots(J, M, n)
+        assert r == [int(p) for p in piv[:n]]            # J splits where K does, w.h.p.
+        mu = O.sas_mu(J, r)
+        assert max(mu.values()) < c_const * log2k
+        if log2k <= 10:
+            c = W.complex_gaussian(len(J), rng)
+            idx = O.sas_sample_sets(M, r, max(mu.values()))
+            F = O.sas_samples_direct(M, J, c, idx)
+            got = O.sas_transform(M, J, r, F)
+            conds = [np.linalg.cond(O.sas.__dict__["_z_powers"](M, m, len(m))) for m in O.sas_nodes(J, r).values()]
+            assert rel_l2(got, c) < 1e-14 * max(conds) + 1e-12

@@ -214,13 +214,23 @@ def random_subset_of_homogeneous(M: int, s_h: int, k: int, rng: np.random.Genera
     return np.sort(rng.choice(H, size=k, replace=False)).astype(np.uint64)
 
 
+def bernoulli_subset_of_homogeneous(M: int, s_h: int, k: int, rng: np.random.Generator):
+    """Every element of a homogeneous set K (s_h random pivots) kept
+    independently with probability k / |K| (the model of Theorem
+    "hom_rand_subset"); returns (J sorted, K's pivots)."""
+    piv = random_pivots(M, s_h, rng)
+    K = homogeneous_support(M, piv, rng)
+    keep = rng.random(K.size) < (k / K.size)
+    return np.sort(K[keep]).astype(np.uint64), piv
+
+
 def workload_sas(kind: str = "subset", M: int = 20, k: int = 3000, batch: int = 1024, config: int = 6,
                  salt: int = 0) -> np.ndarray:
     """Supports for the Shift-and-Sample path: an arithmetic progression with
-    odd difference ("ap"), or a random subset of a homogeneous set with
-    ceil(log2 k) + 2 pivots ("subset")."""
+    odd difference ("ap"), or a Bernoulli subset of expected size k of a
+    homogeneous set with ceil(log2 k) + 2 pivots ("subset")."""
     rng = rng_for(config, salt)
     if kind == "ap":
         return arithmetic_progression(M, k, 2 * int(rng.integers(0, 1 << (M - 2))) + 1, rng)
     s_h = int(np.ceil(np.log2(k))) + 2
-    return random_subset_of_homogeneous(M, s_h, k, rng)
+    return bernoulli_subset_of_homogeneous(M, s_h, k, rng)[0]
