@@ -423,10 +423,31 @@ def run_sas(args):
         mean = statistics.mean(t)
         coeffs = args.sas_batch * p.k
         alg = 8 * args.sas_batch * (p.n_samples + p.k)        # samples in, coefficients out
-        res[kind] = {"k": p.k, "R": p.R, "mu_star": p.mu_star, "samples_per_instance": p.n_samples,
-                     "max_cond": p.max_cond, "batch": args.sas_batch, "coeffs_per_s": coeffs / mean,
-                     "ms_per_step": 1e3 * mean, "alg_GBps": alg / mean / 1e9, "plan_s": t_plan,
-                     "launches_per_step": 2 + (1 if p.R > 12 else 0)}
+        peak, peak_kind = _peaks()
+        entry = {"k": p.k, "R": p.R, "mu_star": p.mu_star, "samples_per_instance": p.n_samples,
+                 "max_cond": p.max_cond, "batch": args.sas_batch, "coeffs_per_s": coeffs / mean,
+                 "ms_per_step": 1e3 * mean, "plan_s": t_plan,
+                 "roofline": {"bound": "hbm", "achieved": alg / mean / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": alg / mean / 1e9 / peak, "peak_kind": peak_kind,
+                              "alg_bytes_per_step": alg},
+                 "launches_per_step": 2 + (1 if p.R > 12 else 0)}
+        if not args.no_cpu:
+            # the oracle's SAS (numpy FP64) on a few of the same instances
+            import oracle as O
+            n_cpu = 4
+            order = [int(j) for j in p.support_order]
+            r = [int(v) for v in p.pivots]
+            f = x[:n_cpu].cpu().numpy().astype(np.complex128).reshape(n_cpu, p.mu_star, -1)
+            t0 = time.perf_counter()
+            ref = np.stack([O.sas_transform(20, order, r, f[b]) for b in range(n_cpu)])
+            dt = time.perf_counter() - t0
+            step()
+            torch.cuda.synchronize()
+            got = y[:n_cpu].cpu().numpy().astype(np.complex128)
+            entry["cpu_oracle"] = {"value": n_cpu * p.k / dt, "unit": UNIT, "kind": "oracle",
+                                   "sample": f"{n_cpu} instances, numpy FP64", "seconds": dt,
+                                   "rel_l2_gpu_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+        res[kind] = entry
     return res
 
 

@@ -23,9 +23,13 @@ def main() -> int:
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
     ap.add_argument("--uneven", type=int, default=0,
                     help="run the uneven workload's recipe with this many instances instead")
+    ap.add_argument("--sas", default="", choices=["", "ap", "subset"],
+                    help="run Shift-and-Sample on that support kind (N = 2^20, k = 3000) instead")
     args = ap.parse_args()
     if args.uneven:
         return uneven(args)
+    if args.sas:
+        return sas(args)
 
     import torch
 
@@ -68,6 +72,26 @@ def uneven(args) -> int:
     print(f"profile_case uneven={args.uneven} coeffs={b.total} items={n_items} counters={n_ctr} grid={grid} "
           f"reps={args.reps} device_status={st:#x}", flush=True)
     return 0 if st == 0 else 3
+
+
+def sas(args) -> int:
+    import torch
+
+    import workloads as W
+    from paper_2211_15299_gb300 import Sas
+
+    J = W.workload_sas(args.sas)
+    p = Sas(20, J, args.prec)
+    dt = torch.complex64 if args.prec == "c64" else torch.complex128
+    x = torch.randn((args.batch, p.n_samples), dtype=dt, device="cuda")
+    w = torch.empty_like(x)
+    y = torch.empty((args.batch, p.k), dtype=dt, device="cuda")
+    for _ in range(args.reps):
+        p.execute(x, y, work=w)
+    torch.cuda.synchronize()
+    print(f"profile_case sas={args.sas} k={p.k} R={p.R} mu*={p.mu_star} batch={args.batch} reps={args.reps}",
+          flush=True)
+    return 0
 
 
 if __name__ == "__main__":
