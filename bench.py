@@ -396,16 +396,17 @@ def run_uneven(args):
 
 def run_sas(args):
     """Shift-and-Sample leg: supports that are not homogeneous (N = 2^20,
-    k = 3000): an arithmetic progression (complete isolation, mu* = 1) and a
-    random subset of a homogeneous set (mu* shifted transforms and per-class
-    solves); complex64, a batch of instances sharing the support."""
+    k about 3000): an arithmetic progression (complete isolation, mu* = 1), a
+    random subset of a homogeneous set and a union of homogeneous sets (mu*
+    shifted transforms and per-class solves); complex64, a batch of instances
+    sharing the support."""
     import torch
     from paper_2211_15299_gb300 import Sas
     dev = torch.device("cuda", 0)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     res = {}
-    for kind in ("ap", "subset"):
+    for kind in ("ap", "subset", "uoh"):
         J = W.workload_sas(kind)
         t0 = time.perf_counter()
         p = Sas(20, J, "c64")

@@ -66,7 +66,7 @@ def test_arbitrary_sets(prec, seed):
     assert rel_l2(got, C) < _tol(prec, p.max_cond)
 
 
-@pytest.mark.parametrize("kind", ["ap", "subset"])
+@pytest.mark.parametrize("kind", ["ap", "subset", "uoh"])
 def test_workloads_reduced(kind):
     # the bench's supports (N = 2^20, k = 3000) on a few instances
     rng = np.random.default_rng(62)

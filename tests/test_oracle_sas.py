@@ -188,3 +188,43 @@ def test_random_subsets_alias_at_most_c_log_k(log2k):
             got = O.sas_transform(M, J, r, F)
             conds = [np.linalg.cond(O.sas.__dict__["_z_powers"](M, m, len(m))) for m in O.sas_nodes(J, r).values()]
             assert rel_l2(got, c) < 1e-14 * max(conds) + 1e-12
+
+
+def test_union_of_elementary_example():
+    # Lemma "UoE1" example: {31, 22}, {3, 4, 9, 10} and {1, 2, 3, 4, 8, 13, 22, 23}
+    # are elementary (one element per class mod 2, 4, 8) and, with {0}, their
+    # union keeps the pivots 0, 1, 2. (The printed J omits the 0 of the
+    # printed union; the union is taken as the set.)
+    parts = [[0], [31, 22], [3, 4, 9, 10], [1, 2, 3, 4, 8, 13, 22, 23]]
+    for i, p in enumerate(parts):
+        assert O.is_homogeneous(p, 5) and O.pivots_by_tree(p, 5) == list(range(i))
+    J = sorted(set().union(*map(set, parts)))
+    assert O.split_levels(J, 5)[:3] == [0, 1, 2]
+    rng = np.random.default_rng(12)
+    c = W.complex_gaussian(len(J), rng)
+    for R in (2, 3):
+        r, mu, idx, got = _run(5, J, R, c)
+        assert rel_l2(got, c) < 1e-11
+
+
+@pytest.mark.parametrize("base", ["elementary", "homogeneous"])
+def test_union_of_homogeneous_alias_bound(base):
+    # Proposition "UoE-mu-r-star-bound" (and its homogeneous analogue under
+    # Theorem "UoE2"): at the s-th pivot level, s <= a, every class holds at most
+    # C (s + 2^(a-s+1) - 1) members, C = max eta_i; the union keeps the parts' pivots
+    for seed in range(4):
+        rng = W.rng_for(0, 5000 + seed)
+        M, a = 14, 6
+        l = list(range(M)) if base == "elementary" else [int(x) for x in W.random_pivots(M, a + 3, rng)]
+        etas = [int(x) for x in rng.integers(1, 4, size=a + 1)]
+        J, parts = W.union_of_homogeneous(M, l, etas, rng, rng)
+        J = [int(j) for j in J]
+        C = max(etas)
+        assert O.split_levels(J, M)[:a] == l[:a]
+        for s in range(1, a + 1):
+            mu = O.sas_mu(J, l[:s])
+            assert max(mu.values()) <= C * (s + 2 ** (a - s + 1) - 1), (s, max(mu.values()))
+        c = W.complex_gaussian(len(J), rng)
+        r, mu, idx, got = _run(M, J, a, c)
+        conds = [np.linalg.cond(O.sas.__dict__["_z_powers"](M, m, len(m))) for m in O.sas_nodes(J, r).values()]
+        assert rel_l2(got, c) < 1e-14 * max(conds) + 1e-12

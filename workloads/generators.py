@@ -227,10 +227,35 @@ def bernoulli_subset_of_homogeneous(M: int, s_h: int, k: int, rng: np.random.Gen
 def workload_sas(kind: str = "subset", M: int = 20, k: int = 3000, batch: int = 1024, config: int = 6,
                  salt: int = 0) -> np.ndarray:
     """Supports for the Shift-and-Sample path: an arithmetic progression with
-    odd difference ("ap"), or a Bernoulli subset of expected size k of a
-    homogeneous set with ceil(log2 k) + 2 pivots ("subset")."""
+    odd difference ("ap"), a Bernoulli subset of expected size k of a
+    homogeneous set with ceil(log2 k) + 2 pivots ("subset"), or a union of
+    homogeneous sets ("uoh", Theorem "UoE2")."""
     rng = rng_for(config, salt)
     if kind == "ap":
         return arithmetic_progression(M, k, 2 * int(rng.integers(0, 1 << (M - 2))) + 1, rng)
+    if kind == "uoh":       # two parts of every size 2^0 .. 2^a inside a homogeneous K, a = log2 k - 2
+        a = int(np.floor(np.log2(k))) - 2
+        l = random_pivots(M, a + 4, rng)
+        return union_of_homogeneous(M, l, [2] * (a + 1), rng, rng)[0]
     s_h = int(np.ceil(np.log2(k))) + 2
     return bernoulli_subset_of_homogeneous(M, s_h, k, rng)[0]
+
+
+def union_of_homogeneous(M: int, l: Sequence[int], etas: Sequence[int], K_rng: np.random.Generator,
+                         rng: np.random.Generator):
+    """A union as in Theorem "UoE2": K homogeneous with pivots l (drawn with
+    K_rng), and for each i, etas[i] sets J_ij of 2^i elements of K that are
+    homogeneous with the first i pivots of l (their bits at the other pivots
+    fixed at random). l = 0..M-1 (K = Z_N) gives a union of elementary sets
+    (Lemma "UoE1"). Returns (J sorted and deduplicated, the parts)."""
+    K = homogeneous_support(M, l, K_rng)
+    l = [int(x) for x in l]
+    bits = np.stack([(K >> np.uint64(p)) & np.uint64(1) for p in l], axis=1)   # K's pivot bits
+    parts = []
+    for i, eta in enumerate(etas):
+        for _ in range(int(eta)):
+            fixed = rng.integers(0, 2, size=len(l) - i)
+            sel = np.all(bits[:, i:] == fixed[None, :].astype(np.uint64), axis=1)
+            parts.append(np.sort(K[sel]))
+    J = np.unique(np.concatenate(parts)).astype(np.uint64)
+    return J, parts
