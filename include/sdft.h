@@ -135,6 +135,21 @@ sdft_status sdft_execute(sdft_plan plan, const void* d_samples, void* d_coeffs, 
 sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_samples,
                                  void* d_coeffs, void* stream);
 
+/*
+ * sdft_synthesize / sdft_synthesize_strided - the inverse map: samples
+ * f_I = F^{-1}(I_r, J) c = (1/N) F(J, I_r)^H c from coefficients c (Section II,
+ * eq. "submatrix-method"; F(J, I_r)^H F(J, I_r) = k Id, so this inverts
+ * sdft_execute). It runs the adjoint of the execute network (Cor.
+ * "block-structure"): the same stages in reverse order with conjugated
+ * twiddles, the N/k folded into the last stage undone exactly and 1/N applied
+ * at stage 1. Layouts, buffers, in-place use and errors as for sdft_execute /
+ * sdft_execute_strided with the roles swapped: coefficients in canonical order
+ * in, samples in sample order out.
+ */
+sdft_status sdft_synthesize(sdft_plan plan, const void* d_coeffs, void* d_samples, void* stream);
+sdft_status sdft_synthesize_strided(sdft_plan plan, uint64_t batch, const void* d_coeffs, void* d_samples,
+                                    void* stream);
+
 /* Execution strategy of a multi-level plan (k > 2^12 for complex64, 2^11 for
  * complex128) in sdft_execute / sdft_execute_strided:
  *   SDFT_STRATEGY_LEVELS: one persistent launch per butterfly level (default);

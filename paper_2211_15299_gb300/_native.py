@@ -59,6 +59,8 @@ SIGNATURES = {
     "sdft_plan_device_bytes": (c_int, [c_vp, P_u64]),
     "sdft_execute": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "sdft_execute_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
+    "sdft_synthesize": (c_int, [c_vp, c_vp, c_vp, c_vp]),
+    "sdft_synthesize_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "sdft_plan_set_strategy": (c_int, [c_vp, c_int]),
     "sdft_plan_autotune": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_int, ctypes.POINTER(c_int),
                                    ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
@@ -201,6 +203,15 @@ def sdft_execute_strided(plan: int, batch: int, d_samples, d_coeffs, stream=None
 
 def sdft_plan_set_strategy(plan: int, strategy: int) -> None:
     _check(_lib.sdft_plan_set_strategy(plan, int(strategy)), "sdft_plan_set_strategy")
+
+
+def sdft_synthesize(plan: int, d_coeffs, d_samples, stream=None) -> None:
+    _check(_lib.sdft_synthesize(plan, _ptr(d_coeffs), _ptr(d_samples), _stream(stream)), "sdft_synthesize")
+
+
+def sdft_synthesize_strided(plan: int, batch: int, d_coeffs, d_samples, stream=None) -> None:
+    _check(_lib.sdft_synthesize_strided(plan, int(batch), _ptr(d_coeffs), _ptr(d_samples), _stream(stream)),
+           "sdft_synthesize_strided")
 
 
 def sdft_plan_autotune(plan: int, batch: int, d_samples, d_coeffs, stream=None, reps: int = 5):

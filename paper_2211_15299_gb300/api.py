@@ -104,6 +104,17 @@ class Plan:
         N.sdft_execute_strided(self.handle, batch, samples, coeffs, _current_stream(stream))
         return coeffs
 
+    def synthesize(self, coeffs, samples=None, stream=None, batch: Optional[int] = None):
+        """Samples from coefficients (the inverse of execute_strided)."""
+        if batch is None:
+            batch = coeffs.numel() // self.k
+        _check_tensor(coeffs, self.dtype, batch * self.k, "coeffs")
+        if samples is None:
+            samples = _torch().empty_like(coeffs)
+        _check_tensor(samples, self.dtype, batch * self.k, "samples")
+        N.sdft_synthesize_strided(self.handle, batch, coeffs, samples, _current_stream(stream))
+        return samples
+
     def set_strategy(self, strategy: str):
         """'levels' (one launch per butterfly level) or 'queue' (one work-queue launch)."""
         N.sdft_plan_set_strategy(self.handle, {"levels": N.SDFT_STRATEGY_LEVELS, "queue": N.SDFT_STRATEGY_QUEUE}[strategy])

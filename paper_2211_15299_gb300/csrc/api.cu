@@ -125,6 +125,19 @@ sdft_status run_strided(sdft_plan_s* h, uint64_t batch, const void* in, void* ou
   return p.prec == SDFT_C64 ? launch_plan_f32(p, batch, in, out, st) : launch_plan_f64(p, batch, in, out, st);
 }
 
+// Synthesis of `batch` instances: samples from coefficients.
+static sdft_status run_strided_inverse(sdft_plan_s* h, uint64_t batch, const void* in, void* out, cudaStream_t st) {
+  const Plan& p = h->p;
+  sdft_status s = check_device(p);
+  if (s != SDFT_OK) return s;
+  if (batch == 0) return SDFT_OK;
+  const uint64_t eb = uint64_t(elem_bytes(p.prec));
+  if (batch > (~0ull / eb) / p.k) return SDFT_ERR_ARG;
+  s = check_buffers(in, out, batch * p.k * eb);
+  if (s != SDFT_OK) return s;
+  return p.prec == SDFT_C64 ? launch_plan_inv_f32(p, batch, in, out, st) : launch_plan_inv_f64(p, batch, in, out, st);
+}
+
 }  // namespace sdft
 
 using sdft::Plan;
@@ -251,6 +264,17 @@ sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_s
                                  void* stream) {
   if (!plan) return SDFT_ERR_ARG;
   return sdft::run_strided(plan, batch, d_samples, d_coeffs, static_cast<cudaStream_t>(stream));
+}
+
+sdft_status sdft_synthesize(sdft_plan plan, const void* d_coeffs, void* d_samples, void* stream) {
+  if (!plan) return SDFT_ERR_ARG;
+  return sdft::run_strided_inverse(plan, 1, d_coeffs, d_samples, static_cast<cudaStream_t>(stream));
+}
+
+sdft_status sdft_synthesize_strided(sdft_plan plan, uint64_t batch, const void* d_coeffs, void* d_samples,
+                                    void* stream) {
+  if (!plan) return SDFT_ERR_ARG;
+  return sdft::run_strided_inverse(plan, batch, d_coeffs, d_samples, static_cast<cudaStream_t>(stream));
 }
 
 sdft_status sdft_plan_set_strategy(sdft_plan plan, sdft_strategy strategy) {

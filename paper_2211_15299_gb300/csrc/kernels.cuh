@@ -99,6 +99,40 @@ __device__ __forceinline__ void bfly_scaled(double2& a, double2& b, const double
   a.y = fma(a.y, sc, ti);
 }
 
+// Adjoint butterflies (synthesis): (a, b) -> (a + b, conj(w) (a - b)); the
+// scaled form multiplies the first output by ga and the second by gb, both
+// powers of two (exact).
+__device__ __forceinline__ void ibfly(float2& a, float2& b, const float2 w) {
+  const float2 d = __ffma2_rn(b, make_float2(-1.f, -1.f), a);   // a - b
+  a = __fadd2_rn(a, b);
+  b.x = fmaf(w.y, d.y, w.x * d.x);
+  b.y = fmaf(-w.y, d.x, w.x * d.y);
+}
+__device__ __forceinline__ void ibfly_scaled(float2& a, float2& b, float2 w, const float ga, const float gb) {
+  w.x *= gb;
+  w.y *= gb;
+  const float2 d = __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+  a = __fmul2_rn(__fadd2_rn(a, b), make_float2(ga, ga));
+  b.x = fmaf(w.y, d.y, w.x * d.x);
+  b.y = fmaf(-w.y, d.x, w.x * d.y);
+}
+__device__ __forceinline__ void ibfly(double2& a, double2& b, const double2 w) {
+  const double dx = a.x - b.x, dy = a.y - b.y;
+  a.x = a.x + b.x;
+  a.y = a.y + b.y;
+  b.x = fma(w.y, dy, w.x * dx);
+  b.y = fma(-w.y, dx, w.x * dy);
+}
+__device__ __forceinline__ void ibfly_scaled(double2& a, double2& b, double2 w, const double ga, const double gb) {
+  w.x *= gb;
+  w.y *= gb;
+  const double dx = a.x - b.x, dy = a.y - b.y;
+  a.x = (a.x + b.x) * ga;
+  a.y = (a.y + b.y) * ga;
+  b.x = fma(w.y, dy, w.x * dx);
+  b.y = fma(-w.y, dx, w.x * dy);
+}
+
 // ---- pass schedule ------------------------------------------------------------------
 // Stage bits [PLO, PHI) of a tile run in passes. Pass p covers the 4-bit window
 // starting at the first stage bit not yet done (or the top window of the tile)
@@ -317,6 +351,114 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
   }
 }
 
+// ---- adjoint passes (synthesis) ------------------------------------------------
+// The same tiles, element ownership and twiddle entries as tile_pass, with the
+// stages of the pass in descending order and the adjoint butterfly. TOPSC: the
+// pass holds the plan's last stage, whose table entries carry the factor N/k;
+// its second outputs are scaled by sc_top = k/N. FINSC: the pass holds stage 1,
+// the last one applied; both its outputs are scaled by sc_fin = 1/N.
+template <class R, int B, int SLO, int SHI, bool TOPSC, bool FINSC, bool FENCE, int SRC>
+__device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc_top,
+                                              R sc_fin, uint32_t wsm = 0) {
+  using C = typename KT<R>::C;
+  static_assert(B >= 0 && B + 4 <= KT<R>::TB, "pass bits out of tile");
+  static_assert(SLO >= B && SHI <= B + 4 && SLO < SHI, "stage bits out of pass");
+  constexpr uint32_t LOWM = (1u << B) - 1u;
+  const uint32_t F = (tid & LOWM) | ((tid >> B) << (B + 4));
+  const uint32_t rF = row_part<R>(F), xF = xor_part<R>(F);
+  C v[16];
+  if constexpr (B == 0 && KT<R>::ES == 8) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float4 t = *reinterpret_cast<const float4*>(buf + rF + (xF ^ (uint32_t(c) << 4)));
+      v[2 * c] = make_float2(t.x, t.y);
+      v[2 * c + 1] = make_float2(t.z, t.w);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const uint32_t E = uint32_t(e) << B;
+      v[e] = *reinterpret_cast<const C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)));
+    }
+  }
+#pragma unroll
+  for (int m1 = SHI - 1; m1 >= SLO; --m1) {
+    const int q = m1 - B;
+    const int off = pass_ntw(B, SLO, m1);
+    const bool top = TOPSC && m1 == SHI - 1, fin = FINSC && m1 == SLO;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      if ((e >> q) & 1) continue;
+      const int eh = e | (1 << q);
+      C wt;
+      if constexpr (SRC == kTwGlobal)
+        wt = __ldg(w + (1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B));
+      else if constexpr (SRC == kTwShared)
+        wt = ld_shared_c<R>(wsm + ((1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B)) * KT<R>::ES);
+      else
+        wt = w[off + (e & ((1 << q) - 1))];
+      if (top || fin)
+        ibfly_scaled(v[e], v[eh], wt, fin ? sc_fin : R(1), (top ? sc_top : R(1)) * (fin ? sc_fin : R(1)));
+      else
+        ibfly(v[e], v[eh], wt);
+    }
+  }
+  if constexpr (B == 0 && KT<R>::ES == 8) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      *reinterpret_cast<float4*>(buf + rF + (xF ^ (uint32_t(c) << 4))) =
+          make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const uint32_t E = uint32_t(e) << B;
+      *reinterpret_cast<C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E))) = v[e];
+    }
+  }
+  if constexpr (FENCE) ptx::fence_proxy_async_smem();
+  __syncthreads();
+}
+
+// Register-twiddle offset of pass P (entries of the earlier register passes).
+constexpr int reg_off(int TB, int PLO, int PHI, int P) {
+  int n = 0;
+  for (int p = 0; p < P; ++p) {
+    const int b = pass_b(TB, PLO, PHI, p);
+    if (pass_src(TB, b) == kTwReg) n += pass_ntw(b, pass_done(TB, PLO, PHI, p), pass_shi(TB, PLO, PHI, p));
+  }
+  return n;
+}
+
+// The passes of a tile in reverse order (P = n-1 .. 0). LAST: the level holds
+// the plan's last stage; PLO == 0: the level holds stage 1. `hook` runs after
+// the first pass applied.
+template <class R, int PLO, int PHI, bool LAST, bool MIDSM, int P, class Hook>
+__device__ __forceinline__ void run_passes_inv(char* buf, const typename KT<R>::C* wreg,
+                                               const typename KT<R>::C* w0,
+                                               const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc_top,
+                                               R sc_fin, uint32_t wsm, const Hook& hook) {
+  constexpr int TB = KT<R>::TB;
+  constexpr int NP = n_passes(TB, PLO, PHI);
+  if constexpr (P >= 0) {
+    constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
+    constexpr bool TOPSC = LAST && P == NP - 1, FINSC = PLO == 0 && P == 0, FENCE = P == 0;
+    constexpr int SRC = pass_src(TB, B);
+    if constexpr (SRC == kTwParam) {
+      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC>(buf, w0, tid, sc_top, sc_fin);
+    } else if constexpr (SRC == kTwGlobal) {
+      if constexpr (MIDSM)
+        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, kTwShared>(buf, twg, tid, sc_top, sc_fin, wsm);
+      else
+        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC>(buf, twg, tid, sc_top, sc_fin);
+    } else {
+      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC>(buf, wreg + reg_off(TB, PLO, PHI, P), tid, sc_top,
+                                                              sc_fin);
+    }
+    if constexpr (P == NP - 1) hook();
+    run_passes_inv<R, PLO, PHI, LAST, MIDSM, P - 1, Hook>(buf, wreg, w0, twg, tid, sc_top, sc_fin, wsm, hook);
+  }
+}
+
 // ---- persistent level kernel ----------------------------------------------------
 // Tile i of a level: a = i / nB selects the twiddle table (a group block for
 // later levels), b = i % nB; TMA coordinates {0, a*a_step1 + b*b_step1, 0, b*b_step3}.
@@ -330,6 +472,7 @@ struct LevelArgs {
   uint64_t tw_len;         // entries per table
   uint64_t tw_stride;      // entries between consecutive tables (0: one shared table)
   double scale;            // N/k, used when LAST
+  double inv_n;            // 1/N, used by the adjoint kernel
   int* status;             // device status word
   uint64_t timeout_ns;     // bound on every mbarrier wait
   typename KT<R>::C tw0[16];  // tw0[i] = level-0 table entry i + 1 (stage bits 0..3), i < 15
@@ -346,7 +489,8 @@ __device__ __forceinline__ char* align1024(char* p) {
 // tile j's first pass, the buffer of tile j-1 is refilled with tile j+2 once its
 // store has finished reading shared memory, so up to two loads stay in flight
 // behind the tile being computed.
-template <class R, int PLO, int PHI, bool LAST>
+// INV: the adjoint (synthesis) passes instead of the forward ones.
+template <class R, int PLO, int PHI, bool LAST, bool INV = false>
 __global__ void __launch_bounds__(KT<R>::NT, 2)
     k_level(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap dst,
             const __grid_constant__ LevelArgs<R> args) {
@@ -453,7 +597,11 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
         issue_load();
       }
     };
-    run_passes<R, PLO, PHI, LAST, 0, 0, MIDSM>(buf, wreg, args.tw0, twt, tid, sc, midtw_addr, refill);
+    if constexpr (INV)
+      run_passes_inv<R, PLO, PHI, LAST, MIDSM, n_passes(KT<R>::TB, PLO, PHI) - 1>(
+          buf, wreg, args.tw0, twt, tid, R(1.0 / args.scale), R(args.inv_n), midtw_addr, refill);
+    else
+      run_passes<R, PLO, PHI, LAST, 0, 0, MIDSM>(buf, wreg, args.tw0, twt, tid, sc, midtw_addr, refill);
     if (tid == 0) {
       int c1, c3;
       coords(cur, c1, c3);
@@ -501,6 +649,40 @@ __global__ void __launch_bounds__(256) k_small(const typename KT<R>::C* __restri
   if constexpr (S == 0) {
     v[0].x *= sc;
     v[0].y *= sc;
+  }
+#pragma unroll
+  for (int e = 0; e < K; ++e) out[i * K + e] = v[e];
+}
+
+// Adjoint of k_small: stages S-1 .. 0; the last stage's entries carry N/k
+// (undone by sc_top = k/N), the final stage scales by sc_fin = 1/N.
+template <class R, int S>
+__global__ void __launch_bounds__(256) k_small_inv(const typename KT<R>::C* __restrict__ in,
+                                                   typename KT<R>::C* __restrict__ out, uint64_t batch,
+                                                   const typename KT<R>::C* __restrict__ tw, R sc_top, R sc_fin) {
+  using C = typename KT<R>::C;
+  constexpr int K = 1 << S;
+  const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= batch) return;
+  C v[K];
+#pragma unroll
+  for (int e = 0; e < K; ++e) v[e] = in[i * K + e];
+#pragma unroll
+  for (int m1 = S - 1; m1 >= 0; --m1) {
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+      if ((e >> m1) & 1) continue;
+      const C w = __ldg(tw + (1u << m1) + (e & ((1 << m1) - 1)));
+      const bool top = m1 == S - 1, fin = m1 == 0;
+      if (top || fin)
+        ibfly_scaled(v[e], v[e | (1 << m1)], w, fin ? sc_fin : R(1), (top ? sc_top : R(1)) * (fin ? sc_fin : R(1)));
+      else
+        ibfly(v[e], v[e | (1 << m1)], w);
+    }
+  }
+  if constexpr (S == 0) {
+    v[0].x *= sc_fin;
+    v[0].y *= sc_fin;
   }
 #pragma unroll
   for (int e = 0; e < K; ++e) out[i * K + e] = v[e];

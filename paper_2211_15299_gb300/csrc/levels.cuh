@@ -7,10 +7,10 @@
 
 namespace sdft {
 
-template <class R, int PLO, int PHI, bool LAST>
+template <class R, int PLO, int PHI, bool LAST, bool INV = false>
 sdft_status launch_level(int grid, const CUtensorMap& src, const CUtensorMap& dst, const LevelArgs<R>& a,
                          cudaStream_t st) {
-  auto fn = k_level<R, PLO, PHI, LAST>;
+  auto fn = k_level<R, PLO, PHI, LAST, INV>;
   sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(kLevelSmem));
   if (s != SDFT_OK) return s;
   fn<<<grid, KT<R>::NT, kLevelSmem, st>>>(src, dst, a);
@@ -19,7 +19,7 @@ sdft_status launch_level(int grid, const CUtensorMap& src, const CUtensorMap& ds
 }
 
 // Level 0: stage bits [0, PHI).
-template <class R, int PHI = 5>
+template <class R, bool INV = false, int PHI = 5>
 sdft_status dispatch_first(int phi, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
                            const LevelArgs<R>& a, cudaStream_t st) {
   constexpr int TB = KT<R>::TB;
@@ -28,17 +28,17 @@ sdft_status dispatch_first(int phi, bool last, int grid, const CUtensorMap& src,
   } else {
     if (phi == PHI) {
       if constexpr (PHI == TB) {
-        if (!last) return launch_level<R, 0, PHI, false>(grid, src, dst, a, st);
+        if (!last) return launch_level<R, 0, PHI, false, INV>(grid, src, dst, a, st);
       }
       if (!last) return SDFT_ERR_UNSUPPORTED;
-      return launch_level<R, 0, PHI, true>(grid, src, dst, a, st);
+      return launch_level<R, 0, PHI, true, INV>(grid, src, dst, a, st);
     }
-    return dispatch_first<R, PHI + 1>(phi, last, grid, src, dst, a, st);
+    return dispatch_first<R, INV, PHI + 1>(phi, last, grid, src, dst, a, st);
   }
 }
 
 // Later levels: virtual stage bits [TB - Q, TB).
-template <class R, int Q = 1>
+template <class R, bool INV = false, int Q = 1>
 sdft_status dispatch_later(int q, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
                            const LevelArgs<R>& a, cudaStream_t st) {
   constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
@@ -46,9 +46,9 @@ sdft_status dispatch_later(int q, bool last, int grid, const CUtensorMap& src, c
     return SDFT_ERR_UNSUPPORTED;
   } else {
     if (q == Q)
-      return last ? launch_level<R, TB - Q, TB, true>(grid, src, dst, a, st)
-                  : launch_level<R, TB - Q, TB, false>(grid, src, dst, a, st);
-    return dispatch_later<R, Q + 1>(q, last, grid, src, dst, a, st);
+      return last ? launch_level<R, TB - Q, TB, true, INV>(grid, src, dst, a, st)
+                  : launch_level<R, TB - Q, TB, false, INV>(grid, src, dst, a, st);
+    return dispatch_later<R, INV, Q + 1>(q, last, grid, src, dst, a, st);
   }
 }
 
@@ -143,6 +143,101 @@ sdft_status launch_plan(const Plan& p, uint64_t batch, const void* in, void* out
     if (s != SDFT_OK) return s;
   }
   return SDFT_OK;
+}
+
+template <class R, int S = 0>
+sdft_status dispatch_small_inv(int s, uint64_t batch, const void* in, void* out, const void* tw, double sc_top,
+                               double sc_fin, cudaStream_t st) {
+  using C = typename KT<R>::C;
+  if constexpr (S > int(kSmallMax)) {
+    return SDFT_ERR_UNSUPPORTED;
+  } else {
+    if (s == S) {
+      const uint64_t blocks = (batch + 255) / 256;
+      if (blocks > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
+      k_small_inv<R, S><<<unsigned(blocks), 256, 0, st>>>(static_cast<const C*>(in), static_cast<C*>(out), batch,
+                                                          static_cast<const C*>(tw), R(sc_top), R(sc_fin));
+      const cudaError_t e = cudaGetLastError();
+      return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
+    }
+    return dispatch_small_inv<R, S + 1>(s, batch, in, out, tw, sc_top, sc_fin, st);
+  }
+}
+
+// Synthesis (the adjoint network scaled by 1/N): the levels in reverse order,
+// each running its passes in reverse. The first level applied reads `in`, the
+// others work in place on `out`.
+template <class R>
+sdft_status launch_plan_inv(const Plan& p, uint64_t batch, const void* in, void* out, cudaStream_t st) {
+  using C = typename KT<R>::C;
+  constexpr int TB = KT<R>::TB, CB = KT<R>::CB, ES = KT<R>::ES;
+  const double scale = std::ldexp(1.0, int(p.M) - int(p.s));
+  const double inv_n = std::ldexp(1.0, -int(p.M));
+  if (p.levels.empty()) return dispatch_small_inv<R>(int(p.s), batch, in, out, p.d_tw, 1.0 / scale, inv_n, st);
+
+  const int max_grid = 2 * sm_count();
+  const void* src_base = in;
+  for (size_t j = p.levels.size() - 1; j >= 1; --j) {
+    const Level& L = p.levels[j];
+    const uint32_t Q = L.hi - L.lo;
+    const uint64_t Z = batch << (p.s - L.hi);
+    if (Z > 0x7fffffffull || (1ull << (L.lo - CB)) > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
+    CUtensorMap ms, md;
+    const uint64_t dims[4] = {32, 1ull << (L.lo - CB), 1ull << Q, Z};
+    const uint64_t strides[3] = {128, (1ull << L.lo) * ES, (1ull << L.hi) * ES};
+    const uint32_t box[4] = {32, 1u << L.lg, 1u << Q, 1};
+    sdft_status s = encode_map(&ms, src_base, dims, strides, box);
+    if (s == SDFT_OK) s = encode_map(&md, out, dims, strides, box);
+    if (s != SDFT_OK) return s;
+    LevelArgs<R> a{};
+    for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
+    a.n_tiles = L.n_gb * Z;
+    a.nB = Z;
+    a.a_step1 = int32_t(1u << L.lg);
+    a.b_step1 = 0;
+    a.b_step3 = 1;
+    a.tw_first = 1u << L.plo;
+    a.tw = static_cast<const C*>(p.d_tw) + L.tw_off;
+    a.tw_len = L.tw_len;
+    a.tw_stride = L.tw_len;
+    a.scale = scale;
+    a.inv_n = inv_n;
+    a.status = p.d_status;
+    a.timeout_ns = wait_timeout_ns();
+    const int grid = int(a.n_tiles < uint64_t(max_grid) ? a.n_tiles : uint64_t(max_grid));
+    s = dispatch_later<R, true>(int(Q), L.last, grid, ms, md, a, st);
+    if (s != SDFT_OK) return s;
+    src_base = out;
+  }
+  const Level& L = p.levels[0];
+  const uint64_t rows_per_tile = 1ull << (TB - CB);
+  const uint64_t rows = (batch * p.k) >> CB;
+  const uint64_t n_tiles = (rows + rows_per_tile - 1) / rows_per_tile;
+  if (rows > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
+  CUtensorMap ms, md;
+  const uint64_t dims[4] = {32, rows, 1, 1};
+  const uint64_t strides[3] = {128, rows * 128, rows * 128};
+  const uint32_t box[4] = {32, uint32_t(rows_per_tile), 1, 1};
+  sdft_status s = encode_map(&ms, src_base, dims, strides, box);
+  if (s == SDFT_OK) s = encode_map(&md, out, dims, strides, box);
+  if (s != SDFT_OK) return s;
+  LevelArgs<R> a{};
+  for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
+  a.n_tiles = n_tiles;
+  a.nB = n_tiles;
+  a.a_step1 = 0;
+  a.b_step1 = int32_t(rows_per_tile);
+  a.b_step3 = 0;
+  a.tw_first = 0;
+  a.tw = static_cast<const C*>(p.d_tw) + L.tw_off;
+  a.tw_len = L.tw_len;
+  a.tw_stride = 0;
+  a.scale = scale;
+  a.inv_n = inv_n;
+  a.status = p.d_status;
+  a.timeout_ns = wait_timeout_ns();
+  const int grid = int(n_tiles < uint64_t(max_grid) ? n_tiles : uint64_t(max_grid));
+  return dispatch_first<R, true>(int(L.hi), L.last, grid, ms, md, a, st);
 }
 
 }  // namespace sdft
