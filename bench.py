@@ -221,6 +221,16 @@ def run_ours(args):
 
     tpi = time_device_steps(step64_per_instance, 3, 1, flush, stream)
     fp64_per_instance = n_pi * k / statistics.mean(tpi)
+    # synthesis (the inverse map) on the same batch, graph-replayed
+    ysyn = torch.empty_like(x32)
+
+    def step_syn(s=None):
+        plan32.synthesize(y32, ysyn, stream=(s or stream).cuda_stream)
+
+    ts = time_graph(step_syn, max(3, args.steps // 4), 3, flush, stream)
+    synthesis = {"coeffs_per_s": coeffs_per_step / statistics.mean(ts), "ms_per_step": 1e3 * statistics.mean(ts),
+                 "frac_of_peak": alg_bytes / statistics.mean(ts) / 1e9 / peak}
+    del ysyn
     # context only: a library batched k-point C2C FFT (cuFFT through torch.fft)
     # over the same batch moves the same bytes with a regular twiddle pattern
     yfft = torch.empty_like(x32)
@@ -283,6 +293,7 @@ def run_ours(args):
                  "per_instance_sample": n_pi, "fp32_speedup_vs_per_instance": value / ws / fp64_per_instance},
         "rel_l2_fp32_vs_fp64": rel_fp32_vs_fp64,
         "fft_ceiling": fft_ceiling,
+        "synthesis": synthesis,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
