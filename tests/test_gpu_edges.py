@@ -1,0 +1,92 @@
+"""Edge cases on the GPU: the largest N, the full DFT (J = Z_N), empty
+batches, the smallest supports."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+@pytest.mark.parametrize("s", [5, 13])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_largest_N(s, prec):
+    # N = 2^62 (the largest this build accepts): N/k = 2^(62-s) folded into the
+    # last stage, twiddle residues up to 61 bits
+    if prec == 1 and s > 12:
+        pytest.skip("complex128 at s = 5 only")
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan
+    M = 62
+    rng = np.random.default_rng(6200 + s)
+    piv = np.sort(rng.choice(np.arange(M), size=s, replace=False))
+    J = W.homogeneous_support(M, piv, rng)
+    plan = Plan(M, J, prec)
+    Jc = O.canonical_support_by_key(J, piv)
+    C = W.complex_gaussian((2, J.size), rng)
+    F = O.synthesize_levels(M, piv, Jc, C)
+    np_dt = np.complex64 if prec == 0 else np.complex128
+    x = torch.from_numpy(F.astype(np_dt)).cuda()
+    y = plan.execute_strided(x)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    got = y.cpu().numpy().astype(np.complex128)
+    ref = O.transform_levels(M, piv, Jc, x.cpu().numpy().astype(np.complex128))
+    tol = 1e-5 if prec == 0 else 1e-12
+    assert rel_l2(got, ref) < tol and rel_l2(got, C) < (2e-6 if prec == 0 else 1e-11)
+
+
+@pytest.mark.parametrize("M", [10, 12, 14])
+def test_full_support_is_the_dft(M):
+    # J = Z_N: pivots 0..M-1, the transform is the N-point DFT of the samples
+    # taken in sample order (compared with a library FFT)
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan
+    N = 1 << M
+    plan = Plan(M, np.arange(N, dtype=np.uint64), 0)
+    I = plan.sample_indices.astype(np.int64)
+    Jc = plan.support_order.astype(np.int64)
+    rng = np.random.default_rng(M)
+    f = W.complex_gaussian((3, N), rng)
+    x = torch.from_numpy(f[:, I].astype(np.complex64)).cuda()
+    y = plan.execute_strided(x).cpu().numpy().astype(np.complex128)
+    ref = np.fft.fft(f, axis=1)[:, Jc]
+    assert rel_l2(y, ref) < 1e-5
+
+
+def test_empty_batches_are_no_ops():
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan, Sas, _native as N
+    rng = np.random.default_rng(3)
+    piv = W.random_pivots(16, 8, rng)
+    plan = Plan(16, W.homogeneous_support(16, piv, rng), 0)
+    buf = torch.zeros(16, dtype=torch.complex64, device="cuda")
+    N.sdft_execute_strided(plan.handle, 0, buf, buf, None)
+    N.sdft_synthesize_strided(plan.handle, 0, buf, buf, None)
+    sas = Sas(10, [0, 512, 1, 6, 7], "c64")
+    N.sdft_sas_execute(sas.handle, 0, buf, buf, buf[8:], None)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0 and torch.count_nonzero(buf) == 0
+
+
+@pytest.mark.parametrize("J", [[5], [3, 7], [0, 1, 2]])
+def test_smallest_supports_through_sas(J):
+    torch = _torch()
+    from paper_2211_15299_gb300 import Sas
+    M = 4
+    p = Sas(M, J, "c128")
+    rng = np.random.default_rng(len(J))
+    c = W.complex_gaussian(len(J), rng)
+    order = [int(j) for j in p.support_order]
+    F = O.sas_samples_direct(M, order, c, p.sample_indices)
+    y = p.execute(torch.from_numpy(F.reshape(1, -1)).cuda())
+    torch.cuda.synchronize()
+    assert rel_l2(y[0].cpu().numpy(), c) < 1e-12 * max(1.0, p.max_cond)
