@@ -56,7 +56,7 @@ def test_full_support_is_the_dft(M):
     Jc = plan.support_order.astype(np.int64)
     rng = np.random.default_rng(M)
     f = W.complex_gaussian((3, N), rng)
-    x = torch.from_numpy(f[:, I].astype(np.complex64)).cuda()
+    x = torch.from_numpy(np.ascontiguousarray(f[:, I].astype(np.complex64))).cuda()
     y = plan.execute_strided(x).cpu().numpy().astype(np.complex128)
     ref = np.fft.fft(f, axis=1)[:, Jc]
     assert rel_l2(y, ref) < 1e-5
