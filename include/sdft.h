@@ -248,7 +248,7 @@ sdft_status sdft_batch_set_wait(sdft_batch batch, uint64_t timeout_ns, uint32_t 
 /* Order of a batch's work items (see sdft_batch_set_schedule). No paper
  * counterpart: scheduling of many instances is a property of this library. */
 typedef enum {
-  SDFT_SCHEDULE_AUTO = 0,         /* lanes when there are at least 2 x grid units, else round robin */
+  SDFT_SCHEDULE_AUTO = 0,         /* the library's default (round robin) */
   SDFT_SCHEDULE_LANES = 1,        /* each instance's levels in one CTA, largest first to the least-loaded CTA */
   SDFT_SCHEDULE_ROUND_ROBIN = 2   /* instances in packed order over consecutive CTAs */
 } sdft_schedule;

@@ -218,7 +218,9 @@ constexpr int mid_pass_hi(int TB, int PLO, int PHI) {
 // (m1 ascending, then e mod 2^q). SRC = kTwGlobal: `w` is the absolute-indexed
 // table in global memory. SRC = kTwShared: `wsm` is the shared-memory address of
 // the absolute-indexed table region.
-template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SRC>
+// BAR = 1: the pass ends with named barrier 1 over the NT compute threads
+// instead of a CTA barrier (a kernel with a separate producer warp).
+template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SRC, int BAR = 0>
 __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc,
                                           uint32_t wsm = 0) {
   using C = typename KT<R>::C;
@@ -276,7 +278,10 @@ __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w,
     }
   }
   if constexpr (FENCE) ptx::fence_proxy_async_smem();  // the tile leaves through TMA next
-  __syncthreads();
+  if constexpr (BAR == 0)
+    __syncthreads();
+  else
+    ptx::named_bar_sync(1, KT<R>::NT);
 }
 
 // Load the register twiddles of every B > 0 pass from a table indexed
@@ -326,7 +331,8 @@ struct NoHook {
 // MIDSM: the memory-read pass takes its twiddles from the shared-memory copy
 // at `wsm` instead of global memory. `hook` runs after the first pass's
 // barrier (the level kernel issues its next load there).
-template <class R, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0, bool MIDSM = false, class Hook = NoHook>
+template <class R, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0, bool MIDSM = false, class Hook = NoHook,
+          int BAR = 0>
 __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* wreg, const typename KT<R>::C* w0,
                                            const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc,
                                            uint32_t wsm = 0, const Hook& hook = Hook()) {
@@ -336,18 +342,18 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
     constexpr bool FINAL = (SHI == PHI);
     constexpr int SRC = pass_src(TB, B);
     if constexpr (SRC == kTwParam) {
-      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, w0, tid, sc);
+      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR>(buf, w0, tid, sc);
     } else if constexpr (SRC == kTwGlobal) {
       if constexpr (MIDSM)
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared>(buf, twg, tid, sc, wsm);
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR>(buf, twg, tid, sc, wsm);
       else
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, twg, tid, sc);
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR>(buf, twg, tid, sc);
     } else {
-      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC>(buf, wreg + ROFF, tid, sc);
+      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR>(buf, wreg + ROFF, tid, sc);
     }
     if constexpr (P == 0) hook();
     constexpr int RNEXT = (SRC == kTwReg) ? ROFF + pass_ntw(B, SLO, SHI) : ROFF;
-    run_passes<R, PLO, PHI, LAST, P + 1, RNEXT, MIDSM, Hook>(buf, wreg, w0, twg, tid, sc, wsm, hook);
+    run_passes<R, PLO, PHI, LAST, P + 1, RNEXT, MIDSM, Hook, BAR>(buf, wreg, w0, twg, tid, sc, wsm, hook);
   }
 }
 

@@ -4,7 +4,10 @@
 //
 // Items (host-built, see batch.cu) are processed round-robin: CTA c takes items
 // c, c + G, c + 2G, ... in list order, on a cooperatively launched grid (all
-// CTAs resident). Item kinds:
+// CTAs resident). Each CTA has NT compute threads and one producer warp: the
+// producer loads tiles (TMA) after their dependencies are met, stores computed
+// tiles and publishes counters; the compute threads only wait for tiles
+// (full barriers) and hand buffers back (empty barriers). Item kinds:
 //   * small range: up to NT instances with log2 k <= 4, one thread each;
 //   * level-0 tile: 2^(TB - s) whole instances of size 2^s (s <= TB), or one
 //     2^TB chunk of a larger instance (stage bits [0, min(s, TB)));
@@ -58,8 +61,8 @@ struct QArgs {
   uint32_t need_bias;       // added to every dependency target (0; non-zero only to test timeouts)
 };
 
-// Item records are copied into a shared-memory ring kMetaSlots items ahead of
-// use, so the issuing thread never waits on a global load of a record.
+// Item records are copied by the producer into a shared-memory ring three items
+// ahead of use (cp.async), so it never waits on a global load of a record.
 constexpr int kMetaSlots = 6;
 static_assert(sizeof(QItem) % 16 == 0, "items are copied in 16-byte pieces");
 constexpr uint32_t kQueueSmem = kBufs * kTileBytes + 64 + kMetaSlots * sizeof(QItem) + 1024;
@@ -116,7 +119,7 @@ __device__ __forceinline__ void tile_pass_q(char* buf, const typename KT<R>::C* 
     *reinterpret_cast<C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E))) = v[e];
   }
   if constexpr (FENCE) ptx::fence_proxy_async_smem();
-  __syncthreads();
+  ptx::named_bar_sync(1, KT<R>::NT);     // the compute threads only (not the producer warp)
 }
 
 template <class R, int PLO, int PHI, bool LAST, int SB, int P = 0>
@@ -210,157 +213,6 @@ __device__ __forceinline__ void run_small(const QArgs& a, const QItem& it, uint3
   }
 }
 
-// Per-CTA pipeline of the queue kernel (3 tile buffers, round-robin items).
-template <class R>
-struct QPipe {
-  const QParams& prm;
-  char* smem;
-  uint32_t bar0, tid;
-  uint64_t c, G, n;
-  uint32_t phases = 0;        // bit b: parity of the next completion of buffer b
-  uint32_t inflight = 0;      // thread 0: buffers with an issued, unconsumed load
-  uint32_t sig1 = kNone, sig2 = kNone;   // signals of items j-1 and j-2, not yet published
-  bool failed = false;        // thread 0: a dependency wait expired
-  bool aborted = false;
-
-  __device__ __forceinline__ QPipe(const QParams& p, char* sm, uint32_t b0, uint32_t t)
-      : prm(p), smem(sm), bar0(b0), tid(t), c(blockIdx.x), G(gridDim.x) {
-    n = (p.a.n_items > c) ? (p.a.n_items - c + G - 1) / G : 0;
-  }
-  __device__ __forceinline__ static bool is_tma(const QItem& it) { return it.variant != kVSmall && it.variant != kVNop; }
-
-  // Record of item j in the ring; valid for all threads once thread 0 has
-  // waited for its copy and a barrier has passed.
-  __device__ __forceinline__ const QItem& meta(uint64_t j) const {
-    return reinterpret_cast<const QItem*>(smem + kBufs * kTileBytes + 64)[j % kMetaSlots];
-  }
-
-  // Thread 0: start copying item j's record into its ring slot (one cp.async
-  // group per call, empty past the end of the CTA's items).
-  __device__ __forceinline__ void fetch_record(uint64_t j) const {
-    if (j < n) {
-      const char* src = reinterpret_cast<const char*>(&prm.a.items[c + j * G]);
-      const uint32_t dst = ptx::smem_addr(&meta(j));
-#pragma unroll
-      for (uint32_t o = 0; o < sizeof(QItem); o += 16) ptx::cp_async_16(dst + o, src + o);
-    }
-    ptx::cp_async_commit();
-  }
-
-  __device__ __forceinline__ void issue_load(uint64_t j) {   // thread 0; record j has landed
-    const QItem& it = meta(j);
-    if (!is_tma(it)) return;
-    if (it.dep != kNone) {
-      const uint32_t* ctr = prm.a.counters + it.dep;
-      const uint32_t need = it.need + prm.a.need_bias;
-      if (ptx::ld_acquire_gpu(ctr) < need) {
-        const uint64_t t0 = ptx::globaltimer();
-        while (ptx::ld_acquire_gpu(ctr) < need) {
-          if (ptx::globaltimer() - t0 > prm.a.timeout_ns) {
-            failed = true;
-            break;
-          }
-        }
-      }
-      ptx::fence_proxy_async_global();
-    }
-    const uint32_t b = uint32_t(j % kBufs);
-    const uint32_t bar = bar0 + 8 * b;
-    const uint32_t bytes = (it.variant < 16) ? (128u << (it.map / 2)) : kTileBytes;
-    ptx::mbar_arrive_expect_tx(bar, bytes);
-    // Samples and intermediates are read once: first out of L2.
-    ptx::tma_load_4d_hint(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], bar, 0, it.c1, 0, it.c3,
-                          ptx::policy_evict_first());
-    inflight |= 1u << b;
-    prefetch_tables(it);
-  }
-
-  // Twiddle tables of an item into L2 while its tile is still in flight.
-  __device__ __forceinline__ void prefetch_tables(const QItem& it) const {
-    constexpr int TB = KT<R>::TB;
-    constexpr uint32_t ES = KT<R>::ES;
-    if (it.variant >= 16) {                        // later level: entries [2^plo, 2^TB)
-      const int Q = (it.variant - 16) / 2 + 1;
-      const uint32_t first = 1u << (TB - Q);
-      ptx::prefetch_l2(static_cast<const char*>(it.tw) + first * ES, ((1u << TB) - first) * ES);
-    } else if (it.variant == kVFirstChunk) {
-      ptx::prefetch_l2(it.tw, (1u << TB) * ES);
-    } else {                                       // whole instances of size 2^s
-      // The first instance's table here; the others' two items ahead, by the
-      // threads of warps 1.. (see the kernel loop).
-      const int s = it.variant - 1 + 5;
-      ptx::prefetch_l2(it.tw, (1u << s) * ES);
-    }
-  }
-
-  // Wait for item j's tile; false if the CTA must stop.
-  __device__ __forceinline__ bool begin(uint64_t j, const QItem& it) {
-    const uint32_t b = uint32_t(j % kBufs);
-    bool ok = true;
-    if (is_tma(it)) {
-      ok = ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, prm.a.timeout_ns);
-      if (ok) {
-        phases ^= 1u << b;
-        if (tid == 0) inflight &= ~(1u << b);
-      }
-    }
-    if (__syncthreads_or(!ok || (tid == 0 && failed))) {
-      aborted = true;
-      return false;
-    }
-    return true;
-  }
-
-  // After item j's compute: store it, publish item j-2, prefetch item j + 2.
-  // Every item commits one bulk group (empty if it stores nothing), so group g
-  // is item g. A counter is released two items after its store was issued,
-  // once that store is complete; the buffer of item j-1 is reused as soon as
-  // its store has read shared memory. A consumer therefore sits at least four
-  // items after its producer in the producing CTA (4 x grid list positions).
-  __device__ __forceinline__ void end(uint64_t j, const QItem& it) {
-    if (tid != 0) return;
-    if (is_tma(it)) {
-      const uint32_t slot = (it.variant < 16) ? uint32_t(it.map) + 1u : uint32_t(it.map);
-      // An intermediate (a later level reads it back) stays in L2 ahead of
-      // streaming data; a final result leaves first.
-      const uint64_t pol = (it.sig != kNone) ? ptx::policy_evict_last() : ptx::policy_evict_first();
-      ptx::tma_store_4d_hint(&prm.maps[slot], ptx::smem_addr(smem + (j % kBufs) * kTileBytes), 0, it.c1, 0, it.c3,
-                             pol);
-    }
-    ptx::bulk_commit();
-    if (sig2 != kNone) {                 // store of item j-2 complete: publish it
-      ptx::bulk_wait<2>();
-      ptx::fence_proxy_async_global();
-      ptx::red_add_release_gpu(prm.a.counters + sig2, 1u);
-    }
-    sig2 = sig1;
-    sig1 = is_tma(it) ? it.sig : kNone;
-    ptx::cp_async_wait<2>();             // records up to j + 3 have landed
-    if (j >= 1 && j + 2 < n) {           // into the buffer of item j-1
-      ptx::bulk_wait_read<1>();
-      issue_load(j + 2);
-    }
-    fetch_record(j + kMetaSlots);        // into the slot of item j, read by all threads already
-  }
-
-  __device__ __forceinline__ void finish() {
-    if (tid != 0) return;
-    ptx::cp_async_wait<0>();
-    if (aborted || failed) {
-      // Let loads already issued land before the CTA's shared memory is released.
-      for (int b = 0; b < kBufs; ++b)
-        if (inflight >> b & 1u) ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, prm.a.timeout_ns);
-      atomicExch(prm.a.status, int(SDFT_ERR_TIMEOUT));
-    }
-    ptx::bulk_wait<0>();
-    if (!aborted) {
-      ptx::fence_proxy_async_global();
-      if (sig2 != kNone) ptx::red_add_release_gpu(prm.a.counters + sig2, 1u);
-      if (sig1 != kNone) ptx::red_add_release_gpu(prm.a.counters + sig1, 1u);
-    }
-  }
-};
-
 // A single-table item (a 2^TB chunk, a one-instance tile, a later-level group
 // block): the passes of k_level with the top pass's twiddles loaded into
 // registers for this item (the previous item prefetched them into L1).
@@ -371,7 +223,7 @@ __device__ __forceinline__ void run_single(char* buf, const typename KT<R>::C* t
   C wreg[NREG > 0 ? NREG : 1];
   load_reg_twiddles<R, PLO, PHI>(tab, tid, wreg);
   // pass 0 reads entry 2^m1 + u as w0[2^m1 - 1 + u]: w0 = tab + 1
-  run_passes<R, PLO, PHI, LAST>(buf, wreg, tab + 1, tab, tid, sc);
+  run_passes<R, PLO, PHI, LAST, 0, 0, false, NoHook, 1>(buf, wreg, tab + 1, tab, tid, sc);
 }
 
 template <class R, int Q = 1>
@@ -395,13 +247,157 @@ __device__ __forceinline__ void dispatch_later_prefetch(int v, const typename KT
   }
 }
 
+// Shared-memory layout after the tile buffers: full[3] and empty[3] mbarriers,
+// the abort flag, then the record ring.
+constexpr uint32_t kQFull = 0, kQEmpty = 24, kQAbort = 48;
 template <class R>
-__global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ QParams prm) {
+constexpr uint32_t q_threads() { return KT<R>::NT + 32; }   // compute threads + one producer warp
+
+__device__ __forceinline__ bool q_is_tma(const QItem& it) { return it.variant != kVSmall && it.variant != kVNop; }
+
+__device__ __forceinline__ const QItem& q_meta(char* smem, uint64_t j) {
+  return reinterpret_cast<const QItem*>(smem + kBufs * kTileBytes + 64)[j % kMetaSlots];
+}
+
+// The producer warp's loop (lane 0). CTA c takes items c, c + G, ... Iteration
+// j: (1) once item i = j - 3 is computed (empty[i % 3]), store it from its
+// buffer, commit one bulk group, and publish item i - 1's counter (its store
+// complete); (2) load item j into the freed buffer (after its dependency, if
+// any, is met) and announce it on full[j % 3]; fetch record j + 3. A counter is
+// published before the dependency wait of the item four places later in the
+// same CTA, so items that wait on one another sit at least 4 x grid list
+// positions apart and every wait ends (all CTAs are resident).
+template <class R>
+__device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint64_t n) {
+  const uint64_t c = blockIdx.x, G = gridDim.x;
+  const uint32_t bars = ptx::smem_addr(smem + kBufs * kTileBytes);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kBufs * kTileBytes + kQAbort);
+  const uint64_t tmo = prm.a.timeout_ns;
+  auto fetch_record = [&](uint64_t j) {
+    if (j < n) {
+      const char* src = reinterpret_cast<const char*>(&prm.a.items[c + j * G]);
+      const uint32_t dst = ptx::smem_addr(&q_meta(smem, j));
+#pragma unroll
+      for (uint32_t o = 0; o < sizeof(QItem); o += 16) ptx::cp_async_16(dst + o, src + o);
+    }
+    ptx::cp_async_commit();
+  };
+  for (uint64_t j = 0; j < 3; ++j) fetch_record(j);
+  uint32_t pending_sig = kNone;       // counter of the last stored item, not yet published
+  uint32_t inflight = 0;              // buffers with a load whose tile is not yet consumed
+  uint32_t load_par = 0;              // bit q: phase parity of buffer q's last load
+  const void* last_tab = nullptr;     // table of the last item whose tables were prefetched
+  bool failed = false;
+  uint64_t j = 0;
+  for (; j < n + kBufs; ++j) {
+    const uint32_t b = uint32_t(j % kBufs);
+    if (j >= kBufs) {
+      const uint64_t i = j - kBufs;
+      if (!ptx::mbar_wait_bounded(bars + kQEmpty + 8 * b, uint32_t((i / kBufs) & 1), tmo)) {
+        failed = true;
+        break;
+      }
+      inflight &= ~(1u << b);
+      const QItem& it = q_meta(smem, i);
+      const bool tma = q_is_tma(it);
+      if (tma) {
+        const uint32_t slot = (it.variant < 16) ? uint32_t(it.map) + 1u : uint32_t(it.map);
+        // an intermediate (read back by a later level) stays in L2 ahead of streaming data
+        const uint64_t pol = (it.sig != kNone) ? ptx::policy_evict_last() : ptx::policy_evict_first();
+        ptx::tma_store_4d_hint(&prm.maps[slot], ptx::smem_addr(smem + b * kTileBytes), 0, it.c1, 0, it.c3, pol);
+      }
+      ptx::bulk_commit();
+      if (pending_sig != kNone) {      // the previous store is complete: publish it
+        ptx::bulk_wait<1>();
+        ptx::fence_proxy_async_global();
+        ptx::red_add_release_gpu(prm.a.counters + pending_sig, 1u);
+      }
+      pending_sig = tma ? it.sig : kNone;
+      if (j < n) ptx::bulk_wait_read<0>();   // the buffer is refilled below
+    }
+    if (j < n) {
+      ptx::cp_async_wait<2>();         // record j has landed
+      const QItem& it = q_meta(smem, j);
+      const uint32_t full = bars + kQFull + 8 * b;
+      if (q_is_tma(it)) {
+        if (it.dep != kNone) {
+          const uint32_t* ctr = prm.a.counters + it.dep;
+          const uint32_t need = it.need + prm.a.need_bias;
+          if (ptx::ld_acquire_gpu(ctr) < need) {
+            const uint64_t t0 = ptx::globaltimer();
+            while (ptx::ld_acquire_gpu(ctr) < need) {
+              if (ptx::globaltimer() - t0 > tmo) {
+                failed = true;
+                break;
+              }
+            }
+          }
+          if (failed) {
+            // wake the compute warps at this item: they stop at the abort flag
+            *abort_flag = 1;
+            ptx::mbar_arrive(full);
+            break;
+          }
+          ptx::fence_proxy_async_global();
+        }
+        const uint32_t bytes = (it.variant < 16) ? (128u << (it.map / 2)) : kTileBytes;
+        ptx::mbar_arrive_expect_tx(full, bytes);
+        // samples and intermediates are read once: first out of L2
+        ptx::tma_load_4d_hint(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], full, 0, it.c1, 0, it.c3,
+                              ptx::policy_evict_first());
+        inflight |= 1u << b;
+        load_par = (load_par & ~(1u << b)) | (uint32_t((j / kBufs) & 1) << b);
+        // the item's tables into L2 while its tile is in flight (once per table
+        // in a row of items: repeated bulk prefetches of the same lines queue in
+        // front of the tile copies)
+        constexpr int TB = KT<R>::TB;
+        constexpr uint32_t ES = KT<R>::ES;
+        if (it.variant >= 16) {
+          if (it.tw != last_tab) {
+            const uint32_t first = 1u << (TB - ((it.variant - 16) / 2 + 1));
+            ptx::prefetch_l2(static_cast<const char*>(it.tw) + first * ES, ((1u << TB) - first) * ES);
+          }
+        } else if (it.variant == kVFirstChunk || it.variant == q_variant_first(TB)) {
+          if (it.tw != last_tab) ptx::prefetch_l2(it.tw, (1u << TB) * ES);
+        } else {
+          const int ss = it.variant - 1 + 5;
+          const uint32_t cnt = it.count < 16u ? it.count : 16u;
+          const void* last = nullptr;
+          for (uint32_t g = 0; g < cnt; ++g) {        // distinct tables only
+            const void* tw = prm.a.insts[it.inst + g].tw;
+            if (tw && tw != last) ptx::prefetch_l2(tw, (1u << ss) * ES);
+            last = tw;
+          }
+        }
+        last_tab = it.tw;
+      } else {
+        ptx::mbar_arrive(full);        // nothing to load: the phase completes at once
+      }
+      fetch_record(j + 3);             // into the slot of item j - 3, computed already
+    }
+  }
+  ptx::cp_async_wait<0>();
+  if (failed) {
+    // let every issued load land before the CTA's shared memory is released
+    for (int q = 0; q < kBufs; ++q)
+      if (inflight >> q & 1u) ptx::mbar_wait_bounded(bars + kQFull + 8 * q, (load_par >> q) & 1u, tmo);
+    atomicExch(prm.a.status, int(SDFT_ERR_TIMEOUT));
+  }
+  ptx::bulk_wait<0>();
+  if (!failed && pending_sig != kNone) {
+    ptx::fence_proxy_async_global();
+    ptx::red_add_release_gpu(prm.a.counters + pending_sig, 1u);
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(q_threads<R>(), 2) k_queue(const __grid_constant__ QParams prm) {
   const QArgs& a = prm.a;
   extern __shared__ char smem_raw[];
   char* smem = align1024(smem_raw);
-  const uint32_t bar0 = ptx::smem_addr(smem + kBufs * kTileBytes);
+  const uint32_t bars = ptx::smem_addr(smem + kBufs * kTileBytes);
   const uint32_t tid = threadIdx.x;
+  constexpr uint32_t NT = KT<R>::NT;
   {
     const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 64 + kMetaSlots * uint32_t(sizeof(QItem));
     int bad = 0;
@@ -413,25 +409,37 @@ __global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ 
       return;
     }
   }
-  QPipe<R> q(prm, smem, bar0, tid);
-  if (q.n == 0) return;
+  const uint64_t c = blockIdx.x, G = gridDim.x;
+  const uint64_t n = (a.n_items > c) ? (a.n_items - c + G - 1) / G : 0;
+  if (n == 0) return;
   if (tid == 0) {
-    for (int b = 0; b < kBufs; ++b) ptx::mbar_init(bar0 + 8 * b, 1);
+    for (int b = 0; b < kBufs; ++b) {
+      ptx::mbar_init(bars + kQFull + 8 * b, 1);        // the producer's arrival (+ the tile's bytes)
+      ptx::mbar_init(bars + kQEmpty + 8 * b, NT);      // every compute thread, once done with the buffer
+    }
+    *reinterpret_cast<volatile int*>(smem + kBufs * kTileBytes + kQAbort) = 0;
     ptx::fence_mbar_init();
-    for (int j = 0; j < kMetaSlots; ++j) q.fetch_record(uint64_t(j));
-    ptx::cp_async_wait<kMetaSlots - kBufs>();     // records 0 .. kBufs-1
-    for (uint64_t j = 0; j < q.n && j < uint64_t(kBufs); ++j) q.issue_load(j);
   }
   __syncthreads();
+  if (tid >= NT) {                     // the producer warp
+    if (tid == NT) q_producer<R>(prm, smem, n);
+    return;
+  }
   using C = typename KT<R>::C;
   constexpr int TB = KT<R>::TB;
-  for (uint64_t j = 0; j < q.n; ++j) {
-    const QItem it = q.meta(j);
+  const volatile int* abort_flag = reinterpret_cast<const volatile int*>(smem + kBufs * kTileBytes + kQAbort);
+  for (uint64_t j = 0; j < n; ++j) {
+    const uint32_t b = uint32_t(j % kBufs);
+    const bool ok = ptx::mbar_wait_bounded(bars + kQFull + 8 * b, uint32_t((j / kBufs) & 1), a.timeout_ns);
+    if (ptx::named_bar_or(1, NT, !ok || *abort_flag != 0)) {
+      if (tid == 0 && !ok) atomicExch(a.status, int(SDFT_ERR_TIMEOUT));
+      break;
+    }
+    const QItem it = q_meta(smem, j);
     const int v = it.variant;
     const C* tab = static_cast<const C*>(it.tw);
     const R sc = R(it.scale);
-    if (!q.begin(j, it)) break;
-    char* buf = smem + (j % kBufs) * kTileBytes;
+    char* buf = smem + b * kTileBytes;
     if (v == kVNop) {
       // nothing to do
     } else if (v == kVSmall) {
@@ -445,26 +453,21 @@ __global__ void __launch_bounds__(KT<R>::NT, 2) k_queue(const __grid_constant__ 
     } else {
       dispatch_first_q<R>(v, buf, a, it, tid);   // several instances per tile
     }
-    if (j + 1 < q.n) {   // the next item's register and L1 twiddles, while this store drains
-      const QItem& nx = q.meta(j + 1);
-      const int nv = nx.variant;
-      const C* nt = static_cast<const C*>(nx.tw);
-      if (nt && nt != tab) {
-        if (nv == kVFirstChunk || nv == q_variant_first(TB)) prefetch_twiddles<R, 0, TB>(nt, tid);
-        else if (nv >= 16 && nv != kVNop) dispatch_later_prefetch<R>(nv, nt, tid);
+    ptx::mbar_arrive(bars + kQEmpty + 8 * b);   // after the final pass's proxy fence and barrier
+    // the next item's register and L1 twiddles, if its tile has landed already
+    if (j + 1 < n) {
+      const uint32_t nb = uint32_t((j + 1) % kBufs);
+      if (ptx::mbar_test_wait(bars + kQFull + 8 * nb, uint32_t(((j + 1) / kBufs) & 1))) {
+        const QItem& nx = q_meta(smem, j + 1);
+        const int nv = nx.variant;
+        const C* nt = static_cast<const C*>(nx.tw);
+        if (nt && nt != tab) {
+          if (nv == kVFirstChunk || nv == q_variant_first(TB)) prefetch_twiddles<R, 0, TB>(nt, tid);
+          else if (nv >= 16 && nv != kVNop) dispatch_later_prefetch<R>(nv, nt, tid);
+        }
       }
     }
-    if (j + 2 < q.n && tid >= 32) {   // tables of a multi-instance tile two items ahead, into L2
-      const QItem& n2 = q.meta(j + 2);
-      const uint32_t g = tid - 32;
-      if (n2.variant >= 1 && n2.variant < q_variant_first(TB) && g < n2.count) {
-        const void* t2 = a.insts[n2.inst + g].tw;
-        if (t2) ptx::prefetch_l2(t2, (1u << (n2.variant - 1 + 5)) * KT<R>::ES);
-      }
-    }
-    q.end(j, it);
   }
-  q.finish();
 }
 
 }  // namespace sdft
@@ -483,7 +486,8 @@ int queue_grid() {
   auto fn = k_queue<R>;
   if (ensure_smem(reinterpret_cast<const void*>(fn), int(kQueueSmem)) != SDFT_OK) return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, KT<R>::NT, kQueueSmem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, q_threads<R>(), kQueueSmem) != cudaSuccess)
+    return 0;
   return per_sm * sm_count();
 }
 
@@ -494,7 +498,7 @@ sdft_status launch_queue(const QParams& prm, int grid, cudaStream_t st) {
   if (s != SDFT_OK) return s;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
-  cfg.blockDim = dim3(KT<R>::NT);
+  cfg.blockDim = dim3(q_threads<R>());
   cfg.dynamicSmemBytes = kQueueSmem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];

@@ -50,12 +50,14 @@ def test_host_only_batch_cannot_execute():
     assert ei.value.name == "SDFT_ERR_NO_DEVICE"
 
 
-def test_lane_schedule_invariants_full_uneven_workload():
-    # 10,000 instances give far more units than CTAs: the lane schedule is used
+@pytest.mark.parametrize("schedule", ["lanes", "round_robin"])
+def test_schedule_invariants_full_uneven_workload(schedule):
+    # 10,000 instances, far more units than CTAs
     from paper_2211_15299_gb300 import Batch
     insts = W.workload_uneven(count=10000)
     plans = _plans(insts)
     b = Batch(plans)
+    b.set_schedule(schedule)
     n_items, n_ctr, grid = b.stats()        # raises if a dependency is closer than 4 x grid
     multi = sum(1 for p in plans if p.s > 12)
     assert n_ctr == multi
