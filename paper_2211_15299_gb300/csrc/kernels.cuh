@@ -331,8 +331,9 @@ struct NoHook {
 // MIDSM: the memory-read pass takes its twiddles from the shared-memory copy
 // at `wsm` instead of global memory. `hook` runs after the first pass's
 // barrier (the level kernel issues its next load there).
+// P0SM: the first pass (B = 0) also reads the shared-memory copy at `wsm`.
 template <class R, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0, bool MIDSM = false, class Hook = NoHook,
-          int BAR = 0>
+          int BAR = 0, bool P0SM = false>
 __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* wreg, const typename KT<R>::C* w0,
                                            const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc,
                                            uint32_t wsm = 0, const Hook& hook = Hook()) {
@@ -342,7 +343,10 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
     constexpr bool FINAL = (SHI == PHI);
     constexpr int SRC = pass_src(TB, B);
     if constexpr (SRC == kTwParam) {
-      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR>(buf, w0, tid, sc);
+      if constexpr (P0SM)
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR>(buf, twg, tid, sc, wsm);
+      else
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR>(buf, w0, tid, sc);
     } else if constexpr (SRC == kTwGlobal) {
       if constexpr (MIDSM)
         tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR>(buf, twg, tid, sc, wsm);
@@ -353,7 +357,7 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
     }
     if constexpr (P == 0) hook();
     constexpr int RNEXT = (SRC == kTwReg) ? ROFF + pass_ntw(B, SLO, SHI) : ROFF;
-    run_passes<R, PLO, PHI, LAST, P + 1, RNEXT, MIDSM, Hook, BAR>(buf, wreg, w0, twg, tid, sc, wsm, hook);
+    run_passes<R, PLO, PHI, LAST, P + 1, RNEXT, MIDSM, Hook, BAR, P0SM>(buf, wreg, w0, twg, tid, sc, wsm, hook);
   }
 }
 

@@ -186,6 +186,14 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<uint64_t>(p)));
 }
 
+// Untiled bulk copy global -> shared (both 16-byte aligned, bytes a multiple of
+// 16), completing on the mbarrier `bar` with complete_tx.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 // Bring `bytes` (a multiple of 16, 16-byte aligned address) into L2 without
 // waiting for it.
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {

@@ -65,7 +65,26 @@ struct QArgs {
 // ahead of use (cp.async), so it never waits on a global load of a record.
 constexpr int kMetaSlots = 6;
 static_assert(sizeof(QItem) % 16 == 0, "items are copied in 16-byte pieces");
-constexpr uint32_t kQueueSmem = kBufs * kTileBytes + 64 + kMetaSlots * sizeof(QItem) + 1024;
+// Per tile buffer, a shared-memory copy of the table entries its first and
+// middle passes read (copied by the producer with the tile, on its barrier).
+template <class R>
+constexpr uint32_t q_tw_bytes() { return 256 * KT<R>::ES; }
+constexpr uint32_t kQTwOff = kBufs * kTileBytes + 64 + kMetaSlots * sizeof(QItem);
+static_assert(kQTwOff % 16 == 0, "table copies need 16-byte alignment");
+template <class R>
+constexpr uint32_t q_smem() { return kQTwOff + kBufs * q_tw_bytes<R>() + 1024; }
+
+// Entries [lo, hi) of an item's table staged in shared memory, for a tile
+// whose stages are [PLO, TB): the first pass's entries (PLO = 0) and the
+// memory-read pass's, when they fit the copy; hi = 0: none.
+constexpr int q_stage_hi(int TB, int PLO) {
+  const int mlo = mid_pass_lo(TB, PLO, TB), mhi = mid_pass_hi(TB, PLO, TB);
+  if (mlo >= mhi || (1 << mhi) > 256) return PLO == 0 ? 16 : 0;
+  return 1 << mhi;
+}
+constexpr int q_stage_lo(int TB, int PLO) {
+  return PLO == 0 ? 0 : (q_stage_hi(TB, PLO) ? (1 << mid_pass_lo(TB, PLO, TB)) : 0);
+}
 
 // Kernel parameters: the arguments and the tensor maps over the packed buffers
 // (maps in parameter space are baked into a captured CUDA graph).
@@ -217,23 +236,28 @@ __device__ __forceinline__ void run_small(const QArgs& a, const QItem& it, uint3
 // block): the passes of k_level with the top pass's twiddles loaded into
 // registers for this item (the previous item prefetched them into L1).
 template <class R, int PLO, int PHI, bool LAST>
-__device__ __forceinline__ void run_single(char* buf, const typename KT<R>::C* tab, R sc, uint32_t tid) {
+__device__ __forceinline__ void run_single(char* buf, const typename KT<R>::C* tab, R sc, uint32_t tid,
+                                           uint32_t wsm) {
   using C = typename KT<R>::C;
-  constexpr int NREG = reg_twiddles(KT<R>::TB, PLO, PHI);
+  constexpr int TB = KT<R>::TB;
+  constexpr int NREG = reg_twiddles(TB, PLO, PHI);
   C wreg[NREG > 0 ? NREG : 1];
   load_reg_twiddles<R, PLO, PHI>(tab, tid, wreg);
-  // pass 0 reads entry 2^m1 + u as w0[2^m1 - 1 + u]: w0 = tab + 1
-  run_passes<R, PLO, PHI, LAST, 0, 0, false, NoHook, 1>(buf, wreg, tab + 1, tab, tid, sc);
+  // staged entries (q_stage_lo/hi) come from shared memory at wsm; the rest from
+  // global memory (pass 0 reads entry 2^m1 + u as w0[2^m1 - 1 + u]: w0 = tab + 1)
+  constexpr bool MID = q_stage_hi(TB, PLO) > 16 || (PLO > 0 && q_stage_hi(TB, PLO) > 0);
+  constexpr bool P0 = PLO == 0;
+  run_passes<R, PLO, PHI, LAST, 0, 0, MID, NoHook, 1, P0>(buf, wreg, tab + 1, tab, tid, sc, wsm);
 }
 
 template <class R, int Q = 1>
 __device__ __forceinline__ void dispatch_later_single(int v, char* buf, const typename KT<R>::C* tab, R sc,
-                                                      uint32_t tid) {
+                                                      uint32_t tid, uint32_t wsm) {
   constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
   if constexpr (Q <= TB - CB) {
-    if (v == q_variant_later(Q, true)) return run_single<R, TB - Q, TB, true>(buf, tab, sc, tid);
-    if (v == q_variant_later(Q, false)) return run_single<R, TB - Q, TB, false>(buf, tab, sc, tid);
-    dispatch_later_single<R, Q + 1>(v, buf, tab, sc, tid);
+    if (v == q_variant_later(Q, true)) return run_single<R, TB - Q, TB, true>(buf, tab, sc, tid, wsm);
+    if (v == q_variant_later(Q, false)) return run_single<R, TB - Q, TB, false>(buf, tab, sc, tid, wsm);
+    dispatch_later_single<R, Q + 1>(v, buf, tab, sc, tid, wsm);
   }
 }
 
@@ -341,10 +365,25 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
           ptx::fence_proxy_async_global();
         }
         const uint32_t bytes = (it.variant < 16) ? (128u << (it.map / 2)) : kTileBytes;
-        ptx::mbar_arrive_expect_tx(full, bytes);
+        // the table entries the first and middle passes read, copied with the tile
+        constexpr int TBs = KT<R>::TB;
+        int slo = 0, shi = 0;
+        if (it.variant == kVFirstChunk || it.variant == q_variant_first(TBs)) {
+          slo = q_stage_lo(TBs, 0);
+          shi = q_stage_hi(TBs, 0);
+        } else if (it.variant >= 16) {
+          const int plo = TBs - ((it.variant - 16) / 2 + 1);
+          slo = q_stage_lo(TBs, plo);
+          shi = q_stage_hi(TBs, plo);
+        }
+        const uint32_t tw_bytes = shi > slo ? uint32_t(shi - slo) * KT<R>::ES : 0u;
+        ptx::mbar_arrive_expect_tx(full, bytes + tw_bytes);
         // samples and intermediates are read once: first out of L2
         ptx::tma_load_4d_hint(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], full, 0, it.c1, 0, it.c3,
                               ptx::policy_evict_first());
+        if (tw_bytes)
+          ptx::bulk_load(ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R>()) + uint32_t(slo) * KT<R>::ES,
+                         static_cast<const char*>(it.tw) + size_t(slo) * KT<R>::ES, tw_bytes, full);
         inflight |= 1u << b;
         load_par = (load_par & ~(1u << b)) | (uint32_t((j / kBufs) & 1) << b);
         // the item's tables into L2 while its tile is in flight (once per table
@@ -399,7 +438,7 @@ __global__ void __launch_bounds__(q_threads<R>(), 2) k_queue(const __grid_consta
   const uint32_t tid = threadIdx.x;
   constexpr uint32_t NT = KT<R>::NT;
   {
-    const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 64 + kMetaSlots * uint32_t(sizeof(QItem));
+    const uint32_t used = uint32_t(smem - smem_raw) + kQTwOff + kBufs * q_tw_bytes<R>();
     int bad = 0;
     if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
     else if (reinterpret_cast<uintptr_t>(&prm.maps[0]) & 63u) bad = kBadMap;
@@ -440,16 +479,17 @@ __global__ void __launch_bounds__(q_threads<R>(), 2) k_queue(const __grid_consta
     const C* tab = static_cast<const C*>(it.tw);
     const R sc = R(it.scale);
     char* buf = smem + b * kTileBytes;
+    const uint32_t wsm = ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R>());
     if (v == kVNop) {
       // nothing to do
     } else if (v == kVSmall) {
       run_small<R>(a, it, tid);
     } else if (v == kVFirstChunk) {
-      run_single<R, 0, TB, false>(buf, tab, sc, tid);
+      run_single<R, 0, TB, false>(buf, tab, sc, tid, wsm);
     } else if (v == q_variant_first(TB)) {
-      run_single<R, 0, TB, true>(buf, tab, sc, tid);
+      run_single<R, 0, TB, true>(buf, tab, sc, tid, wsm);
     } else if (v >= 16) {
-      dispatch_later_single<R>(v, buf, tab, sc, tid);
+      dispatch_later_single<R>(v, buf, tab, sc, tid, wsm);
     } else {
       dispatch_first_q<R>(v, buf, a, it, tid);   // several instances per tile
     }
@@ -484,9 +524,9 @@ int queue_grid_f64();
 template <class R>
 int queue_grid() {
   auto fn = k_queue<R>;
-  if (ensure_smem(reinterpret_cast<const void*>(fn), int(kQueueSmem)) != SDFT_OK) return 0;
+  if (ensure_smem(reinterpret_cast<const void*>(fn), int(q_smem<R>())) != SDFT_OK) return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, q_threads<R>(), kQueueSmem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, q_threads<R>(), q_smem<R>()) != cudaSuccess)
     return 0;
   return per_sm * sm_count();
 }
@@ -494,12 +534,12 @@ int queue_grid() {
 template <class R>
 sdft_status launch_queue(const QParams& prm, int grid, cudaStream_t st) {
   auto fn = k_queue<R>;
-  sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(kQueueSmem));
+  sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(q_smem<R>()));
   if (s != SDFT_OK) return s;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
   cfg.blockDim = dim3(q_threads<R>());
-  cfg.dynamicSmemBytes = kQueueSmem;
+  cfg.dynamicSmemBytes = q_smem<R>();
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs resident: dependency waits make progress
