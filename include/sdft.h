@@ -157,7 +157,10 @@ sdft_status sdft_synthesize_strided(sdft_plan plan, uint64_t batch, const void* 
  *     later-level tiles follow their instance's previous level, so the
  *     intermediate is read back from L2; the first call with a given batch size
  *     builds and caches the queue (allocates: make that call before capturing
- *     a CUDA graph). Single-level plans ignore the strategy. */
+ *     a CUDA graph). The cached queue's dependency counters are shared, so
+ *     with this strategy calls on one plan with the same batch size must not
+ *     overlap on the GPU (the default strategy has no such state). Single-level
+ *     plans ignore the strategy. */
 typedef enum { SDFT_STRATEGY_LEVELS = 1, SDFT_STRATEGY_QUEUE = 2 } sdft_strategy;
 sdft_status sdft_plan_set_strategy(sdft_plan plan, sdft_strategy strategy);
 
