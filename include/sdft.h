@@ -211,8 +211,10 @@ sdft_status sdft_batch_info(sdft_batch batch, uint64_t* total, uint64_t* offsets
 /*
  * sdft_batch_execute - run every instance of the batch: one persistent kernel
  * over the work queue. Buffers as described at sdft_batch_create, 16-byte
- * aligned, not overlapping. Asynchronous, allocates nothing, and may be
- * captured into a CUDA graph.
+ * aligned, identical (in place) or disjoint. Asynchronous, allocates nothing,
+ * and may be captured into a CUDA graph. A launch uses the batch's dependency
+ * counters: launches of one batch must not overlap on the GPU (one stream, or
+ * one batch per stream).
  */
 sdft_status sdft_batch_execute(sdft_batch batch, const void* d_samples, void* d_coeffs,
                                void* stream);
