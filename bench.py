@@ -280,6 +280,7 @@ def run_ours(args):
     if not args.no_extra and ws == 1:      # the other workloads run at N = 1 only
         del x64, y64, h_in, h_out, d_in, d_out
         torch.cuda.empty_cache()
+        extra["single"] = run_single(args)
         extra["uneven"] = run_uneven(args)
         extra["large_k"] = run_large(args)
         extra["serving"] = run_serving(args)
@@ -343,6 +344,35 @@ def time_graph(fn, steps, warmup, flush, stream):
             fn(s)
     torch.cuda.synchronize()
     return time_device_steps(lambda: g.replay(), steps, warmup, flush, stream)
+
+
+def run_single(args):
+    """Single-instance leg: N = 2^10, k = 2^5, complex128 (latency): one
+    execute per step as a CUDA-graph replay, and the relative L2 against the
+    oracle's dense solve."""
+    import torch
+    import oracle as O
+    from paper_2211_15299_gb300 import Plan
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    inst = W.workload_single()
+    plan = Plan(inst.M, inst.J, "c128")
+    Jc = O.canonical_support_by_key(inst.J, inst.pivots)
+    I = O.sample_set(inst.M, inst.pivots)
+    pos = {int(j): i for i, j in enumerate(inst.J)}
+    c = np.asarray([inst.coeffs[pos[int(j)]] for j in Jc])
+    f = O.synthesize(inst.M, Jc, c, I)
+    x = torch.from_numpy(f).to(dev)
+    y = torch.empty_like(x)
+
+    def step(s=None):
+        plan.execute_strided(x, y, stream=(s or stream).cuda_stream)
+
+    t = time_graph(step, max(10, args.steps), args.warmup, flush, stream)
+    got = y.cpu().numpy()
+    return {"workload": f"N=2^{inst.M} k=2^{inst.s} complex128, one instance", "us_per_call": 1e6 * statistics.median(t),
+            "rel_l2_vs_oracle": float(np.linalg.norm(got - c) / np.linalg.norm(c)), "launches_per_call": 1}
 
 
 def run_large(args):
