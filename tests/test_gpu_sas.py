@@ -105,3 +105,12 @@ def test_random_subset_at_the_theorems_pivot_count(prec):
     assert p.mu_star < (4 + 3 * np.log(2)) * log2k
     assert rel_l2(got, ref) < _tol(prec, p.max_cond), p.max_cond
     assert rel_l2(got, C) < _tol(prec, p.max_cond)
+
+
+@pytest.mark.parametrize("sizes", [(32, 32), (10, 12, 14)])
+def test_generalized_progression(sizes):
+    # Lemma "gap-complexity": a proper GAP has few pivots; SAS on the GPU
+    rng = W.rng_for(0, 8100 + sum(sizes))
+    J = [int(j) for j in W.generalized_arithmetic_progression(20, sizes, rng)]
+    p, got, C, ref = _case(20, J, "c64", 0, 2, np.random.default_rng(9))
+    assert rel_l2(got, ref) < _tol("c64", p.max_cond) and rel_l2(got, C) < _tol("c64", p.max_cond)

@@ -228,3 +228,26 @@ def test_union_of_homogeneous_alias_bound(base):
         r, mu, idx, got = _run(M, J, a, c)
         conds = [np.linalg.cond(O.sas.__dict__["_z_powers"](M, m, len(m))) for m in O.sas_nodes(J, r).values()]
         assert rel_l2(got, c) < 1e-14 * max(conds) + 1e-12
+
+
+@pytest.mark.parametrize("sizes", [(8, 8), (5, 6, 7), (16, 3)])
+def test_generalized_progressions_have_few_pivots(sizes):
+    # Lemma "gap-complexity", eq. "gap-pivot-bound": a proper GAP of dimension d
+    # with n split levels satisfies 2^n <= n^d 2^d |J|; SAS recovers its coefficients
+    d = len(sizes)
+    for seed in range(4):
+        rng = W.rng_for(0, 7000 + 17 * seed + sum(sizes))
+        M = 20
+        J = [int(j) for j in W.generalized_arithmetic_progression(M, sizes, rng)]
+        n = len(O.split_levels(J, M))
+        assert 2 ** n <= n ** d * 2 ** d * len(J), (n, len(J))
+    c = W.complex_gaussian(len(J), rng)
+    levels = O.split_levels(J, M)
+    R = min(len(levels), int(np.ceil(np.log2(len(J)))) + 1)
+    r = O.sas_pivots(J, M, R)
+    mu = O.sas_mu(J, r)
+    idx = O.sas_sample_sets(M, r, max(mu.values()))
+    F = O.sas_samples_direct(M, J, c, idx)
+    got = O.sas_transform(M, J, r, F)
+    conds = [np.linalg.cond(O.sas.__dict__["_z_powers"](M, m, len(m))) for m in O.sas_nodes(J, r).values()]
+    assert rel_l2(got, c) < 1e-14 * max(conds) + 1e-12
