@@ -206,7 +206,8 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "k_level<float,0,12,true>" if n_levels == 1 else "multi-level",
-                "alg_bytes_per_launch": alg_bytes}
+                "alg_bytes_per_launch": alg_bytes,
+                "frac_of_nominal_7900": round(achieved / 7900.0, 4)}
 
     if args.only_fp32:
         if rank == 0:
