@@ -44,11 +44,16 @@ constexpr uint32_t kTileBytes = 32768;
 constexpr int kBadSmem = 0x101;   // less dynamic shared memory than the layout needs
 constexpr int kBadMap = 0x102;    // tensor map parameter not 64-byte aligned
 constexpr int kBadTable = 0x103;  // twiddle table not 16-byte aligned
-constexpr int kBufs = 3;                                             // tiles in flight per CTA
+constexpr int kBufs = 3;                                             // tile buffers per work-queue CTA
+// Tile buffers per level-kernel CTA. Two keep the level kernel at the speed of a
+// copy-only variant of itself (TMA in and out, no passes) on the 2^12-point
+// batches, and leave more of the SM's combined L1/shared storage to the L1 cache
+// that serves the table reads of later levels.
+constexpr int kLevelBufs = 2;
 // Shared-memory copy of the middle pass's table region (entries [16, 256),
 // absolute-indexed) for the level kernel.
 constexpr uint32_t kMidTwBytes = 256 * 16;
-constexpr uint32_t kLevelSmem = kBufs * kTileBytes + 64 + kMidTwBytes + 1024;   // tiles, barriers, table, slack
+constexpr uint32_t kLevelSmem = kLevelBufs * kTileBytes + 64 + kMidTwBytes + 1024;   // tiles, barriers, table, slack
 
 // ---- swizzled tile addressing -------------------------------------------------
 // byte(T) = (T >> CB) * 128 + ((col_chunk(T) ^ (row(T) & 7)) << 4) + sub(T) * ES.
@@ -488,17 +493,19 @@ struct LevelArgs {
   typename KT<R>::C tw0[16];  // tw0[i] = level-0 table entry i + 1 (stage bits 0..3), i < 15
 };
 
+// Pointer arithmetic on the shared-memory symbol itself (no round trip through
+// an integer), so that accesses through the result stay shared-space loads and
+// stores instead of generic ones.
 __device__ __forceinline__ char* align1024(char* p) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
   const uint32_t s = ptx::smem_addr(p);
-  return reinterpret_cast<char*>(a + ((1024u - (s & 1023u)) & 1023u));
+  return p + ((1024u - (s & 1023u)) & 1023u);
 }
 
-// Pipeline per CTA (kBufs = 3 tile buffers): tile j waits on full[j % 3], runs
-// its passes in place, and leaves through a TMA store issued by thread 0. After
-// tile j's first pass, the buffer of tile j-1 is refilled with tile j+2 once its
-// store has finished reading shared memory, so up to two loads stay in flight
-// behind the tile being computed.
+// Pipeline per CTA (kLevelBufs = 2 tile buffers): tile j waits on full[j % 2],
+// runs its passes in place, and leaves through a TMA store issued by thread 0.
+// After tile j's first pass, the buffer of tile j-1 is refilled with tile j+1
+// once its store has finished reading shared memory, so the next tile's load is
+// in flight behind the tile being computed.
 // INV: the adjoint (synthesis) passes instead of the forward ones.
 template <class R, int PLO, int PHI, bool LAST, bool INV = false>
 __global__ void __launch_bounds__(KT<R>::NT, 2)
@@ -508,13 +515,13 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   constexpr int NREG = reg_twiddles(KT<R>::TB, PLO, PHI);
   extern __shared__ char smem_raw[];
   char* smem = align1024(smem_raw);
-  const uint32_t bar0 = ptx::smem_addr(smem + kBufs * kTileBytes);
+  const uint32_t bar0 = ptx::smem_addr(smem + kLevelBufs * kTileBytes);
   const uint32_t tid = threadIdx.x;
   // Self-check of the launch before any shared-memory or TMA access: enough
   // dynamic shared memory for the aligned layout, tensor maps 64-byte aligned,
   // twiddle tables 16-byte aligned. A failed check records a status and exits.
   {
-    const uint32_t used = uint32_t(smem - smem_raw) + kBufs * kTileBytes + 64 + kMidTwBytes;
+    const uint32_t used = uint32_t(smem - smem_raw) + kLevelBufs * kTileBytes + 64 + kMidTwBytes;
     int bad = 0;
     if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
     else if ((reinterpret_cast<uintptr_t>(&src) | reinterpret_cast<uintptr_t>(&dst)) & 63u) bad = kBadMap;
@@ -549,7 +556,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   uint32_t load_buf = 0;               // thread 0: its buffer (tiles load in order, buffers cycle)
   auto issue_load = [&]() {
     const uint32_t b = load_buf;
-    load_buf = (load_buf + 1 == uint32_t(kBufs)) ? 0u : load_buf + 1;
+    load_buf = (load_buf + 1 == uint32_t(kLevelBufs)) ? 0u : load_buf + 1;
     const uint32_t bar = bar0 + 8 * b;
     int c1, c3;
     coords(load_cur, c1, c3);
@@ -559,11 +566,11 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   };
 
   if (tid == 0) {
-    for (int b = 0; b < kBufs; ++b) ptx::mbar_init(bar0 + 8 * b, 1);
+    for (int b = 0; b < kLevelBufs; ++b) ptx::mbar_init(bar0 + 8 * b, 1);
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&src);
     ptx::prefetch_tensormap(&dst);
-    for (uint64_t j = 0; j < n && j < uint64_t(kBufs); ++j) issue_load();
+    for (uint64_t j = 0; j < n && j < uint64_t(kLevelBufs); ++j) issue_load();
   }
   __syncthreads();
   const R sc = R(args.scale);
@@ -572,7 +579,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   constexpr int MLO = mid_pass_lo(KT<R>::TB, PLO, PHI), MHI = mid_pass_hi(KT<R>::TB, PLO, PHI);
   // a middle pass whose region fits the shared copy reads it from there
   constexpr bool MIDSM = MLO < MHI && (1u << MHI) * sizeof(C) <= kMidTwBytes;
-  C* midtw = reinterpret_cast<C*>(smem + kBufs * kTileBytes + 64);
+  C* midtw = reinterpret_cast<C*>(smem + kLevelBufs * kTileBytes + 64);
   const uint32_t midtw_addr = ptx::smem_addr(midtw);
   const C* twt = tw;
   uint64_t cur_tab = ~0ull;
@@ -581,7 +588,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   uint32_t b = 0;                      // its buffer
   uint32_t phases = 0;                 // bit q: parity of buffer q's next completion
   uint64_t j = 0;
-  for (; j < n; ++j, advance(cur), b = (b + 1 == uint32_t(kBufs)) ? 0u : b + 1) {
+  for (; j < n; ++j, advance(cur), b = (b + 1 == uint32_t(kLevelBufs)) ? 0u : b + 1) {
     char* buf = smem + b * kTileBytes;
     const uint64_t tab = args.tw_stride ? cur.a : 0;
     if (tab != cur_tab) {  // uniform across the CTA; the previous tile's passes are done
@@ -599,10 +606,10 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
       break;
     }
     // After the first pass: once the store of tile j-1 (the latest one issued)
-    // has left its buffer, load tile j+2 into it, two thirds of a tile earlier
-    // than at the end of this tile.
+    // has left its buffer, load tile j + kLevelBufs - 1 into it, two thirds of a
+    // tile earlier than at the end of this tile.
     auto refill = [&]() {
-      if (tid == 0 && j >= 1 && j + 2 < n) {
+      if (tid == 0 && j >= 1 && j + kLevelBufs - 1 < n) {
         ptx::bulk_wait_read<0>();
         issue_load();
       }
@@ -621,11 +628,12 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   }
   if (tid == 0) {
     if (aborted) {
-      // Let loads already issued (tiles j .. max(j+1, kBufs-1)) land before the
-      // CTA's shared memory is released.
-      const uint64_t last = (j + 1 > uint64_t(kBufs - 1)) ? j + 1 : uint64_t(kBufs - 1);
+      // Let loads already issued (tiles j .. max(j + kLevelBufs - 2, kLevelBufs - 1))
+      // land before the CTA's shared memory is released.
+      const uint64_t last = (j + kLevelBufs - 2 > uint64_t(kLevelBufs - 1)) ? j + kLevelBufs - 2
+                                                                             : uint64_t(kLevelBufs - 1);
       for (uint64_t q = j; q <= last && q < n; ++q)
-        ptx::mbar_wait_bounded(bar0 + 8 * uint32_t(q % kBufs), uint32_t((q / kBufs) & 1), args.timeout_ns);
+        ptx::mbar_wait_bounded(bar0 + 8 * uint32_t(q % kLevelBufs), uint32_t((q / kLevelBufs) & 1), args.timeout_ns);
       atomicExch(args.status, int(SDFT_ERR_TIMEOUT));
     }
     ptx::bulk_wait<0>();

@@ -21,6 +21,8 @@ def main() -> int:
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--reps", type=int, default=4)
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--strategy", default="", choices=["", "levels", "queue"],
+                    help="multi-level plans: per-level launches or one work-queue launch")
     ap.add_argument("--uneven", type=int, default=0,
                     help="run the uneven workload's recipe with this many instances instead")
     ap.add_argument("--sas", default="", choices=["", "ap", "subset"],
@@ -38,6 +40,8 @@ def main() -> int:
 
     inst, _ = W.workload_shared(M=args.log2n, s=args.log2k, batch=1, coeffs=False)
     plan = Plan(args.log2n, inst.J, args.prec)
+    if args.strategy:
+        plan.set_strategy(args.strategy)
     dt = torch.complex64 if args.prec == "c64" else torch.complex128
     g = torch.Generator(device="cuda")
     g.manual_seed(1)
@@ -48,7 +52,7 @@ def main() -> int:
     torch.cuda.synchronize()
     st = plan.device_status()
     print(f"profile_case log2n={args.log2n} log2k={args.log2k} batch={args.batch} {args.prec} "
-          f"reps={args.reps} device_status={st:#x}", flush=True)
+          f"strategy={args.strategy or 'default'} reps={args.reps} device_status={st:#x}", flush=True)
     return 0 if st == 0 else 3
 
 
