@@ -71,75 +71,103 @@ sdft_status dispatch_small(int s, uint64_t batch, const void* in, void* out, con
   }
 }
 
+// Tensor maps and kernel arguments of level 0 (stage bits [0, min(s, TB)) on
+// contiguous tiles of 2^TB elements) over the packed buffers (src, dst).
+template <class R>
+sdft_status level0_setup(const Plan& p, uint64_t batch, const void* src, void* dst, CUtensorMap& ms,
+                         CUtensorMap& md, LevelArgs<R>& a) {
+  using C = typename KT<R>::C;
+  constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
+  const Level& L = p.levels[0];
+  const uint64_t rows_per_tile = 1ull << (TB - CB);
+  const uint64_t rows = (batch * p.k) >> CB;
+  const uint64_t n_tiles = (rows + rows_per_tile - 1) / rows_per_tile;
+  if (rows > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
+  const uint64_t dims[4] = {32, rows, 1, 1};
+  const uint64_t strides[3] = {128, rows * 128, rows * 128};
+  const uint32_t box[4] = {32, uint32_t(rows_per_tile), 1, 1};
+  sdft_status s = encode_map(&ms, src, dims, strides, box);
+  if (s == SDFT_OK) s = encode_map(&md, dst, dims, strides, box);
+  if (s != SDFT_OK) return s;
+  a = LevelArgs<R>{};
+  for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
+  a.n_tiles = n_tiles;
+  a.nB = n_tiles;
+  a.a_step1 = 0;
+  a.b_step1 = int32_t(rows_per_tile);
+  a.b_step3 = 0;
+  a.tw_first = 0;
+  a.tw = static_cast<const C*>(p.d_tw) + L.tw_off;
+  a.tw_len = L.tw_len;
+  a.tw_stride = 0;
+  a.scale = std::ldexp(1.0, int(p.M) - int(p.s));
+  a.inv_n = std::ldexp(1.0, -int(p.M));
+  a.status = p.d_status;
+  a.timeout_ns = wait_timeout_ns();
+  return SDFT_OK;
+}
+
+// Tensor maps and kernel arguments of later level j (stage bits [lo, hi) on
+// group blocks: 2^lg column groups x 2^Q rows spaced 2^lo elements apart).
+template <class R>
+sdft_status later_setup(const Plan& p, uint64_t batch, size_t j, const void* src, void* dst, CUtensorMap& ms,
+                        CUtensorMap& md, LevelArgs<R>& a) {
+  using C = typename KT<R>::C;
+  constexpr int CB = KT<R>::CB, ES = KT<R>::ES;
+  const Level& L = p.levels[j];
+  const uint32_t Q = L.hi - L.lo;
+  const uint64_t Z = batch << (p.s - L.hi);
+  if (Z > 0x7fffffffull || (1ull << (L.lo - CB)) > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
+  const uint64_t dims[4] = {32, 1ull << (L.lo - CB), 1ull << Q, Z};
+  const uint64_t strides[3] = {128, (1ull << L.lo) * ES, (1ull << L.hi) * ES};
+  const uint32_t box[4] = {32, 1u << L.lg, 1u << Q, 1};
+  sdft_status s = encode_map(&ms, src, dims, strides, box);
+  if (s == SDFT_OK) s = encode_map(&md, dst, dims, strides, box);
+  if (s != SDFT_OK) return s;
+  a = LevelArgs<R>{};
+  for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
+  a.n_tiles = L.n_gb * Z;
+  a.nB = Z;
+  a.a_step1 = int32_t(1u << L.lg);
+  a.b_step1 = 0;
+  a.b_step3 = 1;
+  a.tw_first = 1u << L.plo;
+  a.tw = static_cast<const C*>(p.d_tw) + L.tw_off;
+  a.tw_len = L.tw_len;
+  a.tw_stride = L.tw_len;
+  a.scale = std::ldexp(1.0, int(p.M) - int(p.s));
+  a.inv_n = std::ldexp(1.0, -int(p.M));
+  a.status = p.d_status;
+  a.timeout_ns = wait_timeout_ns();
+  return SDFT_OK;
+}
+
+inline int level_grid(uint64_t n_tiles) {
+  const uint64_t max_grid = 2ull * uint64_t(sm_count());
+  return int(n_tiles < max_grid ? n_tiles : max_grid);
+}
+
 template <class R>
 sdft_status launch_plan(const Plan& p, uint64_t batch, const void* in, void* out, cudaStream_t st) {
-  using C = typename KT<R>::C;
-  constexpr int TB = KT<R>::TB, CB = KT<R>::CB, ES = KT<R>::ES;
   const double scale = std::ldexp(1.0, int(p.M) - int(p.s));
   if (p.levels.empty()) return dispatch_small<R>(int(p.s), batch, in, out, p.d_tw, scale, st);
-
-  const int max_grid = 2 * sm_count();
-  const uint64_t rows_per_tile = 1ull << (TB - CB);
   // Level 0 on contiguous tiles.
   {
-    const Level& L = p.levels[0];
-    const uint64_t elems = batch * p.k;
-    const uint64_t rows = elems >> CB;
-    const uint64_t n_tiles = (rows + rows_per_tile - 1) / rows_per_tile;
-    if (rows > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
     CUtensorMap ms, md;
-    const uint64_t dims[4] = {32, rows, 1, 1};
-    const uint64_t strides[3] = {128, rows * 128, rows * 128};
-    const uint32_t box[4] = {32, uint32_t(rows_per_tile), 1, 1};
-    sdft_status s = encode_map(&ms, in, dims, strides, box);
-    if (s == SDFT_OK) s = encode_map(&md, out, dims, strides, box);
+    LevelArgs<R> a;
+    sdft_status s = level0_setup<R>(p, batch, in, out, ms, md, a);
     if (s != SDFT_OK) return s;
-    LevelArgs<R> a{};
-    for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
-    a.n_tiles = n_tiles;
-    a.nB = n_tiles;
-    a.a_step1 = 0;
-    a.b_step1 = int32_t(rows_per_tile);
-    a.b_step3 = 0;
-    a.tw_first = 0;
-    a.tw = static_cast<const C*>(p.d_tw) + L.tw_off;
-    a.tw_len = L.tw_len;
-    a.tw_stride = 0;
-    a.scale = scale;
-    a.status = p.d_status;
-    a.timeout_ns = wait_timeout_ns();
-    const int grid = int(n_tiles < uint64_t(max_grid) ? n_tiles : uint64_t(max_grid));
-    s = dispatch_first<R>(int(L.hi), L.last, grid, ms, md, a, st);
+    s = dispatch_first<R>(int(p.levels[0].hi), p.levels[0].last, level_grid(a.n_tiles), ms, md, a, st);
     if (s != SDFT_OK) return s;
   }
   // Later levels in place on the output.
   for (size_t j = 1; j < p.levels.size(); ++j) {
     const Level& L = p.levels[j];
-    const uint32_t Q = L.hi - L.lo;
-    const uint64_t Z = batch << (p.s - L.hi);
-    if (Z > 0x7fffffffull || (1ull << (L.lo - CB)) > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
-    CUtensorMap m;
-    const uint64_t dims[4] = {32, 1ull << (L.lo - CB), 1ull << Q, Z};
-    const uint64_t strides[3] = {128, (1ull << L.lo) * ES, (1ull << L.hi) * ES};
-    const uint32_t box[4] = {32, 1u << L.lg, 1u << Q, 1};
-    sdft_status s = encode_map(&m, out, dims, strides, box);
+    CUtensorMap m, m2;
+    LevelArgs<R> a;
+    sdft_status s = later_setup<R>(p, batch, j, out, out, m, m2, a);
     if (s != SDFT_OK) return s;
-    LevelArgs<R> a{};
-    for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
-    a.n_tiles = L.n_gb * Z;
-    a.nB = Z;
-    a.a_step1 = int32_t(1u << L.lg);
-    a.b_step1 = 0;
-    a.b_step3 = 1;
-    a.tw_first = 1u << L.plo;
-    a.tw = static_cast<const C*>(p.d_tw) + L.tw_off;
-    a.tw_len = L.tw_len;
-    a.tw_stride = L.tw_len;
-    a.scale = scale;
-    a.status = p.d_status;
-    a.timeout_ns = wait_timeout_ns();
-    const int grid = int(a.n_tiles < uint64_t(max_grid) ? a.n_tiles : uint64_t(max_grid));
-    s = dispatch_later<R>(int(Q), L.last, grid, m, m, a, st);
+    s = dispatch_later<R>(int(L.hi - L.lo), L.last, level_grid(a.n_tiles), m, m, a, st);
     if (s != SDFT_OK) return s;
   }
   return SDFT_OK;
@@ -169,75 +197,26 @@ sdft_status dispatch_small_inv(int s, uint64_t batch, const void* in, void* out,
 // others work in place on `out`.
 template <class R>
 sdft_status launch_plan_inv(const Plan& p, uint64_t batch, const void* in, void* out, cudaStream_t st) {
-  using C = typename KT<R>::C;
-  constexpr int TB = KT<R>::TB, CB = KT<R>::CB, ES = KT<R>::ES;
   const double scale = std::ldexp(1.0, int(p.M) - int(p.s));
   const double inv_n = std::ldexp(1.0, -int(p.M));
   if (p.levels.empty()) return dispatch_small_inv<R>(int(p.s), batch, in, out, p.d_tw, 1.0 / scale, inv_n, st);
-
-  const int max_grid = 2 * sm_count();
+  // Later levels first (last one first), the first reading `in`, then level 0.
   const void* src_base = in;
   for (size_t j = p.levels.size() - 1; j >= 1; --j) {
     const Level& L = p.levels[j];
-    const uint32_t Q = L.hi - L.lo;
-    const uint64_t Z = batch << (p.s - L.hi);
-    if (Z > 0x7fffffffull || (1ull << (L.lo - CB)) > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
     CUtensorMap ms, md;
-    const uint64_t dims[4] = {32, 1ull << (L.lo - CB), 1ull << Q, Z};
-    const uint64_t strides[3] = {128, (1ull << L.lo) * ES, (1ull << L.hi) * ES};
-    const uint32_t box[4] = {32, 1u << L.lg, 1u << Q, 1};
-    sdft_status s = encode_map(&ms, src_base, dims, strides, box);
-    if (s == SDFT_OK) s = encode_map(&md, out, dims, strides, box);
+    LevelArgs<R> a;
+    sdft_status s = later_setup<R>(p, batch, j, src_base, out, ms, md, a);
     if (s != SDFT_OK) return s;
-    LevelArgs<R> a{};
-    for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
-    a.n_tiles = L.n_gb * Z;
-    a.nB = Z;
-    a.a_step1 = int32_t(1u << L.lg);
-    a.b_step1 = 0;
-    a.b_step3 = 1;
-    a.tw_first = 1u << L.plo;
-    a.tw = static_cast<const C*>(p.d_tw) + L.tw_off;
-    a.tw_len = L.tw_len;
-    a.tw_stride = L.tw_len;
-    a.scale = scale;
-    a.inv_n = inv_n;
-    a.status = p.d_status;
-    a.timeout_ns = wait_timeout_ns();
-    const int grid = int(a.n_tiles < uint64_t(max_grid) ? a.n_tiles : uint64_t(max_grid));
-    s = dispatch_later<R, true>(int(Q), L.last, grid, ms, md, a, st);
+    s = dispatch_later<R, true>(int(L.hi - L.lo), L.last, level_grid(a.n_tiles), ms, md, a, st);
     if (s != SDFT_OK) return s;
     src_base = out;
   }
-  const Level& L = p.levels[0];
-  const uint64_t rows_per_tile = 1ull << (TB - CB);
-  const uint64_t rows = (batch * p.k) >> CB;
-  const uint64_t n_tiles = (rows + rows_per_tile - 1) / rows_per_tile;
-  if (rows > 0x7fffffffull) return SDFT_ERR_UNSUPPORTED;
   CUtensorMap ms, md;
-  const uint64_t dims[4] = {32, rows, 1, 1};
-  const uint64_t strides[3] = {128, rows * 128, rows * 128};
-  const uint32_t box[4] = {32, uint32_t(rows_per_tile), 1, 1};
-  sdft_status s = encode_map(&ms, src_base, dims, strides, box);
-  if (s == SDFT_OK) s = encode_map(&md, out, dims, strides, box);
+  LevelArgs<R> a;
+  sdft_status s = level0_setup<R>(p, batch, src_base, out, ms, md, a);
   if (s != SDFT_OK) return s;
-  LevelArgs<R> a{};
-  for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
-  a.n_tiles = n_tiles;
-  a.nB = n_tiles;
-  a.a_step1 = 0;
-  a.b_step1 = int32_t(rows_per_tile);
-  a.b_step3 = 0;
-  a.tw_first = 0;
-  a.tw = static_cast<const C*>(p.d_tw) + L.tw_off;
-  a.tw_len = L.tw_len;
-  a.tw_stride = 0;
-  a.scale = scale;
-  a.inv_n = inv_n;
-  a.status = p.d_status;
-  a.timeout_ns = wait_timeout_ns();
-  const int grid = int(n_tiles < uint64_t(max_grid) ? n_tiles : uint64_t(max_grid));
-  return dispatch_first<R, true>(int(L.hi), L.last, grid, ms, md, a, st);
+  return dispatch_first<R, true>(int(p.levels[0].hi), p.levels[0].last, level_grid(a.n_tiles), ms, md, a, st);
 }
 
 }  // namespace sdft
