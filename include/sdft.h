@@ -136,6 +136,29 @@ sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_s
                                  void* d_coeffs, void* stream);
 
 /*
+ * sdft_execute_strided_host - sdft_execute_strided on samples and coefficients
+ * in host memory: h_samples (batch x k values, sample order) is copied to the
+ * device buffer d_samples, transformed into d_coeffs and copied back into
+ * h_coeffs, in chunks of `chunk` instances (0: about 16 MiB; rounded up so
+ * that every chunk is a multiple of 16 bytes) so that a chunk's copy-in, the
+ * previous chunk's transform and an earlier chunk's copy-out overlap. Host
+ * buffers should be page-locked (cudaHostAlloc / cudaHostRegister) for the
+ * copies to be asynchronous; they may be identical or must be disjoint. Device
+ * buffers as for sdft_execute_strided (caller-owned, 16-byte aligned, identical
+ * or disjoint), each of batch x k values. The copies run on two streams of the
+ * plan (created with three events on the first call; no device memory is
+ * allocated) that start after the work already queued on `stream`; `stream`
+ * itself runs the transforms and, when the call returns, has been made to wait
+ * for the last copy-out, so synchronising `stream` (or an event recorded on it
+ * afterwards) covers the whole call. Calls on one plan are serialised while
+ * they enqueue; graph capture of `stream` captures the fork and join. Errors:
+ * SDFT_ERR_ARG, SDFT_ERR_NO_DEVICE, SDFT_ERR_CUDA, and those of
+ * sdft_execute_strided.
+ */
+sdft_status sdft_execute_strided_host(sdft_plan plan, uint64_t batch, const void* h_samples, void* h_coeffs,
+                                      void* d_samples, void* d_coeffs, uint64_t chunk, void* stream);
+
+/*
  * sdft_synthesize / sdft_synthesize_strided - the inverse map: samples
  * f_I = F^{-1}(I_r, J) c = (1/N) F(J, I_r)^H c from coefficients c (Section II,
  * eq. "submatrix-method"; F(J, I_r)^H F(J, I_r) = k Id, so this inverts

@@ -104,6 +104,35 @@ class Plan:
         N.sdft_execute_strided(self.handle, batch, samples, coeffs, _current_stream(stream))
         return coeffs
 
+    def execute_host(self, h_samples, h_coeffs=None, d_samples=None, d_coeffs=None, chunk: int = 0,
+                     stream=None, batch: Optional[int] = None):
+        """execute_strided on host tensors (pinned for overlap): copy-in, transform
+        and copy-out in overlapped chunks of `chunk` instances (0: about 16 MiB).
+        Device staging buffers are allocated here when not given. The result is in
+        `h_coeffs` once `stream` (the current stream by default) reaches this point."""
+        torch = _torch()
+        if batch is None:
+            batch = h_samples.numel() // self.k
+        for t, what in ((h_samples, "h_samples"), (h_coeffs, "h_coeffs")):
+            if t is None:
+                continue
+            if not isinstance(t, torch.Tensor) or t.is_cuda:
+                raise ValueError(f"{what} must be a host tensor")
+            if t.dtype != self.dtype or not t.is_contiguous() or t.numel() != batch * self.k:
+                raise ValueError(f"{what} must be a contiguous {self.dtype} tensor of {batch * self.k} values")
+        if h_coeffs is None:
+            h_coeffs = torch.empty_like(h_samples, pin_memory=True)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if d_samples is None:
+            d_samples = torch.empty(batch * self.k, dtype=self.dtype, device=dev)
+        if d_coeffs is None:
+            d_coeffs = torch.empty(batch * self.k, dtype=self.dtype, device=dev)
+        _check_tensor(d_samples, self.dtype, batch * self.k, "d_samples")
+        _check_tensor(d_coeffs, self.dtype, batch * self.k, "d_coeffs")
+        N.sdft_execute_strided_host(self.handle, batch, h_samples, h_coeffs, d_samples, d_coeffs, chunk,
+                                    _current_stream(stream))
+        return h_coeffs
+
     def synthesize(self, coeffs, samples=None, stream=None, batch: Optional[int] = None):
         """Samples from coefficients (the inverse of execute_strided)."""
         if batch is None:

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -267,6 +268,73 @@ sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_s
   return sdft::run_strided(plan, batch, d_samples, d_coeffs, static_cast<cudaStream_t>(stream));
 }
 
+sdft_status sdft_execute_strided_host(sdft_plan plan, uint64_t batch, const void* h_samples, void* h_coeffs,
+                                      void* d_samples, void* d_coeffs, uint64_t chunk, void* stream) {
+  if (!plan || !h_samples || !h_coeffs) return SDFT_ERR_ARG;
+  const sdft::Plan& p = plan->p;
+  if (p.device < 0 || !p.d_status) return SDFT_ERR_NO_DEVICE;
+  if (batch == 0) return SDFT_OK;
+  const uint64_t inst_bytes = p.k * uint64_t(sdft::elem_bytes(p.prec));
+  if (batch > ~0ull / inst_bytes) return SDFT_ERR_ARG;
+  const uint64_t total = batch * inst_bytes;
+  {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(h_samples), b = reinterpret_cast<uintptr_t>(h_coeffs);
+    if (a != b && a < b + total && b < a + total) return SDFT_ERR_ARG;   // host buffers: identical or disjoint
+  }
+  // chunks of about 16 MiB, each a multiple of 16 bytes so that every chunk's
+  // device offset keeps the 16-byte alignment of the buffers
+  const uint64_t unit = inst_bytes >= 16 ? 1 : 16 / inst_bytes;
+  if (chunk == 0) chunk = std::max<uint64_t>(1, (16ull << 20) / inst_bytes);
+  chunk = (chunk + unit - 1) / unit * unit;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(plan->host_mu);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    if (!plan->host_st[i]) {
+      cudaStream_t st = nullptr;
+      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      plan->host_st[i] = st;
+    }
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    if (!plan->host_ev[i]) {
+      cudaEvent_t ev = nullptr;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      plan->host_ev[i] = ev;
+    }
+  if (e != cudaSuccess) return sdft::cuda_fail(e);
+  cudaStream_t in_st = static_cast<cudaStream_t>(plan->host_st[0]);
+  cudaStream_t out_st = static_cast<cudaStream_t>(plan->host_st[1]);
+  cudaEvent_t ev_in = static_cast<cudaEvent_t>(plan->host_ev[0]);    // a chunk's samples are on the device
+  cudaEvent_t ev_done = static_cast<cudaEvent_t>(plan->host_ev[1]);  // a chunk's coefficients are computed
+  cudaEvent_t ev_mark = static_cast<cudaEvent_t>(plan->host_ev[2]);  // start and end of the call
+  // the copies start after the work already on the caller's stream
+  e = cudaEventRecord(ev_mark, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(in_st, ev_mark, 0);
+  if (e != cudaSuccess) return sdft::cuda_fail(e);
+  const char* hi = static_cast<const char*>(h_samples);
+  char* ho = static_cast<char*>(h_coeffs);
+  char* di = static_cast<char*>(d_samples);
+  char* dout = static_cast<char*>(d_coeffs);
+  for (uint64_t b0 = 0; b0 < batch; b0 += chunk) {
+    const uint64_t nb = std::min(chunk, batch - b0);
+    const uint64_t off = b0 * inst_bytes, bytes = nb * inst_bytes;
+    e = cudaMemcpyAsync(di + off, hi + off, bytes, cudaMemcpyHostToDevice, in_st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in, in_st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in, 0);
+    if (e != cudaSuccess) return sdft::cuda_fail(e);
+    const sdft_status s = sdft::run_strided(plan, nb, di + off, dout + off, cs);
+    if (s != SDFT_OK) return s;
+    e = cudaEventRecord(ev_done, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(out_st, ev_done, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ho + off, dout + off, bytes, cudaMemcpyDeviceToHost, out_st);
+    if (e != cudaSuccess) return sdft::cuda_fail(e);
+  }
+  // the caller's stream continues once the last copy-out is done
+  e = cudaEventRecord(ev_mark, out_st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_mark, 0);
+  return e == cudaSuccess ? SDFT_OK : sdft::cuda_fail(e);
+}
+
 sdft_status sdft_synthesize(sdft_plan plan, const void* d_coeffs, void* d_samples, void* stream) {
   if (!plan) return SDFT_ERR_ARG;
   return sdft::run_strided_inverse(plan, 1, d_coeffs, d_samples, static_cast<cudaStream_t>(stream));
@@ -339,6 +407,10 @@ sdft_status sdft_plan_device_status(sdft_plan plan, int clear) {
 sdft_status sdft_plan_destroy(sdft_plan plan) {
   if (!plan) return SDFT_ERR_ARG;
   sdft::free_strided_queues(plan->p);
+  for (void* st : plan->host_st)
+    if (st) cudaStreamDestroy(static_cast<cudaStream_t>(st));
+  for (void* ev : plan->host_ev)
+    if (ev) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
   if (plan->p.d_tw) cudaFree(plan->p.d_tw);
   if (plan->p.d_status) cudaFree(plan->p.d_status);
   delete plan;

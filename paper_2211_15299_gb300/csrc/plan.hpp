@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "sdft.h"
@@ -85,4 +86,10 @@ template <class T> void fill_device_tables(const Plan& p, T* out);
 // The opaque handle of the C ABI.
 struct sdft_plan_s {
   sdft::Plan p;
+  // sdft_execute_strided_host: copy-in / copy-out streams and three events,
+  // created on first use (cudaStream_t / cudaEvent_t), and the lock that keeps
+  // one call's chain of copies, launches and event records in order.
+  std::mutex host_mu;
+  void* host_st[2] = {nullptr, nullptr};
+  void* host_ev[3] = {nullptr, nullptr, nullptr};
 };

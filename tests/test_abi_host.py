@@ -109,6 +109,13 @@ def test_host_only_plan_refuses_execution():
         with pytest.raises(N.SdftError) as ei:
             N.sdft_execute(h, 16, 16, None)
         assert ei.value.name == "SDFT_ERR_NO_DEVICE"
+        host = np.zeros(8, dtype=np.complex64)
+        with pytest.raises(N.SdftError) as ei:
+            N.sdft_execute_strided_host(h, 1, host.ctypes.data, host.ctypes.data, 16, 16, 0, None)
+        assert ei.value.name == "SDFT_ERR_NO_DEVICE"
+        with pytest.raises(N.SdftError) as ei:       # host buffers neither identical nor disjoint
+            N.sdft_execute_strided_host(h, 1, None, host.ctypes.data, 16, 16, 0, None)
+        assert ei.value.name == "SDFT_ERR_ARG"
     finally:
         N.sdft_plan_destroy(h)
 
