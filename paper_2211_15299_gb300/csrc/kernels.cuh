@@ -678,6 +678,62 @@ __global__ void __launch_bounds__(256) k_small(const typename KT<R>::C* __restri
   for (int e = 0; e < K; ++e) out[i * K + e] = v[e];
 }
 
+// ---- warp path for small batches of 2^5 <= k <= 2^10 (latency) -------------------------
+// One warp per instance, plain coalesced loads and stores (no TMA, no shared
+// memory): element t = 32 r + lane sits in lane `lane`, register r. Stage bits
+// 0..4 pair lanes (shuffles), stage bits 5..S-1 pair registers; the table is
+// level 0's, indexed absolutely (entry 2^m1 + u), and its last stage's entries
+// carry N/k, as for the level kernel.
+template <class R, int S>
+__global__ void __launch_bounds__(128) k_warp(const typename KT<R>::C* __restrict__ in,
+                                              typename KT<R>::C* __restrict__ out, uint64_t batch,
+                                              const typename KT<R>::C* __restrict__ tw, R sc) {
+  using C = typename KT<R>::C;
+  static_assert(S >= 5 && S <= 10, "warp path: 2^5 <= k <= 2^10");
+  constexpr int K = 1 << S, V = K / 32;
+  const uint64_t inst = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31u;
+  if (inst >= batch) return;   // whole warps leave together (blockDim is a multiple of 32)
+  const C* src = in + inst * K + lane;
+  C x[V];
+#pragma unroll
+  for (int r = 0; r < V; ++r) x[r] = src[32 * r];
+#pragma unroll
+  for (int m1 = 0; m1 < S; ++m1) {
+    const bool last = m1 == S - 1;
+    if (m1 < 5) {
+      const C w = __ldg(tw + (1u << m1) + (lane & ((1u << m1) - 1u)));
+      const bool hi = (lane >> m1) & 1u;
+#pragma unroll
+      for (int r = 0; r < V; ++r) {
+        C o;
+        o.x = __shfl_xor_sync(0xffffffffu, x[r].x, 1 << m1);
+        o.y = __shfl_xor_sync(0xffffffffu, x[r].y, 1 << m1);
+        C a = hi ? o : x[r], b = hi ? x[r] : o;
+        if (last)
+          bfly_scaled(a, b, w, sc);
+        else
+          bfly(a, b, w);
+        x[r] = hi ? b : a;
+      }
+    } else {
+      const int q = m1 - 5;
+#pragma unroll
+      for (int r = 0; r < V; ++r) {
+        if ((r >> q) & 1) continue;
+        const C w = __ldg(tw + (1u << m1) + lane + 32u * uint32_t(r & ((1 << q) - 1)));
+        if (last)
+          bfly_scaled(x[r], x[r | (1 << q)], w, sc);
+        else
+          bfly(x[r], x[r | (1 << q)], w);
+      }
+    }
+  }
+  C* dst = out + inst * K + lane;
+#pragma unroll
+  for (int r = 0; r < V; ++r) dst[32 * r] = x[r];
+}
+
 // Adjoint of k_small: stages S-1 .. 0; the last stage's entries carry N/k
 // (undone by sc_top = k/N), the final stage scales by sc_fin = 1/N.
 template <class R, int S>

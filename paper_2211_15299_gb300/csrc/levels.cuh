@@ -147,10 +147,35 @@ inline int level_grid(uint64_t n_tiles) {
   return int(n_tiles < max_grid ? n_tiles : max_grid);
 }
 
+// Small batches of 2^5 <= k <= 2^10 (at most kWarpMaxElems values in all): one
+// warp per instance (k_warp) instead of a TMA-fed tile.
+constexpr uint64_t kWarpMaxElems = 1ull << 14;
+
+template <class R, int S = 5>
+sdft_status dispatch_warp(int s, uint64_t batch, const void* in, void* out, const void* tw, double scale,
+                          cudaStream_t st) {
+  using C = typename KT<R>::C;
+  if constexpr (S > 10) {
+    return SDFT_ERR_UNSUPPORTED;
+  } else {
+    if (s == S) {
+      const uint64_t blocks = (batch * 32 + 127) / 128;
+      k_warp<R, S><<<unsigned(blocks), 128, 0, st>>>(static_cast<const C*>(in), static_cast<C*>(out), batch,
+                                                     static_cast<const C*>(tw), R(scale));
+      const cudaError_t e = cudaGetLastError();
+      return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
+    }
+    return dispatch_warp<R, S + 1>(s, batch, in, out, tw, scale, st);
+  }
+}
+
 template <class R>
 sdft_status launch_plan(const Plan& p, uint64_t batch, const void* in, void* out, cudaStream_t st) {
   const double scale = std::ldexp(1.0, int(p.M) - int(p.s));
   if (p.levels.empty()) return dispatch_small<R>(int(p.s), batch, in, out, p.d_tw, scale, st);
+  if (p.levels.size() == 1 && p.s >= 5 && p.s <= 10 && batch * p.k <= kWarpMaxElems)
+    return dispatch_warp<R>(int(p.s), batch, in, out,
+                            static_cast<const typename KT<R>::C*>(p.d_tw) + p.levels[0].tw_off, scale, st);
   // Level 0 on contiguous tiles.
   {
     CUtensorMap ms, md;
