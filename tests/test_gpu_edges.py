@@ -90,3 +90,35 @@ def test_smallest_supports_through_sas(J):
     y = p.execute(torch.from_numpy(F.reshape(1, -1)).cuda())
     torch.cuda.synchronize()
     assert rel_l2(y[0].cpu().numpy(), c) < 1e-12 * max(1.0, p.max_cond)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("s", [5, 7, 10])
+def test_warp_path_and_tile_path_agree_bitwise(s, prec):
+    """Small batches (at most 2^14 values) of 2^5..2^10-point transforms run one
+    warp per instance; larger ones the TMA-fed tile kernel. Both apply the same
+    butterflies in the same stage order, so the first instances agree bit for bit,
+    and both match the oracle."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan
+    rng = np.random.default_rng(6500 + 10 * s + prec)
+    M = s + 6
+    piv = np.sort(rng.choice(np.arange(M), size=s, replace=False))
+    J = W.homogeneous_support(M, piv, rng)
+    plan = Plan(M, J, prec)
+    k = plan.k
+    small = (1 << 14) // k                       # the warp path's largest batch
+    big = small + 3                              # tile path
+    Jc = O.canonical_support_by_key(J, piv)
+    C = W.complex_gaussian((big, k), rng)
+    F = O.synthesize_levels(M, piv, Jc, C).astype(np.complex64 if prec == 0 else np.complex128)
+    x = torch.from_numpy(F).cuda()
+    y_tile = plan.execute_strided(x)
+    y_warp = plan.execute_strided(x[:small].contiguous())
+    y_one = plan.execute(x[0].contiguous())
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    assert torch.equal(y_warp, y_tile[:small])
+    assert torch.equal(y_one, y_tile[0])
+    tol = 1e-5 if prec == 0 else 1e-12
+    assert rel_l2(y_warp.cpu().numpy().astype(np.complex128), C[:small]) < tol
