@@ -328,7 +328,8 @@ typedef struct sdft_sas_s* sdft_sas;
  *           Lemma "computation_shift_sample" (1.5 R 2^R mu* + 6 sum_v mu(v)^2)
  *           among R whose class systems have 1-norm condition <= 32
  *           (complex64) or <= 1000 (complex128), else the best-conditioned R.
- *   flags : 0, or SDFT_PLAN_HOST_ONLY (planning only; cannot execute).
+ *   flags : 0, SDFT_PLAN_HOST_ONLY (planning only; cannot execute), and/or
+ *           SDFT_SAS_TWO_STAGE (see sdft_sas_execute).
  * The classes of J modulo 2^(r_max+1) hold mu(v) <= mu* <= 64 members. The
  * instance needs mu* x 2^R samples: row a (a < mu*) is f at I_r + a (mod N)
  * (sdft_sas_sample_indices). The plan owns a virtual homogeneous plan with
@@ -341,6 +342,10 @@ typedef struct sdft_sas_s* sdft_sas;
  */
 sdft_status sdft_sas_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft_prec prec, uint32_t R,
                             uint32_t flags, sdft_sas* out);
+
+/* sdft_sas_create flag: always run stage 2 as its own launch (the two-launch
+ * path), also where both stages fit one launch. */
+#define SDFT_SAS_TWO_STAGE 0x4u
 
 /* R, mu*, samples per instance (mu* x 2^R), classes J occupies, and the largest
  * 1-norm condition number of the class systems (any output may be NULL). */
@@ -366,8 +371,12 @@ sdft_status sdft_sas_workspace_bytes(sdft_sas sas, uint64_t batch, uint64_t* byt
  * (support_order), d_work is the workspace (it may be d_samples itself, which
  * is then overwritten; it must not overlap d_coeffs). Stage 1 runs the virtual
  * plan over the batch x mu* shifted sample sets (Algorithm 1); stage 2 solves
- * each class with its precomputed inverse. Device buffers 16-byte aligned;
- * asynchronous on `stream`. SDFT_ERR_NO_DEVICE for host-only plans.
+ * each class with its precomputed inverse. Under complete isolation (mu* = 1)
+ * with one virtual instance per tile (R = 12 for complex64, 11 for complex128;
+ * then k <= 2^R) both stages run in one launch that keeps the stage-1 output
+ * on chip: d_work is then not touched and d_samples must not overlap d_coeffs
+ * (SDFT_SAS_TWO_STAGE keeps the two launches). Both paths give the same bits. Device buffers 16-byte
+ * aligned; asynchronous on `stream`. SDFT_ERR_NO_DEVICE for host-only plans.
  */
 sdft_status sdft_sas_execute(sdft_sas sas, uint64_t batch, const void* d_samples, void* d_work, void* d_coeffs,
                              void* stream);

@@ -252,12 +252,20 @@ class Sas:
     a homogeneous virtual support over shifted sample sets, then one small
     Vandermonde solve per class."""
 
-    def __init__(self, log2N: int, J: Sequence[int], prec="c64", R: int = 0, host_only: bool = False):
+    def __init__(self, log2N: int, J: Sequence[int], prec="c64", R: int = 0, host_only: bool = False,
+                 two_stage: bool = False):
+        """two_stage: always run the class solves as their own launch (otherwise
+        both stages share one launch where one virtual instance fills a tile)."""
         self.prec = _PREC[prec] if isinstance(prec, str) else int(prec)
         J = np.asarray(J, dtype=np.uint64)
         self.log2N, self.k = int(log2N), int(J.size)
-        self.handle = N.sdft_sas_create(log2N, J, self.prec, R, N.SDFT_PLAN_HOST_ONLY if host_only else 0)
+        flags = (N.SDFT_PLAN_HOST_ONLY if host_only else 0) | (N.SDFT_SAS_TWO_STAGE if two_stage else 0)
+        self.handle = N.sdft_sas_create(log2N, J, self.prec, R, flags)
         self.R, self.mu_star, self.n_samples, self.occupied, self.max_cond = N.sdft_sas_info(self.handle)
+        # launches per execute: one under complete isolation with one virtual
+        # instance per tile (the rule of sdft_sas_execute), else two
+        tb = 12 if self.prec == N.SDFT_C64 else 11
+        self.launches = 1 if (not two_stage and self.mu_star == 1 and self.R == tb and self.k <= (1 << tb)) else 2
 
     @property
     def pivots(self) -> np.ndarray:

@@ -28,6 +28,7 @@
 
 #include "kernels.cuh"
 #include "launch.hpp"
+#include "levels.cuh"
 #include "plan.hpp"
 
 namespace sdft {
@@ -58,6 +59,9 @@ struct Sas {
   int device = -1;
   SasOut* d_meta = nullptr;
   void* d_winv = nullptr;
+  bool two_stage = false;          // SDFT_SAS_TWO_STAGE: stage 2 as its own launch always
+  uint16_t* d_col = nullptr;       // one-launch path (mu* = 1): t_i per coefficient
+  void* d_w1 = nullptr;            //   and its class's 1 x 1 inverse
 };
 
 // Class keys of J for pivots p[0..R-1]: bit q of the key is bit p[q] of j.
@@ -276,7 +280,11 @@ sdft_status build_sas(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec,
   return SDFT_OK;
 }
 
-// Stage 2: coefficient i of instance b = sum_a Winv_t[u][a] Y[b][a][t].
+// Stage 2: coefficient i of instance b = sum_a Winv_t[u][a] Y[b][a][t]. A
+// thread takes coefficient i of kSasDecodeB instances b = blockIdx.y + q
+// gridDim.y (q < kSasDecodeB): its class's inverse row is read once for all of
+// them and their values are gathered together.
+constexpr uint32_t kSasDecodeB = 8;
 template <class R>
 __global__ void __launch_bounds__(256) k_sas_decode(const typename KT<R>::C* __restrict__ y,
                                                     typename KT<R>::C* __restrict__ out,
@@ -287,26 +295,194 @@ __global__ void __launch_bounds__(256) k_sas_decode(const typename KT<R>::C* __r
   const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= k) return;
   const SasOut m = meta[i];
-  for (uint64_t b = blockIdx.y; b < batch; b += gridDim.y) {
-    const C* yb = y + b * uint64_t(mu_star) * nk + m.t;
-    R re = 0, im = 0;
+  const C* wrow = winv + m.woff + uint32_t(m.u) * m.mu;
+  for (uint64_t b0 = blockIdx.y; b0 < batch; b0 += uint64_t(gridDim.y) * kSasDecodeB) {
+    R re[kSasDecodeB], im[kSasDecodeB];
+#pragma unroll
+    for (uint32_t q = 0; q < kSasDecodeB; ++q) re[q] = im[q] = R(0);
     for (uint32_t a = 0; a < m.mu; ++a) {
-      const C w = winv[m.woff + uint32_t(m.u) * m.mu + a];
-      const C v = yb[uint64_t(a) * nk];
-      re = fma(w.x, v.x, fma(-w.y, v.y, re));
-      im = fma(w.x, v.y, fma(w.y, v.x, im));
+      const C w = wrow[a];
+#pragma unroll
+      for (uint32_t q = 0; q < kSasDecodeB; ++q) {
+        const uint64_t b = b0 + uint64_t(q) * gridDim.y;
+        if (b < batch) {
+          const C v = y[(b * uint64_t(mu_star) + a) * nk + m.t];
+          re[q] = fma(w.x, v.x, fma(-w.y, v.y, re[q]));
+          im[q] = fma(w.x, v.y, fma(w.y, v.x, im[q]));
+        }
+      }
     }
-    C o;
-    o.x = re;
-    o.y = im;
-    out[b * k + i] = o;
+#pragma unroll
+    for (uint32_t q = 0; q < kSasDecodeB; ++q) {
+      const uint64_t b = b0 + uint64_t(q) * gridDim.y;
+      if (b < batch) {
+        C o;
+        o.x = re[q];
+        o.y = im[q];
+        out[b * k + i] = o;
+      }
+    }
   }
 }
+
+// Both stages in one launch for complete isolation (mu* = 1: every class holds
+// one member, coefficient i = Winv_i Y[t_i]) when one virtual instance fills one
+// tile (R = TB) and k <= 2^TB: CTA c takes instances b = c, c + G, ... (one tile
+// each, the level kernel's passes with the last stage scaled), keeps the
+// per-coefficient pairs (t_i, Winv_i) in shared memory for the whole launch,
+// and after the passes writes every coefficient straight from the tile. The
+// stage-1 output never leaves the SM; the product is formed as in k_sas_decode,
+// so both paths give the same bits. (With mu* > 1 the class solves need mu*
+// tiles per instance and their inverse rows: they stay a launch of their own.)
+template <class R>
+struct SasFusedArgs {
+  LevelArgs<R> a;                        // level 0 of the virtual plan over the batch
+  const uint16_t* col;                   // t_i: column of the stage-1 output
+  const typename KT<R>::C* w;            // Winv_i (1 x 1 inverses)
+  typename KT<R>::C* out;                // batch x k coefficients
+  uint64_t k, batch;
+};
+
+template <class R>
+constexpr uint32_t sas_fused_smem() {
+  return kLevelBufs * kTileBytes + 64 + kMidTwBytes +
+         (1u << KT<R>::TB) * uint32_t(sizeof(typename KT<R>::C) + sizeof(uint16_t)) + 1024;
+}
+
+template <class R>
+__global__ void __launch_bounds__(KT<R>::NT, 2)
+    k_sas_fused(const __grid_constant__ CUtensorMap src, const __grid_constant__ SasFusedArgs<R> fa) {
+  using C = typename KT<R>::C;
+  constexpr int TB = KT<R>::TB;
+  constexpr uint32_t NT = KT<R>::NT;
+  constexpr int NREG = reg_twiddles(TB, 0, TB);
+  constexpr int MLO = mid_pass_lo(TB, 0, TB), MHI = mid_pass_hi(TB, 0, TB);
+  constexpr bool MIDSM = MLO < MHI && (1u << MHI) * sizeof(C) <= kMidTwBytes;
+  extern __shared__ char smem_raw[];
+  char* smem = align1024(smem_raw);
+  const uint32_t bar0 = ptx::smem_addr(smem + kLevelBufs * kTileBytes);
+  const uint32_t tid = threadIdx.x;
+  C* midtw = reinterpret_cast<C*>(smem + kLevelBufs * kTileBytes + 64);
+  C* ws = reinterpret_cast<C*>(smem + kLevelBufs * kTileBytes + 64 + kMidTwBytes);
+  uint16_t* cs = reinterpret_cast<uint16_t*>(ws + (1u << TB));
+  {
+    const uint32_t used = uint32_t(smem - smem_raw) + sas_fused_smem<R>() - 1024;
+    int bad = 0;
+    if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
+    else if (reinterpret_cast<uintptr_t>(&src) & 63u) bad = kBadMap;
+    else if (reinterpret_cast<uintptr_t>(fa.a.tw) & 15u) bad = kBadTable;
+    if (bad) {
+      if (tid == 0) atomicCAS(fa.a.status, 0, bad);
+      return;
+    }
+  }
+  const uint64_t G = gridDim.x;
+  if (blockIdx.x >= fa.batch) return;
+  const uint64_t n = (fa.batch - blockIdx.x + G - 1) / G;     // instances (tiles) of this CTA
+  uint32_t load_buf = 0;
+  auto issue_load = [&](uint64_t j) {
+    const uint32_t b = load_buf;
+    load_buf = (load_buf + 1 == uint32_t(kLevelBufs)) ? 0u : load_buf + 1;
+    const uint32_t bar = bar0 + 8 * b;
+    ptx::mbar_arrive_expect_tx(bar, kTileBytes);
+    const int row = int(int64_t(blockIdx.x + j * G) * fa.a.b_step1);
+    ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &src, bar, 0, row, 0, 0);
+  };
+  if (tid == 0) {
+    for (int b = 0; b < kLevelBufs; ++b) ptx::mbar_init(bar0 + 8 * b, 1);
+    ptx::fence_mbar_init();
+    ptx::prefetch_tensormap(&src);
+    for (uint64_t j = 0; j < n && j < uint64_t(kLevelBufs); ++j) issue_load(j);
+  }
+  const C* tw = static_cast<const C*>(fa.a.tw);
+  C wreg[NREG > 0 ? NREG : 1];
+  load_reg_twiddles<R, 0, TB>(tw, tid, wreg);
+  if constexpr (MIDSM) {
+    for (uint32_t e = (1u << MLO) + tid; e < (1u << MHI); e += NT) midtw[e] = tw[e];
+  }
+  for (uint64_t i = tid; i < fa.k; i += NT) {   // the decode table, once per CTA
+    ws[i] = fa.w[i];
+    cs[i] = fa.col[i];
+  }
+  __syncthreads();
+  const uint32_t midtw_addr = ptx::smem_addr(midtw);
+  const R sc = R(fa.a.scale);
+  bool aborted = false;
+  uint32_t b = 0, phases = 0;
+  uint64_t j = 0;
+  for (; j < n; ++j, b = (b + 1 == uint32_t(kLevelBufs)) ? 0u : b + 1) {
+    char* buf = smem + b * kTileBytes;
+    const bool ok = ptx::mbar_wait_bounded(bar0 + 8 * b, (phases >> b) & 1u, fa.a.timeout_ns);
+    phases ^= 1u << b;
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    // after the first pass every thread is done with tile j-1: its buffer takes tile j+1
+    auto refill = [&]() {
+      if (tid == 0 && j >= 1 && j + kLevelBufs - 1 < n) issue_load(j + kLevelBufs - 1);
+    };
+    run_passes<R, 0, TB, true, 0, 0, MIDSM>(buf, wreg, fa.a.tw0, tw, tid, sc, midtw_addr, refill);
+    C* ob = fa.out + (blockIdx.x + j * G) * fa.k;
+    for (uint64_t i = tid; i < fa.k; i += NT) {
+      const C w = ws[i];
+      const uint32_t t = cs[i];
+      const C v = *reinterpret_cast<const C*>(buf + row_part<R>(t) + xor_part<R>(t));
+      C o;
+      o.x = fma(w.x, v.x, fma(-w.y, v.y, R(0)));
+      o.y = fma(w.x, v.y, fma(w.y, v.x, R(0)));
+      ob[i] = o;
+    }
+  }
+  if (tid == 0 && aborted) {
+    const uint64_t last = (j + kLevelBufs - 2 > uint64_t(kLevelBufs - 1)) ? j + kLevelBufs - 2
+                                                                           : uint64_t(kLevelBufs - 1);
+    for (uint64_t q = j; q <= last && q < n; ++q)
+      ptx::mbar_wait_bounded(bar0 + 8 * uint32_t(q % kLevelBufs), uint32_t((q / kLevelBufs) & 1),
+                             fa.a.timeout_ns);
+    atomicExch(fa.a.status, int(SDFT_ERR_TIMEOUT));
+  }
+}
+
+template <class R>
+sdft_status launch_sas_fused(const Sas& S, uint64_t batch, const void* d_samples, void* d_coeffs,
+                             cudaStream_t st) {
+  const Plan& vp = S.vplan->p;
+  CUtensorMap ms, md;
+  SasFusedArgs<R> fa{};
+  sdft_status s = level0_setup<R>(vp, batch, d_samples, const_cast<void*>(d_samples), ms, md, fa.a);
+  if (s != SDFT_OK) return s;
+  fa.col = S.d_col;
+  fa.w = static_cast<const typename KT<R>::C*>(S.d_w1);
+  fa.out = static_cast<typename KT<R>::C*>(d_coeffs);
+  fa.k = S.k;
+  fa.batch = batch;
+  auto fn = k_sas_fused<R>;
+  s = ensure_smem(reinterpret_cast<const void*>(fn), int(sas_fused_smem<R>()));
+  if (s != SDFT_OK) return s;
+  const uint64_t max_grid = 2ull * uint64_t(sm_count());
+  const unsigned grid = unsigned(batch < max_grid ? batch : max_grid);
+  fn<<<grid, KT<R>::NT, sas_fused_smem<R>(), st>>>(ms, fa);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
+}
+
+// Complete isolation, one virtual instance per tile, at most a tile's worth of
+// coefficients.
+bool sas_fused_shape(const Sas& S) {
+  const uint32_t TB = S.prec == SDFT_C64 ? KT<float>::TB : KT<double>::TB;
+  return S.mu_star == 1 && S.R == TB && S.k <= (1ull << TB);
+}
+bool sas_fused_applies(const Sas& S) { return !S.two_stage && S.d_col && S.d_w1 && sas_fused_shape(S); }
 
 void free_sas(Sas& S) {
   if (S.vplan) sdft_plan_destroy(S.vplan);
   if (S.d_meta) cudaFree(S.d_meta);
   if (S.d_winv) cudaFree(S.d_winv);
+  if (S.d_col) cudaFree(S.d_col);
+  if (S.d_w1) cudaFree(S.d_w1);
+  S.d_col = nullptr;
+  S.d_w1 = nullptr;
   S.vplan = nullptr;
   S.d_meta = nullptr;
   S.d_winv = nullptr;
@@ -326,10 +502,11 @@ sdft_status sdft_sas_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft_
   using namespace sdft;
   if (!out) return SDFT_ERR_ARG;
   *out = nullptr;
-  if (flags & ~SDFT_PLAN_HOST_ONLY) return SDFT_ERR_ARG;
+  if (flags & ~(SDFT_PLAN_HOST_ONLY | SDFT_SAS_TWO_STAGE)) return SDFT_ERR_ARG;
   sdft_sas_s* h = new (std::nothrow) sdft_sas_s();
   if (!h) return SDFT_ERR_NOMEM;
   Sas& S = h->s;
+  S.two_stage = (flags & SDFT_SAS_TWO_STAGE) != 0;
   sdft_status st;
   try {
     st = build_sas(log2N, J, k, prec, R, S);
@@ -356,6 +533,28 @@ sdft_status sdft_sas_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft_
         e = cudaMemcpy(S.d_winv, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice);
       } else {
         e = cudaMemcpy(S.d_winv, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice);
+      }
+    }
+    // the one-launch path's table: t_i and the 1 x 1 inverse of coefficient i's class,
+    // the same rounded values stage 2 reads
+    if (st == SDFT_OK && e == cudaSuccess && sas_fused_shape(S)) {
+      std::vector<uint16_t> col(S.k);
+      std::vector<double> w1(2 * S.k);
+      for (uint64_t i = 0; i < S.k; ++i) {
+        col[i] = uint16_t(S.meta[i].t);
+        w1[2 * i] = S.winv[S.meta[i].woff].real();
+        w1[2 * i + 1] = S.winv[S.meta[i].woff].imag();
+      }
+      e = cudaMalloc(reinterpret_cast<void**>(&S.d_col), sizeof(uint16_t) * S.k);
+      if (e == cudaSuccess) e = cudaMalloc(&S.d_w1, eb * S.k);
+      if (e == cudaSuccess) e = cudaMemcpy(S.d_col, col.data(), sizeof(uint16_t) * S.k, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) {
+        if (prec == SDFT_C64) {
+          std::vector<float> wf(w1.begin(), w1.end());
+          e = cudaMemcpy(S.d_w1, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice);
+        } else {
+          e = cudaMemcpy(S.d_w1, w1.data(), sizeof(double) * w1.size(), cudaMemcpyHostToDevice);
+        }
       }
     }
     if (st == SDFT_OK && e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? SDFT_ERR_NOMEM : cuda_fail(e);
@@ -421,10 +620,18 @@ sdft_status sdft_sas_execute(sdft_sas sas, uint64_t batch, const void* d_samples
   if (w < o + obytes && o < w + wbytes) return SDFT_ERR_ARG;     // the decoder reads work while writing coeffs
   if ((w | o) & 15u) return SDFT_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (sas_fused_applies(S)) {
+    if (reinterpret_cast<uintptr_t>(d_samples) & 15u) return SDFT_ERR_ARG;
+    const uintptr_t in = reinterpret_cast<uintptr_t>(d_samples);
+    if (in < o + obytes && o < in + wbytes) return SDFT_ERR_ARG;   // samples are read while coeffs are written
+    return S.prec == SDFT_C64 ? launch_sas_fused<float>(S, batch, d_samples, d_coeffs, st)
+                              : launch_sas_fused<double>(S, batch, d_samples, d_coeffs, st);
+  }
   sdft_status s = sdft_execute_strided(S.vplan, batch * S.mu_star, d_samples, d_work, stream);
   if (s != SDFT_OK) return s;
   const dim3 block(256);
-  const dim3 grid(unsigned((S.k + 255) / 256), unsigned(std::min<uint64_t>(batch, 65535)));
+  const uint64_t rows = (batch + kSasDecodeB - 1) / kSasDecodeB;
+  const dim3 grid(unsigned((S.k + 255) / 256), unsigned(std::min<uint64_t>(rows, 65535)));
   if (S.prec == SDFT_C64)
     k_sas_decode<float><<<grid, block, 0, st>>>(static_cast<const float2*>(d_work), static_cast<float2*>(d_coeffs),
                                                 S.d_meta, static_cast<const float2*>(S.d_winv), S.k, nk, S.mu_star,

@@ -114,3 +114,38 @@ def test_generalized_progression(sizes):
     J = [int(j) for j in W.generalized_arithmetic_progression(20, sizes, rng)]
     p, got, C, ref = _case(20, J, "c64", 0, 2, np.random.default_rng(9))
     assert rel_l2(got, ref) < _tol("c64", p.max_cond) and rel_l2(got, C) < _tol("c64", p.max_cond)
+
+
+@pytest.mark.parametrize("kind,k,prec,batch", [("ap", 3000, "c64", 700), ("ap", 3000, "c64", 5),
+                                               ("ap", 2000, "c128", 333), ("subset", 3000, "c64", 5)])
+def test_one_launch_and_two_launch_paths_agree_bitwise(kind, k, prec, batch):
+    """Under complete isolation (mu* = 1) with one virtual instance per tile
+    (R = 12 complex64, 11 complex128) both stages share one launch; the two-launch
+    path (SDFT_SAS_TWO_STAGE) gives the same bits, and both match the oracle
+    (the subset case, mu* = 3, runs two launches either way)."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Sas
+    J = [int(j) for j in W.workload_sas(kind, k=k)]
+    one = Sas(20, J, prec)
+    two = Sas(20, J, prec, two_stage=True)
+    assert (one.R, one.mu_star) == (two.R, two.mu_star)
+    if kind == "ap":
+        assert one.mu_star == 1 and one.R == (12 if prec == "c64" else 11)
+    dt = torch.complex64 if prec == "c64" else torch.complex128
+    g = torch.Generator(device="cuda")
+    g.manual_seed(77)
+    x = torch.randn((batch, one.n_samples), dtype=dt, device="cuda", generator=g)
+    x_keep = x.clone()
+    y1 = one.execute(x)
+    y2 = two.execute(x)
+    torch.cuda.synchronize()
+    assert torch.equal(x, x_keep)               # the samples are left alone
+    assert torch.equal(y1, y2)
+    # a few rows against the oracle on the same rounded samples
+    order = [int(j) for j in one.support_order]
+    r = [int(v) for v in one.pivots]
+    f_in = x.cpu().numpy().astype(np.complex128).reshape(batch, one.mu_star, -1)
+    got = y1.cpu().numpy().astype(np.complex128)
+    for b in (0, batch - 1):
+        ref = O.sas_transform(20, order, r, f_in[b])
+        assert rel_l2(got[b], ref) < _tol(prec, one.max_cond)
