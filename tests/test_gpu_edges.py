@@ -93,7 +93,7 @@ def test_smallest_supports_through_sas(J):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("s", [5, 7, 10])
+@pytest.mark.parametrize("s", [5, 6, 7, 8, 9, 10])
 def test_warp_path_and_tile_path_agree_bitwise(s, prec):
     """Small batches (at most 2^14 values) of 2^5..2^10-point transforms run one
     warp per instance; larger ones the TMA-fed tile kernel. Both apply the same
