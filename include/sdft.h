@@ -158,6 +158,11 @@ sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_s
 sdft_status sdft_execute_strided_host(sdft_plan plan, uint64_t batch, const void* h_samples, void* h_coeffs,
                                       void* d_samples, void* d_coeffs, uint64_t chunk, void* stream);
 
+/* The same for synthesis (sdft_synthesize_strided): h_coeffs in, h_samples out,
+ * through the device buffers d_coeffs and d_samples. */
+sdft_status sdft_synthesize_strided_host(sdft_plan plan, uint64_t batch, const void* h_coeffs, void* h_samples,
+                                         void* d_coeffs, void* d_samples, uint64_t chunk, void* stream);
+
 /*
  * sdft_synthesize / sdft_synthesize_strided - the inverse map: samples
  * f_I = F^{-1}(I_r, J) c = (1/N) F(J, I_r)^H c from coefficients c (Section II,

@@ -61,6 +61,7 @@ SIGNATURES = {
     "sdft_execute": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "sdft_execute_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "sdft_execute_strided_host": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
+    "sdft_synthesize_strided_host": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
     "sdft_synthesize": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "sdft_synthesize_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "sdft_plan_set_strategy": (c_int, [c_vp, c_int]),
@@ -207,6 +208,13 @@ def sdft_execute_strided_host(plan: int, batch: int, h_samples, h_coeffs, d_samp
                               stream=None) -> None:
     _check(_lib.sdft_execute_strided_host(plan, int(batch), _ptr(h_samples), _ptr(h_coeffs), _ptr(d_samples),
                                           _ptr(d_coeffs), int(chunk), _stream(stream)), "sdft_execute_strided_host")
+
+
+def sdft_synthesize_strided_host(plan: int, batch: int, h_coeffs, h_samples, d_coeffs, d_samples, chunk: int = 0,
+                                 stream=None) -> None:
+    _check(_lib.sdft_synthesize_strided_host(plan, int(batch), _ptr(h_coeffs), _ptr(h_samples), _ptr(d_coeffs),
+                                             _ptr(d_samples), int(chunk), _stream(stream)),
+           "sdft_synthesize_strided_host")
 
 
 def sdft_plan_set_strategy(plan: int, strategy: int) -> None:

@@ -110,28 +110,37 @@ class Plan:
         and copy-out in overlapped chunks of `chunk` instances (0: about 16 MiB).
         Device staging buffers are allocated here when not given. The result is in
         `h_coeffs` once `stream` (the current stream by default) reaches this point."""
+        return self._host(N.sdft_execute_strided_host, h_samples, h_coeffs, d_samples, d_coeffs, chunk, stream,
+                          batch)
+
+    def synthesize_host(self, h_coeffs, h_samples=None, d_coeffs=None, d_samples=None, chunk: int = 0,
+                        stream=None, batch: Optional[int] = None):
+        """synthesize on host tensors, copies overlapped in chunks (see execute_host)."""
+        return self._host(N.sdft_synthesize_strided_host, h_coeffs, h_samples, d_coeffs, d_samples, chunk, stream,
+                          batch)
+
+    def _host(self, fn, h_in, h_out, d_in, d_out, chunk, stream, batch):
         torch = _torch()
         if batch is None:
-            batch = h_samples.numel() // self.k
-        for t, what in ((h_samples, "h_samples"), (h_coeffs, "h_coeffs")):
+            batch = h_in.numel() // self.k
+        for t, what in ((h_in, "host input"), (h_out, "host output")):
             if t is None:
                 continue
             if not isinstance(t, torch.Tensor) or t.is_cuda:
                 raise ValueError(f"{what} must be a host tensor")
             if t.dtype != self.dtype or not t.is_contiguous() or t.numel() != batch * self.k:
                 raise ValueError(f"{what} must be a contiguous {self.dtype} tensor of {batch * self.k} values")
-        if h_coeffs is None:
-            h_coeffs = torch.empty_like(h_samples, pin_memory=True)
+        if h_out is None:
+            h_out = torch.empty_like(h_in, pin_memory=True)
         dev = torch.device("cuda", torch.cuda.current_device())
-        if d_samples is None:
-            d_samples = torch.empty(batch * self.k, dtype=self.dtype, device=dev)
-        if d_coeffs is None:
-            d_coeffs = torch.empty(batch * self.k, dtype=self.dtype, device=dev)
-        _check_tensor(d_samples, self.dtype, batch * self.k, "d_samples")
-        _check_tensor(d_coeffs, self.dtype, batch * self.k, "d_coeffs")
-        N.sdft_execute_strided_host(self.handle, batch, h_samples, h_coeffs, d_samples, d_coeffs, chunk,
-                                    _current_stream(stream))
-        return h_coeffs
+        if d_in is None:
+            d_in = torch.empty(batch * self.k, dtype=self.dtype, device=dev)
+        if d_out is None:
+            d_out = torch.empty(batch * self.k, dtype=self.dtype, device=dev)
+        _check_tensor(d_in, self.dtype, batch * self.k, "device input")
+        _check_tensor(d_out, self.dtype, batch * self.k, "device output")
+        fn(self.handle, batch, h_in, h_out, d_in, d_out, chunk, _current_stream(stream))
+        return h_out
 
     def synthesize(self, coeffs, samples=None, stream=None, batch: Optional[int] = None):
         """Samples from coefficients (the inverse of execute_strided)."""

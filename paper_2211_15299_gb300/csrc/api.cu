@@ -268,8 +268,14 @@ sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_s
   return sdft::run_strided(plan, batch, d_samples, d_coeffs, static_cast<cudaStream_t>(stream));
 }
 
-sdft_status sdft_execute_strided_host(sdft_plan plan, uint64_t batch, const void* h_samples, void* h_coeffs,
-                                      void* d_samples, void* d_coeffs, uint64_t chunk, void* stream) {
+// Host-buffer batches: chunked copy-in, transform (or synthesis) and copy-out
+// overlapped on the plan's two copy streams and the caller's stream.
+static sdft_status run_host(sdft_plan plan, uint64_t batch, const void* h_in_buf, void* h_out_buf, void* d_in_buf,
+                            void* d_out_buf, uint64_t chunk, void* stream, bool inverse) {
+  const void* h_samples = h_in_buf;
+  void* h_coeffs = h_out_buf;
+  void* d_samples = d_in_buf;
+  void* d_coeffs = d_out_buf;
   if (!plan || !h_samples || !h_coeffs) return SDFT_ERR_ARG;
   const sdft::Plan& p = plan->p;
   if (p.device < 0 || !p.d_status) return SDFT_ERR_NO_DEVICE;
@@ -322,7 +328,8 @@ sdft_status sdft_execute_strided_host(sdft_plan plan, uint64_t batch, const void
     if (e == cudaSuccess) e = cudaEventRecord(ev_in, in_st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in, 0);
     if (e != cudaSuccess) return sdft::cuda_fail(e);
-    const sdft_status s = sdft::run_strided(plan, nb, di + off, dout + off, cs);
+    const sdft_status s = inverse ? sdft::run_strided_inverse(plan, nb, di + off, dout + off, cs)
+                                  : sdft::run_strided(plan, nb, di + off, dout + off, cs);
     if (s != SDFT_OK) return s;
     e = cudaEventRecord(ev_done, cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(out_st, ev_done, 0);
@@ -333,6 +340,16 @@ sdft_status sdft_execute_strided_host(sdft_plan plan, uint64_t batch, const void
   e = cudaEventRecord(ev_mark, out_st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_mark, 0);
   return e == cudaSuccess ? SDFT_OK : sdft::cuda_fail(e);
+}
+
+sdft_status sdft_execute_strided_host(sdft_plan plan, uint64_t batch, const void* h_samples, void* h_coeffs,
+                                      void* d_samples, void* d_coeffs, uint64_t chunk, void* stream) {
+  return run_host(plan, batch, h_samples, h_coeffs, d_samples, d_coeffs, chunk, stream, false);
+}
+
+sdft_status sdft_synthesize_strided_host(sdft_plan plan, uint64_t batch, const void* h_coeffs, void* h_samples,
+                                         void* d_coeffs, void* d_samples, uint64_t chunk, void* stream) {
+  return run_host(plan, batch, h_coeffs, h_samples, d_coeffs, d_samples, chunk, stream, true);
 }
 
 sdft_status sdft_synthesize(sdft_plan plan, const void* d_coeffs, void* d_samples, void* stream) {

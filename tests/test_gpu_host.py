@@ -70,3 +70,27 @@ def test_host_path_in_place_and_on_a_side_stream():
         torch.cuda.current_stream().synchronize()
         assert torch.equal(h2, ref)
     assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("prec,s,batch", [(0, 12, 40), (0, 15, 6), (1, 11, 10)])
+def test_host_synthesis_round_trip(prec, s, batch):
+    """synthesize_host equals the device synthesis bit for bit, and host
+    transform after host synthesis returns the coefficients."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan
+    rng = np.random.default_rng(8950 + s + prec)
+    M = s + 4
+    piv = W.random_pivots(M, s, rng)
+    plan = Plan(M, W.homogeneous_support(M, piv, rng), prec)
+    dt = torch.complex64 if prec == 0 else torch.complex128
+    C = torch.from_numpy(W.complex_gaussian((batch, plan.k), rng)).to(dt).reshape(-1)
+    ref = plan.synthesize(C.cuda()).cpu()
+    h_c = C.clone().pin_memory()
+    h_f = plan.synthesize_host(h_c, chunk=3)
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(h_f, ref)
+    back = plan.execute_host(h_f.pin_memory(), chunk=5)
+    torch.cuda.current_stream().synchronize()
+    assert plan.device_status() == 0
+    err = float(torch.linalg.vector_norm((back - C).to(torch.complex128)) / torch.linalg.vector_norm(C.to(torch.complex128)))
+    assert err < (1e-5 if prec == 0 else 1e-12)
