@@ -57,7 +57,7 @@ typedef enum {
   SDFT_ERR_BUDGET = 7,          /* request exceeds a caller-set memory budget    */
   SDFT_ERR_CUDA = 8,            /* a CUDA runtime/driver call failed             */
   SDFT_ERR_TIMEOUT = 9,         /* a bounded device-side wait expired            */
-  SDFT_ERR_UNSUPPORTED = 10,    /* size or mode outside what this build supports */
+  SDFT_ERR_UNSUPPORTED = 10,    /* size or mode outside what the library supports */
   SDFT_ERR_NO_DEVICE = 11,      /* plan was created host-only / no CUDA device   */
   SDFT_ERR_PRECISION = 12       /* plans of different precision mixed in a batch */
 } sdft_status;
@@ -71,7 +71,7 @@ typedef enum { SDFT_C64 = 0, SDFT_C128 = 1 } sdft_prec;
                                        (sdft_server_submit), which uploads them into its arena
                                        per request, so creating it allocates no device memory */
 
-/* Largest log2N and log2 k this build accepts. */
+/* Largest log2N and log2 k the library accepts. */
 #define SDFT_MAX_LOG2N 62u
 #define SDFT_MAX_LOG2K 28u
 

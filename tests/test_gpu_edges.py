@@ -19,7 +19,7 @@ def _torch():
 @pytest.mark.parametrize("s", [5, 13])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_largest_N(s, prec):
-    # N = 2^62 (the largest this build accepts): N/k = 2^(62-s) folded into the
+    # N = 2^62 (the largest the library accepts): N/k = 2^(62-s) folded into the
     # last stage, twiddle residues up to 61 bits
     if prec == 1 and s > 12:
         pytest.skip("complex128 at s = 5 only")
