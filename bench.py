@@ -230,6 +230,20 @@ def run_ours(args):
 
     tpi = time_device_steps(step64_per_instance, 3, 1, flush, stream)
     fp64_per_instance = n_pi * k / statistics.mean(tpi)
+    # complex128 in double-float arithmetic on the FP32 pipes (SDFT_PLAN_FP64_DF)
+    plan_df = Plan(M, inst.J, "c128", fp64_df=True)
+    y_df = torch.empty_like(x64)
+
+    def step_df():
+        plan_df.execute_strided(x64, y_df, stream=stream.cuda_stream)
+
+    tdf = time_device_steps(step_df, max(2, args.steps // 4), 2, flush, stream)
+    fp64_df = coeffs_per_step / statistics.mean(tdf)
+    step64()
+    step_df()
+    torch.cuda.synchronize()
+    rel_df_vs_fp64 = float(torch.linalg.vector_norm(y_df - y64) / torch.linalg.vector_norm(y64))
+    del y_df, plan_df
     # synthesis (the inverse map) on the same batch, graph-replayed
     ysyn = torch.empty_like(x32)
 
@@ -300,7 +314,8 @@ def run_ours(args):
         "gpu_launches": int(args.steps * n_levels),
         "roofline": roofline,
         "fp64": {"batched_coeffs_per_s": fp64_batched, "per_instance_coeffs_per_s": fp64_per_instance,
-                 "per_instance_sample": n_pi, "fp32_speedup_vs_per_instance": value / ws / fp64_per_instance},
+                 "per_instance_sample": n_pi, "fp32_speedup_vs_per_instance": value / ws / fp64_per_instance,
+                 "batched_double_float_coeffs_per_s": fp64_df, "rel_l2_double_float_vs_fp64": rel_df_vs_fp64},
         "rel_l2_fp32_vs_fp64": rel_fp32_vs_fp64,
         "fft_ceiling": fft_ceiling,
         "synthesis": synthesis,

@@ -32,6 +32,7 @@ SDFT_C64, SDFT_C128 = 0, 1
 SDFT_STRATEGY_LEVELS, SDFT_STRATEGY_QUEUE = 1, 2
 SDFT_SCHEDULE_AUTO, SDFT_SCHEDULE_LANES, SDFT_SCHEDULE_ROUND_ROBIN = 0, 1, 2
 SDFT_PLAN_HOST_ONLY = 0x1
+SDFT_PLAN_FP64_DF = 0x8
 SDFT_SAS_TWO_STAGE = 0x4
 SDFT_PLAN_DEFER_DEVICE = 0x2
 

@@ -48,11 +48,14 @@ def _check_tensor(t, dtype, numel: int, what: str):
 class Plan:
     """A validated homogeneous support with its sample set and device twiddles."""
 
-    def __init__(self, log2N: int, J: Sequence[int], prec="c64", host_only: bool = False, defer: bool = False):
+    def __init__(self, log2N: int, J: Sequence[int], prec="c64", host_only: bool = False, defer: bool = False,
+                 fp64_df: bool = False):
         """host_only: host tables only (introspection). defer: device tables kept in host
-        memory until a Server uploads them with a request (no device allocation)."""
+        memory until a Server uploads them with a request (no device allocation).
+        fp64_df (complex128): butterflies in double-float arithmetic on the FP32 pipes."""
         code = _PREC[prec] if isinstance(prec, str) else int(prec)
         flags = (N.SDFT_PLAN_HOST_ONLY if host_only else 0) | (N.SDFT_PLAN_DEFER_DEVICE if defer else 0)
+        flags |= N.SDFT_PLAN_FP64_DF if fp64_df else 0
         self.handle = N.sdft_plan_create(log2N, J, code, flags)
         self.log2N, self.s, self.prec = N.sdft_plan_info(self.handle)
         self.k = 1 << self.s

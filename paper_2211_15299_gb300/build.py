@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 SOURCES = ["plan.cpp", "api.cu", "batch.cu", "level_f32.cu", "level_f64.cu", "queue_f32.cu", "queue_f64.cu", "server.cu",
-           "sas.cu", "inverse_f32.cu", "inverse_f64.cu"]
+           "sas.cu", "inverse_f32.cu", "inverse_f64.cu", "level_df.cu"]
 
 
 def _nvcc() -> str:

@@ -124,7 +124,8 @@ sdft_status run_strided(sdft_plan_s* h, uint64_t batch, const void* in, void* ou
   // faster at N = 2^30, k = 2^20, batch 64; the queue halves the DRAM traffic
   // there but its per-item work bounds it.
   if (p.levels.size() > 1 && p.strategy == SDFT_STRATEGY_QUEUE) return run_strided_queue(h, batch, in, out, st);
-  return p.prec == SDFT_C64 ? launch_plan_f32(p, batch, in, out, st) : launch_plan_f64(p, batch, in, out, st);
+  if (p.prec == SDFT_C64) return launch_plan_f32(p, batch, in, out, st);
+  return p.d_tw_df ? launch_plan_df(p, batch, in, out, st) : launch_plan_f64(p, batch, in, out, st);
 }
 
 // Synthesis of `batch` instances: samples from coefficients.
@@ -137,7 +138,8 @@ static sdft_status run_strided_inverse(sdft_plan_s* h, uint64_t batch, const voi
   if (batch > (~0ull / eb) / p.k) return SDFT_ERR_ARG;
   s = check_buffers(in, out, batch * p.k * eb);
   if (s != SDFT_OK) return s;
-  return p.prec == SDFT_C64 ? launch_plan_inv_f32(p, batch, in, out, st) : launch_plan_inv_f64(p, batch, in, out, st);
+  if (p.prec == SDFT_C64) return launch_plan_inv_f32(p, batch, in, out, st);
+  return p.d_tw_df ? launch_plan_inv_df(p, batch, in, out, st) : launch_plan_inv_f64(p, batch, in, out, st);
 }
 
 }  // namespace sdft
@@ -150,8 +152,9 @@ sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft
                              sdft_plan* out) {
   if (!out) return SDFT_ERR_ARG;
   *out = nullptr;
-  if (flags & ~(SDFT_PLAN_HOST_ONLY | SDFT_PLAN_DEFER_DEVICE)) return SDFT_ERR_ARG;
+  if (flags & ~(SDFT_PLAN_HOST_ONLY | SDFT_PLAN_DEFER_DEVICE | SDFT_PLAN_FP64_DF)) return SDFT_ERR_ARG;
   if ((flags & SDFT_PLAN_HOST_ONLY) && (flags & SDFT_PLAN_DEFER_DEVICE)) return SDFT_ERR_ARG;
+  if ((flags & SDFT_PLAN_FP64_DF) && prec != SDFT_C128) return SDFT_ERR_ARG;
   sdft_plan_s* h = new (std::nothrow) sdft_plan_s();
   if (!h) return SDFT_ERR_NOMEM;
   sdft_status s;
@@ -201,7 +204,29 @@ sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft
     if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, 256);
     if (e == cudaSuccess && tw_bytes) e = cudaMalloc(&p.d_tw, tw_bytes);
     if (e == cudaSuccess && tw_bytes) e = cudaMemcpy(p.d_tw, host.data(), tw_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && tw_bytes && (flags & SDFT_PLAN_FP64_DF)) {
+      // the same entries split into hi = RN(x), lo = RN(x - hi) pairs, laid out
+      // (re_hi, im_hi, re_lo, im_lo): 16 bytes per entry, as complex128
+      std::vector<float> df;
+      try {
+        df.resize(4 * size_t(p.tw_elems));
+      } catch (const std::bad_alloc&) {
+        e = cudaErrorMemoryAllocation;
+      }
+      const double* tw64 = reinterpret_cast<const double*>(host.data());
+      for (size_t i = 0; e == cudaSuccess && i < size_t(p.tw_elems); ++i) {
+        const double re = tw64[2 * i], im = tw64[2 * i + 1];
+        const float rh = float(re), ih = float(im);
+        df[4 * i] = rh;
+        df[4 * i + 1] = ih;
+        df[4 * i + 2] = float(re - double(rh));
+        df[4 * i + 3] = float(im - double(ih));
+      }
+      if (e == cudaSuccess) e = cudaMalloc(&p.d_tw_df, tw_bytes);
+      if (e == cudaSuccess) e = cudaMemcpy(p.d_tw_df, df.data(), tw_bytes, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
+      if (p.d_tw_df) cudaFree(p.d_tw_df);
       if (p.d_tw) cudaFree(p.d_tw);
       if (p.d_status) cudaFree(p.d_status);
       delete h;
@@ -429,6 +454,7 @@ sdft_status sdft_plan_destroy(sdft_plan plan) {
   for (void* ev : plan->host_ev)
     if (ev) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
   if (plan->p.d_tw) cudaFree(plan->p.d_tw);
+  if (plan->p.d_tw_df) cudaFree(plan->p.d_tw_df);
   if (plan->p.d_status) cudaFree(plan->p.d_status);
   delete plan;
   return SDFT_OK;

@@ -22,6 +22,8 @@
 
 #include <cstdint>
 
+#include <type_traits>
+
 #include "ptx.cuh"
 #include "sdft.h"
 
@@ -34,6 +36,25 @@ template <> struct KT<float> {
 };
 template <> struct KT<double> {
   using C = double2;
+  static constexpr int ES = 16, CB = 3, TB = 11, NT = 128, SUB = 0;
+};
+
+// Double-float arithmetic for complex128 data: a value is an unevaluated sum
+// hi + lo of two FP32 numbers (48-bit significand, FP32 exponent range), so the
+// butterflies run on the FP32 pipes. `dfloat` is the real-type tag (a scale
+// factor, always a power of two) and `dfc` a complex value: hi = (re, im) high
+// parts, lo = (re, im) low parts. Tiles and tables keep 16 bytes per value, as
+// complex128 does.
+struct dfloat {
+  float v;
+  __host__ __device__ constexpr dfloat(double x = 0.0) : v(float(x)) {}
+};
+__host__ __device__ inline dfloat operator*(dfloat a, dfloat b) { return dfloat(double(a.v) * double(b.v)); }
+struct __align__(16) dfc {
+  float2 hi, lo;
+};
+template <> struct KT<dfloat> {
+  using C = dfc;
   static constexpr int ES = 16, CB = 3, TB = 11, NT = 128, SUB = 0;
 };
 
@@ -138,6 +159,177 @@ __device__ __forceinline__ void ibfly_scaled(double2& a, double2& b, double2 w, 
   b.y = fma(-w.y, dx, w.x * dy);
 }
 
+// ---- double-float butterflies ---------------------------------------------------
+// Knuth's TwoSum (s + e = a + b exactly), Dekker's FastTwoSum (|a| >= |b|) and the
+// FMA form of Dekker's TwoProduct; sums and products of hi + lo pairs renormalised
+// by FastTwoSum (the "sloppy" double-float addition, whose error is bounded by a
+// small multiple of 2^-48 (|x| + |y|), the bound a normwise FFT analysis uses).
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, e);
+}
+__device__ __forceinline__ float2 df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {   // (hi, lo) + (hi, lo)
+  const float2 s = df_two_sum(x.x, y.x);
+  return df_fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(x.y, y.y)));
+}
+__device__ __forceinline__ float2 df_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = __fmaf_rn(x.x, y.x, -p);
+  e = __fmaf_rn(x.x, y.y, e);
+  e = __fmaf_rn(x.y, y.x, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 df_re(const dfc& v) { return make_float2(v.hi.x, v.lo.x); }
+__device__ __forceinline__ float2 df_im(const dfc& v) { return make_float2(v.hi.y, v.lo.y); }
+__device__ __forceinline__ dfc df_make(float2 re, float2 im) {
+  dfc r;
+  r.hi = make_float2(re.x, im.x);
+  r.lo = make_float2(re.y, im.y);
+  return r;
+}
+__device__ __forceinline__ dfc df_scale(const dfc& v, float s) {   // s a power of two: exact
+  dfc r;
+  r.hi = make_float2(v.hi.x * s, v.hi.y * s);
+  r.lo = make_float2(v.lo.x * s, v.lo.y * s);
+  return r;
+}
+// Packed forms: the real and imaginary parts travel together as FP32x2 pairs
+// (hi = (re, im), lo = (re, im)), so one packed instruction serves both; the
+// same steps as above, lane by lane.
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ dfc dfc_add(const dfc& x, const dfc& y) {
+  const float2 s = __fadd2_rn(x.hi, y.hi);                  // TwoSum on the high parts
+  const float2 bb = p_sub(s, x.hi);
+  float2 e = __fadd2_rn(p_sub(x.hi, p_sub(s, bb)), p_sub(y.hi, bb));
+  e = __fadd2_rn(e, __fadd2_rn(x.lo, y.lo));
+  dfc r;                                                    // FastTwoSum renormalisation
+  r.hi = __fadd2_rn(s, e);
+  r.lo = p_sub(e, p_sub(r.hi, s));
+  return r;
+}
+__device__ __forceinline__ dfc dfc_flip(const dfc& x, float2 sgn) {   // lane signs (+-1): exact
+  dfc r;
+  r.hi = __fmul2_rn(x.hi, sgn);
+  r.lo = __fmul2_rn(x.lo, sgn);
+  return r;
+}
+// (xr, xr) * (y.re, y.im) for a double-float scalar xr = (xh, xl) and complex y
+__device__ __forceinline__ dfc dfc_scalar_mul(float xh, float xl, const dfc& y) {
+  const float2 xh2 = make_float2(xh, xh), xl2 = make_float2(xl, xl);
+  const float2 p = __fmul2_rn(xh2, y.hi);
+  float2 e = __ffma2_rn(xh2, y.hi, __fmul2_rn(p, make_float2(-1.f, -1.f)));   // TwoProduct error
+  e = __ffma2_rn(xh2, y.lo, e);
+  e = __ffma2_rn(xl2, y.hi, e);
+  dfc r;
+  r.hi = __fadd2_rn(p, e);
+  r.lo = p_sub(e, p_sub(r.hi, p));
+  return r;
+}
+__device__ __forceinline__ dfc dfc_swap(const dfc& y) {
+  dfc r;
+  r.hi = make_float2(y.hi.y, y.hi.x);
+  r.lo = make_float2(y.lo.y, y.lo.x);
+  return r;
+}
+// t = w b (complex); then (a, b) <- (a + t, a - t)
+__device__ __forceinline__ void df_bfly_core(dfc& a, dfc& b, const dfc& w) {
+  // w b = wr (br, bi) + wi (-bi, br)
+  const dfc A = dfc_scalar_mul(w.hi.x, w.lo.x, b);
+  const dfc B = dfc_flip(dfc_scalar_mul(w.hi.y, w.lo.y, dfc_swap(b)), make_float2(-1.f, 1.f));
+  const dfc t = dfc_add(A, B);
+  b = dfc_add(a, dfc_flip(t, make_float2(-1.f, -1.f)));
+  a = dfc_add(a, t);
+}
+__device__ __forceinline__ void bfly(dfc& a, dfc& b, const dfc w) { df_bfly_core(a, b, w); }
+__device__ __forceinline__ void bfly_scaled(dfc& a, dfc& b, const dfc w, const dfloat sc) {
+  a = df_scale(a, sc.v);
+  df_bfly_core(a, b, w);
+}
+// adjoint: (a, b) -> (ga (a + b), gb conj(w) (a - b)); conj(w) d = wr (dr, di) + wi (di, -dr)
+__device__ __forceinline__ void df_ibfly_core(dfc& a, dfc& b, const dfc& w, float ga, float gb) {
+  const dfc d = dfc_add(a, dfc_flip(b, make_float2(-1.f, -1.f)));
+  a = df_scale(dfc_add(a, b), ga);
+  const dfc A = dfc_scalar_mul(w.hi.x, w.lo.x, d);
+  const dfc B = dfc_flip(dfc_scalar_mul(w.hi.y, w.lo.y, dfc_swap(d)), make_float2(1.f, -1.f));
+  b = df_scale(dfc_add(A, B), gb);
+}
+__device__ __forceinline__ void ibfly(dfc& a, dfc& b, const dfc w) { df_ibfly_core(a, b, w, 1.f, 1.f); }
+__device__ __forceinline__ void ibfly_scaled(dfc& a, dfc& b, dfc w, const dfloat ga, const dfloat gb) {
+  df_ibfly_core(a, b, w, ga.v, gb.v);
+}
+
+// ---- double <-> double-float by bit operations --------------------------------------
+// The conversions stay off the FP64 pipe (a few integer operations, one integer
+// to FP32 conversion, two FP32 multiplies; the join adds in FP64 once).
+// Split: hi = x with its significand cut to 24 bits (exact), lo = RN(x - hi)
+// from the 29 dropped bits, an integer times 2^(e - 52). |x| < 2^-126 gives
+// 0 + 0; |x| >= 2^128, infinities and NaN give a signed infinity.
+__device__ __forceinline__ float2 df_split(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const uint32_t hw = uint32_t(b >> 32), lw = uint32_t(b);
+  const uint32_t sign = hw & 0x80000000u;
+  const uint32_t e = (hw >> 20) & 0x7ffu;                       // biased exponent of x
+  if (e < 897u) return make_float2(0.f, 0.f);
+  if (e > 1150u) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const uint32_t frac23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
+  const uint32_t pow_bits = (e - 896u) << 23;                    // 2^(e - 1023) as FP32
+  const float hi = __uint_as_float(sign | pow_bits | frac23);
+  const float rem = __uint2float_rn(lw & 0x1fffffffu);           // 29 bits, rounded to 24
+  const float lo = __fmul_rn(__fmul_rn(rem, 2.220446049250313e-16f), __uint_as_float(pow_bits));   // 2^-52
+  return make_float2(hi, sign ? -lo : lo);
+}
+// An FP32 value as FP64 (exact); zero and subnormals give 0, inf/NaN keep their kind.
+__device__ __forceinline__ double df_f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e8 = (u >> 23) & 0xffu;
+  const uint32_t sign = u & 0x80000000u;
+  if (e8 == 0u) return __hiloint2double(int(sign), 0);
+  const uint32_t e11 = (e8 == 0xffu) ? 0x7ffu : e8 + 896u;
+  return __hiloint2double(int(sign | (e11 << 20) | ((u & 0x7fffffu) >> 3)), int((u & 0x7u) << 29));
+}
+__device__ __forceinline__ double df_join(float hi, float lo) { return __dadd_rn(df_f2d(hi), df_f2d(lo)); }
+
+// ---- element and table access ------------------------------------------------------
+// Tile elements: as stored, except that a double-float pass reads the tile's
+// complex128 values when it is the level's first pass (RAW_IN: the tile came
+// from HBM) and writes complex128 when it is its last (RAW_OUT: the tile goes
+// back to HBM).
+template <class R, bool RAW>
+__device__ __forceinline__ typename KT<R>::C load_elem(const char* p) {
+  if constexpr (std::is_same<R, dfloat>::value && RAW) {
+    const double2 x = *reinterpret_cast<const double2*>(p);
+    const float2 re = df_split(x.x), im = df_split(x.y);
+    return df_make(re, im);
+  } else {
+    return *reinterpret_cast<const typename KT<R>::C*>(p);
+  }
+}
+template <class R, bool RAW>
+__device__ __forceinline__ void store_elem(char* p, const typename KT<R>::C& v) {
+  if constexpr (std::is_same<R, dfloat>::value && RAW) {
+    *reinterpret_cast<double2*>(p) = make_double2(df_join(v.hi.x, v.lo.x), df_join(v.hi.y, v.lo.y));
+  } else {
+    *reinterpret_cast<typename KT<R>::C*>(p) = v;
+  }
+}
+// A table entry through the read-only path.
+__device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg_c(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ dfc ldg_c(const dfc* p) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  dfc r;
+  r.hi = make_float2(t.x, t.y);
+  r.lo = make_float2(t.z, t.w);
+  return r;
+}
+
 // ---- pass schedule ------------------------------------------------------------------
 // Stage bits [PLO, PHI) of a tile run in passes. Pass p covers the 4-bit window
 // starting at the first stage bit not yet done (or the top window of the tile)
@@ -200,6 +392,15 @@ __device__ __forceinline__ double2 ld_shared_c<double>(uint32_t addr) {
   asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr) : "memory");
   return v;
 }
+template <>
+__device__ __forceinline__ dfc ld_shared_c<dfloat>(uint32_t addr) {
+  dfc v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.hi.x), "=f"(v.hi.y), "=f"(v.lo.x), "=f"(v.lo.y)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
 
 // Stage range [lo, hi) of the pass that reads its twiddles from memory
 // (neither kernel parameters nor registers); {0, 0} if there is none.
@@ -225,7 +426,7 @@ constexpr int mid_pass_hi(int TB, int PLO, int PHI) {
 // the absolute-indexed table region.
 // BAR = 1: the pass ends with named barrier 1 over the NT compute threads
 // instead of a CTA barrier (a kernel with a separate producer warp).
-template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SRC, int BAR = 0>
+template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SRC, int BAR = 0, bool FIRST = false>
 __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc,
                                           uint32_t wsm = 0) {
   using C = typename KT<R>::C;
@@ -246,7 +447,7 @@ __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w,
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const uint32_t E = uint32_t(e) << B;
-      v[e] = *reinterpret_cast<const C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)));
+      v[e] = load_elem<R, FIRST>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)));
     }
   }
 #pragma unroll
@@ -259,7 +460,7 @@ __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w,
       const int eh = e | (1 << q);
       C wt;
       if constexpr (SRC == kTwGlobal)
-        wt = __ldg(w + (1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B));
+        wt = ldg_c(w + (1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B));
       else if constexpr (SRC == kTwShared)
         wt = ld_shared_c<R>(wsm + ((1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B)) * KT<R>::ES);
       else
@@ -279,7 +480,7 @@ __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w,
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const uint32_t E = uint32_t(e) << B;
-      *reinterpret_cast<C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E))) = v[e];
+      store_elem<R, FENCE>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)), v[e]);
     }
   }
   if constexpr (FENCE) ptx::fence_proxy_async_smem();  // the tile leaves through TMA next
@@ -303,7 +504,7 @@ __device__ __forceinline__ void load_reg_twiddles(const typename KT<R>::C* __res
       for (int m1 = SLO; m1 < SHI; ++m1)
 #pragma unroll
         for (int v = 0; v < (1 << (m1 - B)); ++v)
-          wreg[ROFF + pass_ntw(B, SLO, m1) + v] = __ldg(base + (1u << m1) + (uint32_t(v) << B));
+          wreg[ROFF + pass_ntw(B, SLO, m1) + v] = ldg_c(base + (1u << m1) + (uint32_t(v) << B));
       load_reg_twiddles<R, PLO, PHI, P + 1, ROFF + pass_ntw(B, SLO, SHI)>(tw, tid, wreg);
     } else {
       load_reg_twiddles<R, PLO, PHI, P + 1, ROFF>(tw, tid, wreg);
@@ -349,16 +550,16 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
     constexpr int SRC = pass_src(TB, B);
     if constexpr (SRC == kTwParam) {
       if constexpr (P0SM)
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR>(buf, twg, tid, sc, wsm);
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, P == 0>(buf, twg, tid, sc, wsm);
       else
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR>(buf, w0, tid, sc);
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, P == 0>(buf, w0, tid, sc);
     } else if constexpr (SRC == kTwGlobal) {
       if constexpr (MIDSM)
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR>(buf, twg, tid, sc, wsm);
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, P == 0>(buf, twg, tid, sc, wsm);
       else
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR>(buf, twg, tid, sc);
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, P == 0>(buf, twg, tid, sc);
     } else {
-      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR>(buf, wreg + ROFF, tid, sc);
+      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, P == 0>(buf, wreg + ROFF, tid, sc);
     }
     if constexpr (P == 0) hook();
     constexpr int RNEXT = (SRC == kTwReg) ? ROFF + pass_ntw(B, SLO, SHI) : ROFF;
@@ -372,7 +573,7 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
 // pass holds the plan's last stage, whose table entries carry the factor N/k;
 // its second outputs are scaled by sc_top = k/N. FINSC: the pass holds stage 1,
 // the last one applied; both its outputs are scaled by sc_fin = 1/N.
-template <class R, int B, int SLO, int SHI, bool TOPSC, bool FINSC, bool FENCE, int SRC>
+template <class R, int B, int SLO, int SHI, bool TOPSC, bool FINSC, bool FENCE, int SRC, bool FIRST = false>
 __device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc_top,
                                               R sc_fin, uint32_t wsm = 0) {
   using C = typename KT<R>::C;
@@ -393,7 +594,7 @@ __device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const uint32_t E = uint32_t(e) << B;
-      v[e] = *reinterpret_cast<const C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)));
+      v[e] = load_elem<R, FIRST>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)));
     }
   }
 #pragma unroll
@@ -407,7 +608,7 @@ __device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C
       const int eh = e | (1 << q);
       C wt;
       if constexpr (SRC == kTwGlobal)
-        wt = __ldg(w + (1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B));
+        wt = ldg_c(w + (1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B));
       else if constexpr (SRC == kTwShared)
         wt = ld_shared_c<R>(wsm + ((1u << m1) + (F & LOWM) + (uint32_t(e & ((1 << q) - 1)) << B)) * KT<R>::ES);
       else
@@ -427,7 +628,7 @@ __device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const uint32_t E = uint32_t(e) << B;
-      *reinterpret_cast<C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E))) = v[e];
+      store_elem<R, FENCE>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)), v[e]);
     }
   }
   if constexpr (FENCE) ptx::fence_proxy_async_smem();
@@ -457,17 +658,18 @@ __device__ __forceinline__ void run_passes_inv(char* buf, const typename KT<R>::
   if constexpr (P >= 0) {
     constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
     constexpr bool TOPSC = LAST && P == NP - 1, FINSC = PLO == 0 && P == 0, FENCE = P == 0;
+    constexpr bool FIRST = P == NP - 1;
     constexpr int SRC = pass_src(TB, B);
     if constexpr (SRC == kTwParam) {
-      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC>(buf, w0, tid, sc_top, sc_fin);
+      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST>(buf, w0, tid, sc_top, sc_fin);
     } else if constexpr (SRC == kTwGlobal) {
       if constexpr (MIDSM)
-        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, kTwShared>(buf, twg, tid, sc_top, sc_fin, wsm);
+        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, kTwShared, FIRST>(buf, twg, tid, sc_top, sc_fin, wsm);
       else
-        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC>(buf, twg, tid, sc_top, sc_fin);
+        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST>(buf, twg, tid, sc_top, sc_fin);
     } else {
-      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC>(buf, wreg + reg_off(TB, PLO, PHI, P), tid, sc_top,
-                                                              sc_fin);
+      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST>(buf, wreg + reg_off(TB, PLO, PHI, P), tid,
+                                                                     sc_top, sc_fin);
     }
     if constexpr (P == NP - 1) hook();
     run_passes_inv<R, PLO, PHI, LAST, MIDSM, P - 1, Hook>(buf, wreg, w0, twg, tid, sc_top, sc_fin, wsm, hook);

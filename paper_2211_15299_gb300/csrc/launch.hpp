@@ -30,6 +30,10 @@ uint64_t wait_timeout_ns();
 // Run every level of `plan` on `batch` packed instances (complex64 / complex128).
 sdft_status launch_plan_f32(const Plan& plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
 sdft_status launch_plan_f64(const Plan& plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
+// complex128 plans with SDFT_PLAN_FP64_DF: double-float butterflies where the
+// level kernels run (small instances take the FP64 paths).
+sdft_status launch_plan_df(const Plan& plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
+sdft_status launch_plan_inv_df(const Plan& plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
 // Synthesis: samples from coefficients (the adjoint network scaled by 1/N).
 sdft_status launch_plan_inv_f32(const Plan& plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
 sdft_status launch_plan_inv_f64(const Plan& plan, uint64_t batch, const void* in, void* out, cudaStream_t st);

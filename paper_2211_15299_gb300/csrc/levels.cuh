@@ -71,6 +71,21 @@ sdft_status dispatch_small(int s, uint64_t batch, const void* in, void* out, con
   }
 }
 
+// A table entry built on the host (kernel parameters), and the device table
+// the level kernels of a real type read.
+template <class R> inline typename KT<R>::C host_c(double re, double im);
+template <> inline float2 host_c<float>(double re, double im) { return make_float2(float(re), float(im)); }
+template <> inline double2 host_c<double>(double re, double im) { return make_double2(re, im); }
+template <> inline dfc host_c<dfloat>(double re, double im) {
+  dfc r;
+  r.hi = make_float2(float(re), float(im));
+  r.lo = make_float2(float(re - double(r.hi.x)), float(im - double(r.hi.y)));
+  return r;
+}
+template <class R> inline const void* level_table(const Plan& p) {
+  return std::is_same<R, dfloat>::value ? p.d_tw_df : p.d_tw;
+}
+
 // Tensor maps and kernel arguments of level 0 (stage bits [0, min(s, TB)) on
 // contiguous tiles of 2^TB elements) over the packed buffers (src, dst).
 template <class R>
@@ -90,14 +105,14 @@ sdft_status level0_setup(const Plan& p, uint64_t batch, const void* src, void* d
   if (s == SDFT_OK) s = encode_map(&md, dst, dims, strides, box);
   if (s != SDFT_OK) return s;
   a = LevelArgs<R>{};
-  for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
+  for (int i = 0; i < 15; ++i) a.tw0[i] = host_c<R>(p.tw0[2 * i], p.tw0[2 * i + 1]);
   a.n_tiles = n_tiles;
   a.nB = n_tiles;
   a.a_step1 = 0;
   a.b_step1 = int32_t(rows_per_tile);
   a.b_step3 = 0;
   a.tw_first = 0;
-  a.tw = static_cast<const C*>(p.d_tw) + L.tw_off;
+  a.tw = static_cast<const C*>(level_table<R>(p)) + L.tw_off;
   a.tw_len = L.tw_len;
   a.tw_stride = 0;
   a.scale = std::ldexp(1.0, int(p.M) - int(p.s));
@@ -125,14 +140,14 @@ sdft_status later_setup(const Plan& p, uint64_t batch, size_t j, const void* src
   if (s == SDFT_OK) s = encode_map(&md, dst, dims, strides, box);
   if (s != SDFT_OK) return s;
   a = LevelArgs<R>{};
-  for (int i = 0; i < 15; ++i) a.tw0[i] = C{R(p.tw0[2 * i]), R(p.tw0[2 * i + 1])};
+  for (int i = 0; i < 15; ++i) a.tw0[i] = host_c<R>(p.tw0[2 * i], p.tw0[2 * i + 1]);
   a.n_tiles = L.n_gb * Z;
   a.nB = Z;
   a.a_step1 = int32_t(1u << L.lg);
   a.b_step1 = 0;
   a.b_step3 = 1;
   a.tw_first = 1u << L.plo;
-  a.tw = static_cast<const C*>(p.d_tw) + L.tw_off;
+  a.tw = static_cast<const C*>(level_table<R>(p)) + L.tw_off;
   a.tw_len = L.tw_len;
   a.tw_stride = L.tw_len;
   a.scale = std::ldexp(1.0, int(p.M) - int(p.s));
@@ -169,13 +184,22 @@ sdft_status dispatch_warp(int s, uint64_t batch, const void* in, void* out, cons
   }
 }
 
+// Small batches of 2^5 <= k <= 2^10 take the warp path.
+inline bool warp_path(const Plan& p, uint64_t batch) {
+  return p.levels.size() == 1 && p.s >= 5 && p.s <= 10 && batch * p.k <= kWarpMaxElems;
+}
+
 template <class R>
 sdft_status launch_plan(const Plan& p, uint64_t batch, const void* in, void* out, cudaStream_t st) {
   const double scale = std::ldexp(1.0, int(p.M) - int(p.s));
-  if (p.levels.empty()) return dispatch_small<R>(int(p.s), batch, in, out, p.d_tw, scale, st);
-  if (p.levels.size() == 1 && p.s >= 5 && p.s <= 10 && batch * p.k <= kWarpMaxElems)
-    return dispatch_warp<R>(int(p.s), batch, in, out,
-                            static_cast<const typename KT<R>::C*>(p.d_tw) + p.levels[0].tw_off, scale, st);
+  if constexpr (std::is_same<R, dfloat>::value) {
+    if (p.levels.empty()) return SDFT_ERR_UNSUPPORTED;     // the caller runs these in FP64
+  } else {
+    if (p.levels.empty()) return dispatch_small<R>(int(p.s), batch, in, out, p.d_tw, scale, st);
+    if (warp_path(p, batch))
+      return dispatch_warp<R>(int(p.s), batch, in, out,
+                              static_cast<const typename KT<R>::C*>(p.d_tw) + p.levels[0].tw_off, scale, st);
+  }
   // Level 0 on contiguous tiles.
   {
     CUtensorMap ms, md;
@@ -224,7 +248,11 @@ template <class R>
 sdft_status launch_plan_inv(const Plan& p, uint64_t batch, const void* in, void* out, cudaStream_t st) {
   const double scale = std::ldexp(1.0, int(p.M) - int(p.s));
   const double inv_n = std::ldexp(1.0, -int(p.M));
-  if (p.levels.empty()) return dispatch_small_inv<R>(int(p.s), batch, in, out, p.d_tw, 1.0 / scale, inv_n, st);
+  if constexpr (std::is_same<R, dfloat>::value) {
+    if (p.levels.empty()) return SDFT_ERR_UNSUPPORTED;     // the caller runs these in FP64
+  } else {
+    if (p.levels.empty()) return dispatch_small_inv<R>(int(p.s), batch, in, out, p.d_tw, 1.0 / scale, inv_n, st);
+  }
   // Later levels first (last one first), the first reading `in`, then level 0.
   const void* src_base = in;
   for (size_t j = p.levels.size() - 1; j >= 1; --j) {

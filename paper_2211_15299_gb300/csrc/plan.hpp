@@ -56,6 +56,7 @@ struct Plan {
   uint64_t tw_elems = 0;          // complex entries in the device table buffer
   int device = -1;
   void* d_tw = nullptr;           // device twiddles (float2 or double2)
+  void* d_tw_df = nullptr;        // the same table as double-float pairs (SDFT_PLAN_FP64_DF)
   int* d_status = nullptr;        // device status word
   uint64_t device_bytes = 0;
   double tw0[32] = {0};           // level-0 table entries 1..15 (rounded to prec), for kernel params

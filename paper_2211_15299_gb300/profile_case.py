@@ -21,6 +21,7 @@ def main() -> int:
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--reps", type=int, default=4)
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--fp64-df", action="store_true", help="complex128 in double-float arithmetic")
     ap.add_argument("--strategy", default="", choices=["", "levels", "queue"],
                     help="multi-level plans: per-level launches or one work-queue launch")
     ap.add_argument("--uneven", type=int, default=0,
@@ -39,7 +40,7 @@ def main() -> int:
     from paper_2211_15299_gb300 import Plan
 
     inst, _ = W.workload_shared(M=args.log2n, s=args.log2k, batch=1, coeffs=False)
-    plan = Plan(args.log2n, inst.J, args.prec)
+    plan = Plan(args.log2n, inst.J, args.prec, fp64_df=args.fp64_df)
     if args.strategy:
         plan.set_strategy(args.strategy)
     dt = torch.complex64 if args.prec == "c64" else torch.complex128

@@ -64,6 +64,10 @@ def test_plan_errors():
         assert ei.value.name == want, (M, J)
     with pytest.raises(SdftError):
         Plan(4, [], host_only=True)
+    with pytest.raises(SdftError) as ei:              # double-float mode is for complex128 plans
+        Plan(4, [0, 1, 2, 3], "c64", host_only=True, fp64_df=True)
+    assert ei.value.name == "SDFT_ERR_ARG"
+    assert Plan(4, [0, 1, 2, 3], "c128", host_only=True, fp64_df=True).k == 4
 
 
 def test_homogeneity_decision_matches_oracle_on_near_misses():
