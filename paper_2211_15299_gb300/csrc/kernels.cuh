@@ -297,10 +297,11 @@ __device__ __forceinline__ double df_f2d(float f) {
 __device__ __forceinline__ double df_join(float hi, float lo) { return __dadd_rn(df_f2d(hi), df_f2d(lo)); }
 
 // ---- element and table access ------------------------------------------------------
-// Tile elements: as stored, except that a double-float pass reads the tile's
-// complex128 values when it is the level's first pass (RAW_IN: the tile came
-// from HBM) and writes complex128 when it is its last (RAW_OUT: the tile goes
-// back to HBM).
+// Tile elements: as stored, except that a double-float pass reads complex128
+// values (RAW) when it is the first pass of the plan's first level (the samples
+// as the caller gave them) and writes complex128 from the last pass of its last
+// level; between levels the split values go through HBM as they are (16 bytes
+// per value, as complex128).
 template <class R, bool RAW>
 __device__ __forceinline__ typename KT<R>::C load_elem(const char* p) {
   if constexpr (std::is_same<R, dfloat>::value && RAW) {
@@ -426,7 +427,8 @@ constexpr int mid_pass_hi(int TB, int PLO, int PHI) {
 // the absolute-indexed table region.
 // BAR = 1: the pass ends with named barrier 1 over the NT compute threads
 // instead of a CTA barrier (a kernel with a separate producer warp).
-template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SRC, int BAR = 0, bool FIRST = false>
+template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SRC, int BAR = 0, bool FIRST = false,
+          bool RAWOUT = false>
 __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc,
                                           uint32_t wsm = 0) {
   using C = typename KT<R>::C;
@@ -480,7 +482,7 @@ __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w,
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const uint32_t E = uint32_t(e) << B;
-      store_elem<R, FENCE>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)), v[e]);
+      store_elem<R, RAWOUT>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)), v[e]);
     }
   }
   if constexpr (FENCE) ptx::fence_proxy_async_smem();  // the tile leaves through TMA next
@@ -547,19 +549,22 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
   if constexpr (P < n_passes(TB, PLO, PHI)) {
     constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
     constexpr bool FINAL = (SHI == PHI);
+    // double-float: values arrive as complex128 only in the plan's first level and
+    // leave as complex128 only from its last; between levels they stay split
+    constexpr bool RAWIN = P == 0 && PLO == 0, RAWOUT = FINAL && LAST;
     constexpr int SRC = pass_src(TB, B);
     if constexpr (SRC == kTwParam) {
       if constexpr (P0SM)
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, P == 0>(buf, twg, tid, sc, wsm);
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc, wsm);
       else
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, P == 0>(buf, w0, tid, sc);
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, w0, tid, sc);
     } else if constexpr (SRC == kTwGlobal) {
       if constexpr (MIDSM)
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, P == 0>(buf, twg, tid, sc, wsm);
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc, wsm);
       else
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, P == 0>(buf, twg, tid, sc);
+        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc);
     } else {
-      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, P == 0>(buf, wreg + ROFF, tid, sc);
+      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, wreg + ROFF, tid, sc);
     }
     if constexpr (P == 0) hook();
     constexpr int RNEXT = (SRC == kTwReg) ? ROFF + pass_ntw(B, SLO, SHI) : ROFF;
@@ -573,7 +578,8 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
 // pass holds the plan's last stage, whose table entries carry the factor N/k;
 // its second outputs are scaled by sc_top = k/N. FINSC: the pass holds stage 1,
 // the last one applied; both its outputs are scaled by sc_fin = 1/N.
-template <class R, int B, int SLO, int SHI, bool TOPSC, bool FINSC, bool FENCE, int SRC, bool FIRST = false>
+template <class R, int B, int SLO, int SHI, bool TOPSC, bool FINSC, bool FENCE, int SRC, bool FIRST = false,
+          bool RAWOUT = false>
 __device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc_top,
                                               R sc_fin, uint32_t wsm = 0) {
   using C = typename KT<R>::C;
@@ -628,7 +634,7 @@ __device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const uint32_t E = uint32_t(e) << B;
-      store_elem<R, FENCE>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)), v[e]);
+      store_elem<R, RAWOUT>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)), v[e]);
     }
   }
   if constexpr (FENCE) ptx::fence_proxy_async_smem();
@@ -658,18 +664,21 @@ __device__ __forceinline__ void run_passes_inv(char* buf, const typename KT<R>::
   if constexpr (P >= 0) {
     constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
     constexpr bool TOPSC = LAST && P == NP - 1, FINSC = PLO == 0 && P == 0, FENCE = P == 0;
-    constexpr bool FIRST = P == NP - 1;
+    // double-float: complex128 in at the first level applied (the plan's last),
+    // out at the last applied (level 0); split values between levels
+    constexpr bool FIRST = P == NP - 1 && LAST, RAWOUT = P == 0 && PLO == 0;
     constexpr int SRC = pass_src(TB, B);
     if constexpr (SRC == kTwParam) {
-      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST>(buf, w0, tid, sc_top, sc_fin);
+      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST, RAWOUT>(buf, w0, tid, sc_top, sc_fin);
     } else if constexpr (SRC == kTwGlobal) {
       if constexpr (MIDSM)
-        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, kTwShared, FIRST>(buf, twg, tid, sc_top, sc_fin, wsm);
+        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, kTwShared, FIRST, RAWOUT>(buf, twg, tid, sc_top, sc_fin,
+                                                                                 wsm);
       else
-        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST>(buf, twg, tid, sc_top, sc_fin);
+        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST, RAWOUT>(buf, twg, tid, sc_top, sc_fin);
     } else {
-      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST>(buf, wreg + reg_off(TB, PLO, PHI, P), tid,
-                                                                     sc_top, sc_fin);
+      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST, RAWOUT>(buf, wreg + reg_off(TB, PLO, PHI, P),
+                                                                             tid, sc_top, sc_fin);
     }
     if constexpr (P == NP - 1) hook();
     run_passes_inv<R, PLO, PHI, LAST, MIDSM, P - 1, Hook>(buf, wreg, w0, twg, tid, sc_top, sc_fin, wsm, hook);
