@@ -66,12 +66,14 @@ typedef enum { SDFT_C64 = 0, SDFT_C128 = 1 } sdft_prec;
 
 /* Plan flags. */
 #define SDFT_PLAN_HOST_ONLY 0x1u    /* build the host tables only; no device upload */
-#define SDFT_PLAN_FP64_DF 0x8u      /* complex128 plans: strided transforms and synthesis of k > 2^10
-                                       run their butterflies in double-float arithmetic (pairs of
+#define SDFT_PLAN_FP64_DF 0x8u      /* complex128 plans: strided transforms and synthesis run
+                                       their level kernels in double-float arithmetic (pairs of
                                        FP32 values, 48-bit significand, FP32 exponent range) on
-                                       the FP32 pipes instead of the FP64 pipe; data stay
-                                       complex128 in memory; relative L2 error about 1e-14 for
-                                       values of magnitude 1e-30 .. 1e30 */
+                                       the FP32 pipes instead of the FP64 pipe (small batches of
+                                       k <= 2^10 and k <= 16 stay FP64); the caller's buffers stay
+                                       complex128; relative L2 error about 1e-14 for values of
+                                       magnitude 1e-30 .. 1e30. Batches and servers run such
+                                       plans in FP64. */
 #define SDFT_PLAN_DEFER_DEVICE 0x2u /* build the device tables in host memory but do not upload:
                                        the plan can only be used through a server
                                        (sdft_server_submit), which uploads them into its arena
