@@ -122,3 +122,38 @@ def test_warp_path_and_tile_path_agree_bitwise(s, prec):
     assert torch.equal(y_one, y_tile[0])
     tol = 1e-5 if prec == 0 else 1e-12
     assert rel_l2(y_warp.cpu().numpy().astype(np.complex128), C[:small]) < tol
+
+
+def test_largest_k():
+    """k = 2^28 (the largest the library accepts), complex64, one instance: three
+    levels of butterflies. Synthesis then transform returns the coefficients;
+    Parseval holds; two coefficients match the oracle's closed form."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan
+    M, s = 40, 28
+    rng = np.random.default_rng(6600)
+    piv = np.sort(rng.choice(np.arange(M), size=s, replace=False))
+    J = W.homogeneous_support(M, piv, rng)
+    plan = Plan(M, J, 0)
+    assert len(plan.pivots) == s
+    g = torch.Generator(device="cuda")
+    g.manual_seed(66)
+    C = torch.randn(1 << s, dtype=torch.complex64, device="cuda", generator=g)
+    f = plan.synthesize(C)
+    y = plan.execute_strided(f)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    c128 = C.to(torch.complex128)
+    assert float(torch.linalg.vector_norm(y.to(torch.complex128) - c128) / torch.linalg.vector_norm(c128)) < 1e-5
+    fn = float(torch.linalg.vector_norm(f.to(torch.complex128)))
+    yn = float(torch.linalg.vector_norm(y.to(torch.complex128)))
+    assert abs(yn - fn * (1 << M) / np.sqrt(1 << s)) / yn < 1e-5
+    del C
+    I = O.sample_set(M, piv)
+    Jc = O.canonical_support_by_key(J, piv)
+    f_h = f.cpu().numpy().astype(np.complex128)
+    y_h = y.cpu().numpy()
+    idx = rng.choice(1 << s, size=2, replace=False)
+    spot = O.coefficients_at(M, Jc[idx], I, f_h)
+    scale = np.linalg.norm(y_h.astype(np.complex128)) / np.sqrt(1 << s)
+    assert np.abs(y_h[idx] - spot).max() / scale < 1e-4
