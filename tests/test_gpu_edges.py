@@ -149,11 +149,13 @@ def test_largest_k():
     yn = float(torch.linalg.vector_norm(y.to(torch.complex128)))
     assert abs(yn - fn * (1 << M) / np.sqrt(1 << s)) / yn < 1e-5
     del C
+    # two support elements: canonical position t = sum_q bit_{r_q}(j) 2^q, value by
+    # the closed form over the oracle's sample set
     I = O.sample_set(M, piv)
-    Jc = O.canonical_support_by_key(J, piv)
     f_h = f.cpu().numpy().astype(np.complex128)
     y_h = y.cpu().numpy()
-    idx = rng.choice(1 << s, size=2, replace=False)
-    spot = O.coefficients_at(M, Jc[idx], I, f_h)
+    js = [int(J[i]) for i in rng.choice(J.size, size=2, replace=False)]
+    ts = [sum(((j >> int(r)) & 1) << q for q, r in enumerate(piv)) for j in js]
+    spot = O.coefficients_at(M, np.asarray(js, dtype=np.uint64), I, f_h)
     scale = np.linalg.norm(y_h.astype(np.complex128)) / np.sqrt(1 << s)
-    assert np.abs(y_h[idx] - spot).max() / scale < 1e-4
+    assert np.abs(y_h[ts] - spot).max() / scale < 1e-4
