@@ -8,10 +8,16 @@ Legs:
   * value        device-timed coeffs/s of the batched complex64 path (CUDA
                  events around each step on the launching stream, L2 flushed
                  between steps, untimed)
-  * e2e          the same through the public API with pinned host buffers,
-                 H2D of the samples and D2H of the coefficients inside the timing
-  * fp64         the plain per-instance complex128 path (one call per instance)
-                 and the batched complex128 path, device-timed
+  * e2e          the same through the public API with pinned host buffers
+                 (one sdft_execute_strided_host call: H2D of the samples, the
+                 transform and D2H of the coefficients, overlapped in chunks,
+                 inside the timing)
+  * fp64         the plain per-instance complex128 path (one call per instance),
+                 the batched complex128 path on the FP64 pipe and in
+                 double-float arithmetic, device-timed
+  * extras       (N = 1) synthesis, a cuFFT context figure, the single-instance
+                 latency, the uneven batch, the large-k plans, Shift-and-Sample
+                 and the serving engine
   * roofline     algorithmic bytes / kernel time against measured HBM bandwidth
   * cpu_baseline the FP64 oracle on the host cores: its plain-C Algorithm 1
                  (OpenMP) on the whole batch, its dense k x k solve on a
