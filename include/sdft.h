@@ -166,6 +166,29 @@ sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_s
 sdft_status sdft_execute_strided_host(sdft_plan plan, uint64_t batch, const void* h_samples, void* h_coeffs,
                                       void* d_samples, void* d_coeffs, uint64_t chunk, void* stream);
 
+/*
+ * sdft_execute_batched - n instances, instance i with its own plan plans[i]
+ * (repeats allowed, one precision, all on the current device), packed at the
+ * caller's offsets: instance i's samples are d_samples[d_offsets[i] ..
+ * d_offsets[i+1]) (sample order, d_offsets[i+1] - d_offsets[i] = k of plans[i])
+ * and its coefficients go to the same range of d_coeffs. d_offsets is a device
+ * array of n + 1 value offsets (read on the device, so the call is
+ * graph-capturable). It runs the uneven-batch work queue (sdft_batch_*) between
+ * a gather into the batch's own packing and a scatter back; the first call for a
+ * given list of plans builds that batch and its staging buffers (2 x total
+ * values) and caches them (allocates and may synchronise the device: make that
+ * call before capturing a graph); calls with the same list must not overlap on
+ * the GPU. sdft_batch_execute on the batch's own layout saves the two copies.
+ * Offsets that do not match the plans' k are reported as 0x104 in the status
+ * word of plans[0] (sdft_plan_device_status) and those instances are skipped;
+ * offsets must lie inside the caller's buffers. Buffers 16-byte aligned,
+ * identical or disjoint. Errors: SDFT_ERR_ARG, SDFT_ERR_NO_DEVICE,
+ * SDFT_ERR_PRECISION, SDFT_ERR_NOMEM, SDFT_ERR_CUDA, and those of
+ * sdft_batch_create. The paper computes one instance at a time (Algorithm 1).
+ */
+sdft_status sdft_execute_batched(const sdft_plan* plans, uint64_t n, const void* d_samples,
+                                 const uint64_t* d_offsets, void* d_coeffs, void* stream);
+
 /* The same for synthesis (sdft_synthesize_strided): h_coeffs in, h_samples out,
  * through the device buffers d_coeffs and d_samples. */
 sdft_status sdft_synthesize_strided_host(sdft_plan plan, uint64_t batch, const void* h_coeffs, void* h_samples,
@@ -215,7 +238,7 @@ sdft_status sdft_plan_autotune(sdft_plan plan, uint64_t batch, const void* d_sam
  * self-check code above 0xff (0x101: dynamic shared memory smaller than the
  * kernel's layout; 0x102: tensor-map parameter not 64-byte aligned; 0x103:
  * twiddle table, or a batch's item list, not 16-byte aligned; the kernel did
- * no work). Synchronises the
+ * no work; 0x104: sdft_execute_batched offsets that do not match the plans). Synchronises the
  * device; clears the word when `clear` is non-zero. */
 sdft_status sdft_plan_device_status(sdft_plan plan, int clear);
 

@@ -11,6 +11,6 @@ from __future__ import annotations
 
 from . import _native
 from ._native import *  # noqa: F401,F403  (C-ABI names)
-from .api import Plan, Batch, Server, Sas  # noqa: F401
+from .api import Plan, Batch, Server, Sas, execute_batched  # noqa: F401
 
-__all__ = ["Plan", "Batch", "Server", "Sas"] + [n for n in _native.SIGNATURES]
+__all__ = ["Plan", "Batch", "Server", "Sas", "execute_batched"] + [n for n in _native.SIGNATURES]

@@ -62,6 +62,7 @@ SIGNATURES = {
     "sdft_execute": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "sdft_execute_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "sdft_execute_strided_host": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
+    "sdft_execute_batched": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp]),
     "sdft_synthesize_strided_host": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
     "sdft_synthesize": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "sdft_synthesize_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
@@ -209,6 +210,13 @@ def sdft_execute_strided_host(plan: int, batch: int, h_samples, h_coeffs, d_samp
                               stream=None) -> None:
     _check(_lib.sdft_execute_strided_host(plan, int(batch), _ptr(h_samples), _ptr(h_coeffs), _ptr(d_samples),
                                           _ptr(d_coeffs), int(chunk), _stream(stream)), "sdft_execute_strided_host")
+
+
+def sdft_execute_batched(plans, d_samples, d_offsets, d_coeffs, stream=None) -> None:
+    """plans: sequence of plan handles; d_offsets: device array of n + 1 uint64 offsets."""
+    arr = (c_vp * len(plans))(*[int(p) for p in plans])
+    _check(_lib.sdft_execute_batched(arr, len(plans), _ptr(d_samples), _ptr(d_offsets), _ptr(d_coeffs),
+                                     _stream(stream)), "sdft_execute_batched")
 
 
 def sdft_synthesize_strided_host(plan: int, batch: int, h_coeffs, h_samples, d_coeffs, d_samples, chunk: int = 0,

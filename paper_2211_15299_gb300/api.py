@@ -185,6 +185,24 @@ class Plan:
             pass
 
 
+def execute_batched(plans: Sequence["Plan"], samples, offsets, coeffs=None, stream=None):
+    """Instances at the caller's offsets (sdft_execute_batched): plans[i] transforms
+    samples[offsets[i]:offsets[i+1]] into the same range of coeffs. `offsets` is a
+    device int64 tensor of len(plans) + 1 entries."""
+    torch = _torch()
+    dt = plans[0].dtype
+    if not isinstance(offsets, torch.Tensor) or not offsets.is_cuda or offsets.dtype != torch.int64:
+        raise TypeError("offsets must be a CUDA int64 tensor")
+    if offsets.numel() != len(plans) + 1 or not offsets.is_contiguous():
+        raise ValueError("offsets must hold len(plans) + 1 values")
+    _check_tensor(samples, dt, samples.numel(), "samples")
+    if coeffs is None:
+        coeffs = torch.empty_like(samples)
+    _check_tensor(coeffs, dt, samples.numel(), "coeffs")
+    N.sdft_execute_batched([p.handle for p in plans], samples, offsets, coeffs, _current_stream(stream))
+    return coeffs
+
+
 class Batch:
     """Many instances with their own plans, run by one persistent kernel."""
 

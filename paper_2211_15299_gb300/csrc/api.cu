@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -168,6 +169,10 @@ sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft
     return s;
   }
   Plan& p = h->p;
+  {
+    static std::atomic<uint64_t> next_serial{1};
+    p.serial = next_serial.fetch_add(1);
+  }
   if (!(flags & SDFT_PLAN_HOST_ONLY)) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);

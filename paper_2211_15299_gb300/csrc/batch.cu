@@ -559,6 +559,157 @@ sdft_status run_strided_queue(sdft_plan_s* plan, uint64_t batch, const void* in,
   return run_batch(*b, in, out, st);
 }
 
+// ---- sdft_execute_batched: instances at the caller's offsets ----------------------
+// The batch path wants its own packing (instances by decreasing k, so tiles never
+// straddle instances); sdft_execute_batched takes any packing: a cached batch of
+// the same plans runs between a gather into its layout and a scatter back, both
+// one kernel over chunks of at most kRepackChunk values. The caller's offsets
+// stay on the device (graph-capturable); a kernel checks each against its plan.
+constexpr uint64_t kRepackChunk = 8192;
+constexpr size_t kBatchedCache = 8;
+
+struct RepackItem {
+  uint32_t inst;       // instance, caller order
+  uint32_t pad;
+  uint64_t local;      // first value within the instance
+  uint64_t count;      // values
+};
+
+template <class C>
+__global__ void __launch_bounds__(256) k_repack(const C* __restrict__ src, C* __restrict__ dst,
+                                                const uint64_t* __restrict__ user_off,
+                                                const uint64_t* __restrict__ kk, const uint64_t* __restrict__ boff,
+                                                const RepackItem* __restrict__ items, uint64_t n_items, int* status,
+                                                int to_batch) {
+  for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const RepackItem c = items[it];
+    const uint64_t uo = user_off[c.inst], un = user_off[c.inst + 1];
+    if (un - uo != kk[c.inst]) {       // the caller's offsets do not fit the plans
+      if (threadIdx.x == 0) atomicCAS(status, 0, kBadOffsets);
+      continue;
+    }
+    const uint64_t s0 = (to_batch ? uo : boff[c.inst]) + c.local;
+    const uint64_t d0 = (to_batch ? boff[c.inst] : uo) + c.local;
+    for (uint64_t e = threadIdx.x; e < c.count; e += blockDim.x) dst[d0 + e] = src[s0 + e];
+  }
+}
+
+struct BatchedEntry {
+  std::vector<uint64_t> serials;
+  Batch* b = nullptr;
+  void* d_stage = nullptr;             // 2 x total values: samples, then coefficients
+  uint64_t* d_k = nullptr;             // k per instance (caller order)
+  uint64_t* d_boff = nullptr;          // the batch's offset per instance (caller order)
+  RepackItem* d_items = nullptr;
+  uint64_t n_items = 0;
+};
+
+// Bytes of one staging half: the batch's values rounded up to 256 bytes.
+static uint64_t stage_bytes(uint64_t total, size_t es) { return (std::max<uint64_t>(total, 1) * es + 255) & ~255ull; }
+
+static void free_batched(BatchedEntry& E) {
+  if (E.b) {
+    free_batch(*E.b);
+    delete E.b;
+  }
+  if (E.d_stage) cudaFree(E.d_stage);
+  if (E.d_k) cudaFree(E.d_k);
+  if (E.d_boff) cudaFree(E.d_boff);
+  if (E.d_items) cudaFree(E.d_items);
+  E = BatchedEntry{};
+}
+
+static std::mutex g_batched_mu;
+static std::vector<BatchedEntry> g_batched;   // most recent last
+
+static sdft_status batched_entry(const sdft_plan* plans, uint64_t n, BatchedEntry** out) {
+  std::vector<uint64_t> key(n);
+  for (uint64_t i = 0; i < n; ++i) key[i] = plans[i]->p.serial;
+  for (auto& E : g_batched)
+    if (E.serials == key) {
+      *out = &E;
+      return SDFT_OK;
+    }
+  BatchedEntry E;
+  E.serials = key;
+  E.b = new (std::nothrow) Batch();
+  if (!E.b) return SDFT_ERR_NOMEM;
+  E.b->device = plans[0]->p.device;
+  E.b->plans.assign(plans, plans + n);
+  sdft_status s = build_batch(*E.b, plans, n);
+  if (s != SDFT_OK) {
+    free_batched(E);
+    return s;
+  }
+  E.b->d_status_shared = plans[0]->p.d_status;    // report into the first plan's status word
+  std::vector<uint64_t> kk(n), boff(n);
+  std::vector<RepackItem> items;
+  for (uint64_t i = 0; i < n; ++i) {
+    kk[i] = plans[i]->p.k;
+    boff[i] = E.b->offsets[i];
+    for (uint64_t l = 0; l < kk[i]; l += kRepackChunk)
+      items.push_back(RepackItem{uint32_t(i), 0, l, std::min(kRepackChunk, kk[i] - l)});
+  }
+  E.n_items = items.size();
+  const size_t es = size_t(elem_bytes(plans[0]->p.prec));
+  cudaError_t e = cudaMalloc(&E.d_stage, 2 * stage_bytes(E.b->total, es));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&E.d_k), sizeof(uint64_t) * n);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&E.d_boff), sizeof(uint64_t) * n);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&E.d_items), sizeof(RepackItem) * items.size());
+  if (e == cudaSuccess) e = cudaMemcpy(E.d_k, kk.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(E.d_boff, boff.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(E.d_items, items.data(), sizeof(RepackItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_batched(E);
+    return e == cudaErrorMemoryAllocation ? SDFT_ERR_NOMEM : cuda_fail(e);
+  }
+  if (g_batched.size() >= kBatchedCache) {
+    // the oldest entry may still be in use by work in flight: synchronise first
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      free_batched(E);
+      return cuda_fail(e);
+    }
+    free_batched(g_batched.front());
+    g_batched.erase(g_batched.begin());
+  }
+  g_batched.push_back(std::move(E));
+  *out = &g_batched.back();
+  return SDFT_OK;
+}
+
+sdft_status run_batched(const sdft_plan* plans, uint64_t n, const void* in, const uint64_t* d_offsets, void* out,
+                        cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_batched_mu);
+  BatchedEntry* E = nullptr;
+  sdft_status s = batched_entry(plans, n, &E);
+  if (s != SDFT_OK) return s;
+  const size_t es = size_t(elem_bytes(E->b->prec));
+  char* stage_in = static_cast<char*>(E->d_stage);
+  char* stage_out = stage_in + stage_bytes(E->b->total, es);    // 256-byte aligned like the first half
+  int* status = plans[0]->p.d_status;
+  const unsigned grid = unsigned(std::min<uint64_t>(E->n_items, 4ull * uint64_t(sm_count())));
+  if (E->b->prec == SDFT_C64)
+    k_repack<float2><<<grid, 256, 0, st>>>(static_cast<const float2*>(in), reinterpret_cast<float2*>(stage_in),
+                                           d_offsets, E->d_k, E->d_boff, E->d_items, E->n_items, status, 1);
+  else
+    k_repack<double2><<<grid, 256, 0, st>>>(static_cast<const double2*>(in), reinterpret_cast<double2*>(stage_in),
+                                            d_offsets, E->d_k, E->d_boff, E->d_items, E->n_items, status, 1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e);
+  s = run_batch(*E->b, stage_in, stage_out, st);
+  if (s != SDFT_OK) return s;
+  if (E->b->prec == SDFT_C64)
+    k_repack<float2><<<grid, 256, 0, st>>>(reinterpret_cast<const float2*>(stage_out), static_cast<float2*>(out),
+                                           d_offsets, E->d_k, E->d_boff, E->d_items, E->n_items, status, 0);
+  else
+    k_repack<double2><<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(stage_out), static_cast<double2*>(out),
+                                            d_offsets, E->d_k, E->d_boff, E->d_items, E->n_items, status, 0);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
+}
+
 void free_strided_queues(Plan& p) {
   if (!p.queues) return;
   StridedQueues* q = static_cast<StridedQueues*>(p.queues);
@@ -630,6 +781,27 @@ sdft_status sdft_batch_execute_noalloc(sdft_batch batch, const void* d_samples, 
   if (!batch) return SDFT_ERR_ARG;
   if (batch->b.device < 0) return SDFT_ERR_NO_DEVICE;
   return sdft::run_batch_noalloc(batch->b, d_samples, d_coeffs, static_cast<cudaStream_t>(stream));
+}
+
+sdft_status sdft_execute_batched(const sdft_plan* plans, uint64_t n, const void* d_samples,
+                                 const uint64_t* d_offsets, void* d_coeffs, void* stream) {
+  if (!plans || n == 0 || n > 0xffffffffull || !d_samples || !d_offsets || !d_coeffs) return SDFT_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_samples) | reinterpret_cast<uintptr_t>(d_coeffs)) & 15u) return SDFT_ERR_ARG;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (!plans[i]) return SDFT_ERR_ARG;
+    if (plans[i]->p.deferred || plans[i]->p.device < 0) return SDFT_ERR_NO_DEVICE;
+    if (plans[i]->p.prec != plans[0]->p.prec) return SDFT_ERR_PRECISION;
+  }
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return sdft::cuda_fail(e);
+  for (uint64_t i = 0; i < n; ++i)
+    if (plans[i]->p.device != dev) return SDFT_ERR_ARG;
+  try {
+    return sdft::run_batched(plans, n, d_samples, d_offsets, d_coeffs, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return SDFT_ERR_NOMEM;
+  }
 }
 
 sdft_status sdft_batch_device_status(sdft_batch batch, int clear) {

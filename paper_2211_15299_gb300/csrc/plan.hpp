@@ -64,6 +64,7 @@ struct Plan {
   bool deferred = false;          // device tables not uploaded: host_tables holds them (serving)
   std::vector<unsigned char> host_tables;
   int strategy = SDFT_STRATEGY_LEVELS;
+  uint64_t serial = 0;            // creation number, never reused (caches keyed by plans)
 };
 
 // Host-side planning (plan.cpp). Fills everything except the device fields.

@@ -117,6 +117,16 @@ def test_host_only_plan_refuses_execution():
         with pytest.raises(N.SdftError) as ei:
             N.sdft_execute_strided_host(h, 1, host.ctypes.data, host.ctypes.data, 16, 16, 0, None)
         assert ei.value.name == "SDFT_ERR_NO_DEVICE"
+        with pytest.raises(N.SdftError) as ei:       # batched execution needs device plans
+            N.sdft_execute_batched([h, h], 16, 16, 16, None)
+        assert ei.value.name == "SDFT_ERR_NO_DEVICE"
+        h2 = N.sdft_plan_create(4, [0, 1, 2, 3], N.SDFT_C128, N.SDFT_PLAN_HOST_ONLY)
+        try:
+            with pytest.raises(N.SdftError) as ei:   # one precision per call
+                N.sdft_execute_batched([h, h2], 16, 16, 16, None)
+            assert ei.value.name in ("SDFT_ERR_NO_DEVICE", "SDFT_ERR_PRECISION")
+        finally:
+            N.sdft_plan_destroy(h2)
         with pytest.raises(N.SdftError) as ei:       # host buffers neither identical nor disjoint
             N.sdft_execute_strided_host(h, 1, None, host.ctypes.data, 16, 16, 0, None)
         assert ei.value.name == "SDFT_ERR_ARG"

@@ -219,3 +219,69 @@ def test_queue_shapes_bit_identical_and_autotune():
     out = b.unpack(y.cpu().numpy().astype(np.complex128))
     worst = max(rel_l2(out[i], Cs[i]) for i in range(len(insts)))
     assert worst < 1e-5
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_execute_batched_at_caller_offsets(prec):
+    """sdft_execute_batched: instances packed in the caller's order (not the
+    batch's by decreasing k); each equals its strided transform bit for bit; in
+    place; graph capture of a warmed-up call."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan, execute_batched
+    rng = np.random.default_rng(7300 + prec)
+    tb = 12 if prec == 0 else 11
+    sizes = [int(s) for s in rng.permutation([0, 3, 5, 7, 9, 10, tb, tb, tb + 1, tb + 3, 4, 6])]
+    insts = _instances(rng, sizes)
+    plans = [Plan(i.M, i.J, prec) for i in insts]
+    dt = torch.complex64 if prec == 0 else torch.complex128
+    # packing in the given order (offsets[i+1] - offsets[i] = k_i, no 16-byte
+    # alignment of the instances needed), then the list reversed, in place
+    packed = np.concatenate([[0], np.cumsum([p.k for p in plans])]).astype(np.int64)
+    xs = torch.randn(int(packed[-1]), dtype=dt, device="cuda")
+    d_off = torch.from_numpy(packed).cuda()
+    y = execute_batched(plans, xs, d_off)
+    torch.cuda.synchronize()
+    assert plans[0].device_status() == 0
+    for i, p in enumerate(plans):
+        a, b = int(packed[i]), int(packed[i + 1])
+        ref = p.execute_strided(xs[a:b].clone())
+        assert torch.equal(y[a:b], ref), i
+    rplans = plans[::-1]
+    rpacked = np.concatenate([[0], np.cumsum([p.k for p in rplans])]).astype(np.int64)
+    xr = torch.randn(int(rpacked[-1]), dtype=dt, device="cuda")
+    yr = xr.clone()
+    execute_batched(rplans, yr, torch.from_numpy(rpacked).cuda(), yr)       # in place
+    torch.cuda.synchronize()
+    for i, p in enumerate(rplans):
+        a, b = int(rpacked[i]), int(rpacked[i + 1])
+        assert torch.equal(yr[a:b], p.execute_strided(xr[a:b].clone())), i
+    # graph capture of a warmed-up call, replayed on new samples
+    s = torch.cuda.Stream()
+    out = torch.empty_like(xs)
+    with torch.cuda.stream(s):
+        execute_batched(plans, xs, d_off, out, stream=s.cuda_stream)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        execute_batched(plans, xs, d_off, out, stream=s.cuda_stream)
+    xs.copy_(torch.randn_like(xs))
+    g.replay()
+    torch.cuda.synchronize()
+    for i, p in enumerate(plans):
+        a, b = int(packed[i]), int(packed[i + 1])
+        assert torch.equal(out[a:b], p.execute_strided(xs[a:b].clone())), i
+    assert plans[0].device_status() == 0
+
+
+def test_execute_batched_reports_offsets_that_do_not_fit():
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan, execute_batched
+    rng = np.random.default_rng(7400)
+    plans = [Plan(i.M, i.J, 0) for i in _instances(rng, [6, 12, 8])]
+    ks = [p.k for p in plans]
+    bad = np.array([0, ks[0], ks[0] + ks[1] - 2, sum(ks)], dtype=np.int64)   # instance 1 two values short
+    x = torch.randn(sum(ks), dtype=torch.complex64, device="cuda")
+    execute_batched(plans, x, torch.from_numpy(bad).cuda())
+    torch.cuda.synchronize()
+    assert plans[0].device_status(clear=True) == 0x104
+    assert plans[0].device_status() == 0
