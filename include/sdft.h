@@ -66,6 +66,9 @@ typedef enum { SDFT_C64 = 0, SDFT_C128 = 1 } sdft_prec;
 
 /* Plan flags. */
 #define SDFT_PLAN_HOST_ONLY 0x1u    /* build the host tables only; no device upload */
+#define SDFT_PLAN_USER_ORDER 0x10u  /* also keep, on the device, the canonical position of every
+                                       J[u] as passed (4 bytes per frequency), for
+                                       sdft_plan_to_user_order */
 #define SDFT_PLAN_FP64_DF 0x8u      /* complex128 plans: strided transforms and synthesis run
                                        their level kernels in double-float arithmetic (pairs of
                                        FP32 values, 48-bit significand, FP32 exponent range) on
@@ -165,6 +168,19 @@ sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_s
  */
 sdft_status sdft_execute_strided_host(sdft_plan plan, uint64_t batch, const void* h_samples, void* h_coeffs,
                                       void* d_samples, void* d_coeffs, uint64_t chunk, void* stream);
+
+/*
+ * sdft_plan_to_user_order - the optional reordering of the coefficients into the
+ * caller's order of J: for `batch` instances, d_user[b k + u] = d_canonical[b k +
+ * t(u)], where t(u) is the canonical position of J[u] (J as passed to
+ * sdft_plan_create; the canonical order is the one sdft_execute returns and
+ * sdft_plan_support_order lists). One gather kernel, out of place (the buffers
+ * must not overlap), asynchronous on `stream`. Needs a plan created with
+ * SDFT_PLAN_USER_ORDER (SDFT_ERR_ARG otherwise); SDFT_ERR_NO_DEVICE for
+ * host-only plans.
+ */
+sdft_status sdft_plan_to_user_order(sdft_plan plan, uint64_t batch, const void* d_canonical, void* d_user,
+                                    void* stream);
 
 /*
  * sdft_execute_batched - n instances, instance i with its own plan plans[i]

@@ -33,6 +33,7 @@ SDFT_STRATEGY_LEVELS, SDFT_STRATEGY_QUEUE = 1, 2
 SDFT_SCHEDULE_AUTO, SDFT_SCHEDULE_LANES, SDFT_SCHEDULE_ROUND_ROBIN = 0, 1, 2
 SDFT_PLAN_HOST_ONLY = 0x1
 SDFT_PLAN_FP64_DF = 0x8
+SDFT_PLAN_USER_ORDER = 0x10
 SDFT_SAS_TWO_STAGE = 0x4
 SDFT_PLAN_DEFER_DEVICE = 0x2
 
@@ -63,6 +64,7 @@ SIGNATURES = {
     "sdft_execute_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "sdft_execute_strided_host": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
     "sdft_execute_batched": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp]),
+    "sdft_plan_to_user_order": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "sdft_synthesize_strided_host": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
     "sdft_synthesize": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "sdft_synthesize_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
@@ -210,6 +212,11 @@ def sdft_execute_strided_host(plan: int, batch: int, h_samples, h_coeffs, d_samp
                               stream=None) -> None:
     _check(_lib.sdft_execute_strided_host(plan, int(batch), _ptr(h_samples), _ptr(h_coeffs), _ptr(d_samples),
                                           _ptr(d_coeffs), int(chunk), _stream(stream)), "sdft_execute_strided_host")
+
+
+def sdft_plan_to_user_order(plan: int, batch: int, d_canonical, d_user, stream=None) -> None:
+    _check(_lib.sdft_plan_to_user_order(plan, int(batch), _ptr(d_canonical), _ptr(d_user), _stream(stream)),
+           "sdft_plan_to_user_order")
 
 
 def sdft_execute_batched(plans, d_samples, d_offsets, d_coeffs, stream=None) -> None:

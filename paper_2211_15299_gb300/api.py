@@ -49,13 +49,14 @@ class Plan:
     """A validated homogeneous support with its sample set and device twiddles."""
 
     def __init__(self, log2N: int, J: Sequence[int], prec="c64", host_only: bool = False, defer: bool = False,
-                 fp64_df: bool = False):
+                 fp64_df: bool = False, user_order: bool = False):
         """host_only: host tables only (introspection). defer: device tables kept in host
         memory until a Server uploads them with a request (no device allocation).
         fp64_df (complex128): butterflies in double-float arithmetic on the FP32 pipes."""
         code = _PREC[prec] if isinstance(prec, str) else int(prec)
         flags = (N.SDFT_PLAN_HOST_ONLY if host_only else 0) | (N.SDFT_PLAN_DEFER_DEVICE if defer else 0)
         flags |= N.SDFT_PLAN_FP64_DF if fp64_df else 0
+        flags |= N.SDFT_PLAN_USER_ORDER if user_order else 0
         self.handle = N.sdft_plan_create(log2N, J, code, flags)
         self.log2N, self.s, self.prec = N.sdft_plan_info(self.handle)
         self.k = 1 << self.s
@@ -144,6 +145,18 @@ class Plan:
         _check_tensor(d_out, self.dtype, batch * self.k, "device output")
         fn(self.handle, batch, h_in, h_out, d_in, d_out, chunk, _current_stream(stream))
         return h_out
+
+    def to_user_order(self, coeffs, out=None, stream=None, batch: Optional[int] = None):
+        """Coefficients from canonical order into the order of J as given to the
+        plan (plans created with user_order=True)."""
+        if batch is None:
+            batch = coeffs.numel() // self.k
+        _check_tensor(coeffs, self.dtype, batch * self.k, "coeffs")
+        if out is None:
+            out = _torch().empty_like(coeffs)
+        _check_tensor(out, self.dtype, batch * self.k, "out")
+        N.sdft_plan_to_user_order(self.handle, batch, coeffs, out, _current_stream(stream))
+        return out
 
     def synthesize(self, coeffs, samples=None, stream=None, batch: Optional[int] = None):
         """Samples from coefficients (the inverse of execute_strided)."""

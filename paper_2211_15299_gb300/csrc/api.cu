@@ -109,6 +109,30 @@ static sdft_status check_device(const Plan& p) {
   return dev == p.device ? SDFT_OK : SDFT_ERR_ARG;
 }
 
+// d_user[b k + u] = d_canonical[b k + pos[u]]: reads within one instance (cached),
+// coalesced writes.
+template <class C>
+__global__ void __launch_bounds__(256) k_user_order(const C* __restrict__ src, C* __restrict__ dst,
+                                                    const uint32_t* __restrict__ pos, uint64_t k, uint64_t total) {
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t b = i / k, u = i - b * k;
+    dst[i] = src[b * k + pos[u]];
+  }
+}
+
+sdft_status launch_user_order(const Plan& p, uint64_t batch, const void* in, void* out, cudaStream_t st) {
+  const uint64_t total = batch * p.k;
+  const uint64_t blocks = std::min<uint64_t>((total + 255) / 256, 8ull * uint64_t(sm_count()));
+  if (p.prec == SDFT_C64)
+    k_user_order<float2><<<unsigned(blocks), 256, 0, st>>>(static_cast<const float2*>(in), static_cast<float2*>(out),
+                                                            p.d_user_pos, p.k, total);
+  else
+    k_user_order<double2><<<unsigned(blocks), 256, 0, st>>>(static_cast<const double2*>(in),
+                                                             static_cast<double2*>(out), p.d_user_pos, p.k, total);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
+}
+
 sdft_status run_strided(sdft_plan_s* h, uint64_t batch, const void* in, void* out, cudaStream_t st) {
   const Plan& p = h->p;
   sdft_status s = check_device(p);
@@ -153,7 +177,8 @@ sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft
                              sdft_plan* out) {
   if (!out) return SDFT_ERR_ARG;
   *out = nullptr;
-  if (flags & ~(SDFT_PLAN_HOST_ONLY | SDFT_PLAN_DEFER_DEVICE | SDFT_PLAN_FP64_DF)) return SDFT_ERR_ARG;
+  if (flags & ~(SDFT_PLAN_HOST_ONLY | SDFT_PLAN_DEFER_DEVICE | SDFT_PLAN_FP64_DF | SDFT_PLAN_USER_ORDER))
+    return SDFT_ERR_ARG;
   if ((flags & SDFT_PLAN_HOST_ONLY) && (flags & SDFT_PLAN_DEFER_DEVICE)) return SDFT_ERR_ARG;
   if ((flags & SDFT_PLAN_FP64_DF) && prec != SDFT_C128) return SDFT_ERR_ARG;
   sdft_plan_s* h = new (std::nothrow) sdft_plan_s();
@@ -230,7 +255,25 @@ sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft
       if (e == cudaSuccess) e = cudaMalloc(&p.d_tw_df, tw_bytes);
       if (e == cudaSuccess) e = cudaMemcpy(p.d_tw_df, df.data(), tw_bytes, cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess && (flags & SDFT_PLAN_USER_ORDER)) {
+      // canonical position of J[u]: bit q of the key is bit r_q of J[u]
+      std::vector<uint32_t> pos;
+      try {
+        pos.resize(size_t(p.k));
+      } catch (const std::bad_alloc&) {
+        e = cudaErrorMemoryAllocation;
+      }
+      for (uint64_t u = 0; e == cudaSuccess && u < p.k; ++u) {
+        uint64_t t = 0;
+        for (uint32_t q = 0; q < p.s; ++q) t |= ((J[u] >> p.pivots[q]) & 1ull) << q;
+        pos[size_t(u)] = uint32_t(t);
+      }
+      if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p.d_user_pos), sizeof(uint32_t) * p.k);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(p.d_user_pos, pos.data(), sizeof(uint32_t) * p.k, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
+      if (p.d_user_pos) cudaFree(p.d_user_pos);
       if (p.d_tw_df) cudaFree(p.d_tw_df);
       if (p.d_tw) cudaFree(p.d_tw);
       if (p.d_status) cudaFree(p.d_status);
@@ -382,6 +425,21 @@ sdft_status sdft_synthesize_strided_host(sdft_plan plan, uint64_t batch, const v
   return run_host(plan, batch, h_coeffs, h_samples, d_coeffs, d_samples, chunk, stream, true);
 }
 
+sdft_status sdft_plan_to_user_order(sdft_plan plan, uint64_t batch, const void* d_canonical, void* d_user,
+                                    void* stream) {
+  if (!plan || !d_canonical || !d_user) return SDFT_ERR_ARG;
+  const sdft::Plan& p = plan->p;
+  if (p.device < 0 || !p.d_status) return SDFT_ERR_NO_DEVICE;
+  if (!p.d_user_pos) return SDFT_ERR_ARG;
+  if (batch == 0) return SDFT_OK;
+  const uint64_t eb = uint64_t(sdft::elem_bytes(p.prec));
+  if (batch > (~0ull / eb) / p.k) return SDFT_ERR_ARG;
+  const uint64_t bytes = batch * p.k * eb;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(d_canonical), b = reinterpret_cast<uintptr_t>(d_user);
+  if (a < b + bytes && b < a + bytes) return SDFT_ERR_ARG;
+  return sdft::launch_user_order(p, batch, d_canonical, d_user, static_cast<cudaStream_t>(stream));
+}
+
 sdft_status sdft_synthesize(sdft_plan plan, const void* d_coeffs, void* d_samples, void* stream) {
   if (!plan) return SDFT_ERR_ARG;
   return sdft::run_strided_inverse(plan, 1, d_coeffs, d_samples, static_cast<cudaStream_t>(stream));
@@ -460,6 +518,7 @@ sdft_status sdft_plan_destroy(sdft_plan plan) {
     if (ev) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
   if (plan->p.d_tw) cudaFree(plan->p.d_tw);
   if (plan->p.d_tw_df) cudaFree(plan->p.d_tw_df);
+  if (plan->p.d_user_pos) cudaFree(plan->p.d_user_pos);
   if (plan->p.d_status) cudaFree(plan->p.d_status);
   delete plan;
   return SDFT_OK;

@@ -566,6 +566,7 @@ sdft_status run_strided_queue(sdft_plan_s* plan, uint64_t batch, const void* in,
 // one kernel over chunks of at most kRepackChunk values. The caller's offsets
 // stay on the device (graph-capturable); a kernel checks each against its plan.
 constexpr uint64_t kRepackChunk = 8192;
+constexpr int kBadOffsets = 0x104;     // status: offsets[i+1] - offsets[i] differs from plan i's k
 constexpr size_t kBatchedCache = 8;
 
 struct RepackItem {

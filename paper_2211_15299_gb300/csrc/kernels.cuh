@@ -65,7 +65,6 @@ constexpr uint32_t kTileBytes = 32768;
 constexpr int kBadSmem = 0x101;   // less dynamic shared memory than the layout needs
 constexpr int kBadMap = 0x102;    // tensor map parameter not 64-byte aligned
 constexpr int kBadTable = 0x103;  // twiddle table not 16-byte aligned
-constexpr int kBadOffsets = 0x104; // sdft_execute_batched: offsets[i+1] - offsets[i] differs from plan i's k
 constexpr int kBufs = 3;                                             // tile buffers per work-queue CTA
 // Tile buffers per level-kernel CTA. Two keep the level kernel at the speed of a
 // copy-only variant of itself (TMA in and out, no passes) on the 2^12-point

@@ -57,6 +57,7 @@ struct Plan {
   int device = -1;
   void* d_tw = nullptr;           // device twiddles (float2 or double2)
   void* d_tw_df = nullptr;        // the same table as double-float pairs (SDFT_PLAN_FP64_DF)
+  uint32_t* d_user_pos = nullptr; // SDFT_PLAN_USER_ORDER: canonical position of J[u]
   int* d_status = nullptr;        // device status word
   uint64_t device_bytes = 0;
   double tw0[32] = {0};           // level-0 table entries 1..15 (rounded to prec), for kernel params

@@ -187,3 +187,32 @@ def test_config3_full_size(contiguous):
         spot = O.coefficients_at(inst.M, Jc[idx], I, F[b].astype(np.complex128))
         row = y[b].cpu().numpy().astype(np.complex128)
         assert np.abs(row[idx] - spot).max() / (np.linalg.norm(row) / np.sqrt(k)) < 1e-5
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_user_order(prec):
+    """The optional reordering into the caller's order of J: coefficient u is the
+    one of J[u] (J shuffled before planning), against the oracle."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan
+    rng = np.random.default_rng(9400 + prec)
+    M, s, B = 18, 13, 3
+    piv = np.sort(rng.choice(np.arange(M), size=s, replace=False))
+    J = W.homogeneous_support(M, piv, rng)
+    J_user = rng.permutation(J)
+    plan = Plan(M, J_user, prec, user_order=True)
+    Jc = O.canonical_support_by_key(J, piv)
+    C = W.complex_gaussian((B, plan.k), rng)
+    F = O.synthesize_levels(M, piv, Jc, C)
+    dt = np.complex64 if prec == 0 else np.complex128
+    y = plan.execute_strided(torch.from_numpy(F.astype(dt)).cuda())
+    yu = plan.to_user_order(y)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    where = {int(j): t for t, j in enumerate(Jc)}
+    C_user = C[:, [where[int(j)] for j in J_user]]
+    assert rel_l2(yu.cpu().numpy().astype(np.complex128), C_user) < (1e-5 if prec == 0 else 1e-12)
+    # plans without the flag refuse the call
+    from paper_2211_15299_gb300 import SdftError
+    with pytest.raises(SdftError):
+        Plan(M, J_user, prec).to_user_order(y)
