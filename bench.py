@@ -429,13 +429,37 @@ def run_large(args):
             by[name] = statistics.mean(t)
         best = min(by, key=by.get)
         mean = by[best]
+        # the oracle on the host cores: 16 of the instances (the last strategy's output)
+        torch.cuda.synchronize()
+        nrow = min(16, args.large_batch)
+        dt, used, rel = _cpu_oracle_rows(inst.M, inst.pivots, inst.J, x[:nrow].cpu().numpy(), y[:nrow].cpu().numpy())
+        cpu_oracle = {"value": nrow * inst.k / dt, "unit": UNIT, "kind": "oracle", "cores": used,
+                      "sample": f"{nrow} of the {args.large_batch} instances, Algorithm 1 in the oracle's plain C "
+                                "(FP64, OpenMP)", "seconds": dt, "rel_l2_gpu_vs_oracle": rel}
         res["contiguous" if contiguous else "spread"] = {
             "coeffs_per_s": coeffs / mean, "ms_per_step": 1e3 * mean, "strategy": best,
-            "ms_by_strategy": {k: 1e3 * v for k, v in by.items()},
+            "ms_by_strategy": {k: 1e3 * v for k, v in by.items()}, "cpu_oracle": cpu_oracle,
             "alg_GBps": 16 * coeffs / mean / 1e9, "frac_of_peak": 16 * coeffs / mean / 1e9 / _peaks()[0],
             "pivots": [int(p) for p in inst.pivots]}
         assert plan.device_status() == 0
     return res
+
+
+def _cpu_oracle_rows(M, pivots, J, F, got, threads=None):
+    """The oracle's plain-C Algorithm 1 (FP64, OpenMP over instances) on the
+    rows F (B, k) of one support: (seconds, threads, relative L2 of the GPU rows
+    `got` against it)."""
+    threads = threads or os.cpu_count()
+    import oracle as O
+    from oracle import alg1
+    Jc = O.canonical_support_by_key(J, pivots)
+    F = np.ascontiguousarray(F, dtype=np.complex128)
+    alg1.alg1_batch(M, pivots, Jc, F[:1], threads=threads)      # warm-up
+    t0 = time.perf_counter()
+    C, used = alg1.alg1_batch(M, pivots, Jc, F, threads=threads)
+    dt = time.perf_counter() - t0
+    got = np.asarray(got, dtype=np.complex128).reshape(C.shape)
+    return dt, used, float(np.linalg.norm(got - C) / np.linalg.norm(C))
 
 
 def run_uneven(args):
@@ -470,7 +494,24 @@ def run_uneven(args):
     mean = statistics.mean(t)
     total = b.total
     tw_bytes = sum(8 * (p.k - 1) for p in plans)
+    # the oracle on the host cores: the first 64 instances, one call each
+    torch.cuda.synchronize()
+    xh, yh = x.cpu().numpy(), y.cpu().numpy()
+    n_cpu, t_cpu, used_max, rel_max, coeffs_cpu = min(64, len(insts)), 0.0, 0, 0.0, 0
+    for i in range(n_cpu):
+        a, z = b.offsets[i], b.offsets[i] + plans[i].k
+        dt, used, rel = _cpu_oracle_rows(insts[i].M, insts[i].pivots, insts[i].J, xh[None, a:z], yh[None, a:z],
+                                         threads=1)      # one instance per call: one thread
+        t_cpu += dt
+        used_max = max(used_max, used)
+        rel_max = max(rel_max, rel)
+        coeffs_cpu += plans[i].k
+    cpu_oracle = {"value": coeffs_cpu / t_cpu, "unit": UNIT, "kind": "oracle", "cores": used_max,
+                  "sample": f"the first {n_cpu} instances (the largest k), one call and one thread each, "
+                            "Algorithm 1 in the oracle's plain C (FP64)",
+                  "seconds": t_cpu, "max_rel_l2_gpu_vs_oracle": rel_max}
     return {"instances": len(plans), "coeffs_per_step": total, "coeffs_per_s": total / mean,
+            "cpu_oracle": cpu_oracle,
             "ms_per_step": 1e3 * mean, "alg_GBps": (16 * total + tw_bytes) / mean / 1e9,
             "alg_bytes_per_step": 16 * total + tw_bytes, "work_items": n_items,
             "dependency_counters": n_ctr, "grid": grid, "plan_build_s": t_plan,
