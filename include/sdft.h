@@ -66,9 +66,6 @@ typedef enum { SDFT_C64 = 0, SDFT_C128 = 1 } sdft_prec;
 
 /* Plan flags. */
 #define SDFT_PLAN_HOST_ONLY 0x1u    /* build the host tables only; no device upload */
-#define SDFT_PLAN_USER_ORDER 0x10u  /* also keep, on the device, the canonical position of every
-                                       J[u] as passed (4 bytes per frequency), for
-                                       sdft_plan_to_user_order */
 #define SDFT_PLAN_FP64_DF 0x8u      /* complex128 plans: strided transforms and synthesis run
                                        their level kernels in double-float arithmetic (pairs of
                                        FP32 values, 48-bit significand, FP32 exponent range) on
@@ -81,6 +78,9 @@ typedef enum { SDFT_C64 = 0, SDFT_C128 = 1 } sdft_prec;
                                        the plan can only be used through a server
                                        (sdft_server_submit), which uploads them into its arena
                                        per request, so creating it allocates no device memory */
+#define SDFT_PLAN_USER_ORDER 0x10u  /* also keep, on the device, the canonical position of every
+                                       J[u] as passed (4 bytes per frequency), for
+                                       sdft_plan_to_user_order */
 
 /* Largest log2N and log2 k the library accepts. */
 #define SDFT_MAX_LOG2N 62u
@@ -94,7 +94,8 @@ typedef enum { SDFT_C64 = 0, SDFT_C128 = 1 } sdft_prec;
  *            during the call.
  *   k      : |J|, a power of two, k <= 2^SDFT_MAX_LOG2K.
  *   prec   : arithmetic of the device path (complex64 or complex128 buffers).
- *   flags  : 0, SDFT_PLAN_HOST_ONLY or SDFT_PLAN_DEFER_DEVICE.
+ *   flags  : 0, or SDFT_PLAN_HOST_ONLY or SDFT_PLAN_DEFER_DEVICE (not both), with
+ *            SDFT_PLAN_FP64_DF (complex128 only) and SDFT_PLAN_USER_ORDER as needed.
  *   out    : receives the plan; the caller owns it (sdft_plan_destroy).
  * Pivots: the levels l at which the congruence tree T(J) splits (Definition 8),
  * found as the 2-adic valuations of differences of neighbours in bit-reversed
