@@ -802,7 +802,6 @@ def main():
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="instances in the oracle dense-solve baseline (at most the batch; about 10 s of CPU work)")
-    ap.add_argument("--ref-sample", type=int, default=256, help="instances per step of --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only-fp32", action="store_true", help="time the complex64 leg only (profiling)")
     ap.add_argument("--large", action="store_true", help="time only the large-k leg (N=2^30, k=2^20)")
