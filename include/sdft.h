@@ -194,8 +194,9 @@ sdft_status sdft_plan_to_user_order(sdft_plan plan, uint64_t batch, const void* 
  * a gather into the batch's own packing and a scatter back; the first call for a
  * given list of plans builds that batch and its staging buffers (2 x total
  * values) and caches them (allocates and may synchronise the device: make that
- * call before capturing a graph); calls with the same list must not overlap on
- * the GPU. sdft_batch_execute on the batch's own layout saves the two copies.
+ * call before capturing a graph; the 8 most recent lists are kept, and
+ * sdft_plan_destroy of any plan in a list frees that list's batch); calls with
+ * the same list must not overlap on the GPU. sdft_batch_execute on the batch's own layout saves the two copies.
  * Offsets that do not match the plans' k are reported as 0x104 in the status
  * word of plans[0] (sdft_plan_device_status) and those instances are skipped;
  * offsets must lie inside the caller's buffers. Buffers 16-byte aligned,

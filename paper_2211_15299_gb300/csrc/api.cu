@@ -512,6 +512,7 @@ sdft_status sdft_plan_device_status(sdft_plan plan, int clear) {
 sdft_status sdft_plan_destroy(sdft_plan plan) {
   if (!plan) return SDFT_ERR_ARG;
   sdft::free_strided_queues(plan->p);
+  sdft::forget_batched(plan->p.serial);
   for (void* st : plan->host_st)
     if (st) cudaStreamDestroy(static_cast<cudaStream_t>(st));
   for (void* ev : plan->host_ev)

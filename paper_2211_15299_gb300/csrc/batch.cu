@@ -711,6 +711,19 @@ sdft_status run_batched(const sdft_plan* plans, uint64_t n, const void* in, cons
   return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
 }
 
+void forget_batched(uint64_t serial) {
+  std::lock_guard<std::mutex> lk(g_batched_mu);
+  for (size_t i = 0; i < g_batched.size();) {
+    const auto& v = g_batched[i].serials;
+    if (std::find(v.begin(), v.end(), serial) != v.end()) {
+      free_batched(g_batched[i]);
+      g_batched.erase(g_batched.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
 void free_strided_queues(Plan& p) {
   if (!p.queues) return;
   StridedQueues* q = static_cast<StridedQueues*>(p.queues);

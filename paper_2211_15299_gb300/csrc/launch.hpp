@@ -43,5 +43,8 @@ sdft_status launch_plan_inv_f64(const Plan& plan, uint64_t batch, const void* in
 sdft_status run_strided_queue(sdft_plan_s* plan, uint64_t batch, const void* in, void* out, cudaStream_t st);
 // Release the cached queues of a plan.
 void free_strided_queues(Plan& p);
+// Release the cached sdft_execute_batched batches whose plan list names the plan
+// with this serial (the caller has synchronised before destroying the plan).
+void forget_batched(uint64_t serial);
 
 }  // namespace sdft

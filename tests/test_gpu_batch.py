@@ -285,3 +285,33 @@ def test_execute_batched_reports_offsets_that_do_not_fit():
     torch.cuda.synchronize()
     assert plans[0].device_status(clear=True) == 0x104
     assert plans[0].device_status() == 0
+
+
+def test_execute_batched_cache_released_with_its_plans():
+    """Destroying a plan of a cached execute_batched list frees that list's batch
+    and staging buffers (2 x 2^24 complex64 values here, 256 MiB); a new list of
+    new plans then runs correctly."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan, execute_batched
+    rng = np.random.default_rng(7500)
+    insts = _instances(rng, [12] * 4)
+    plans = [Plan(insts[0].M, insts[0].J, 0)] * 4096     # one plan, repeated
+    ks = plans[0].k
+    off = torch.arange(0, ks * 4097, ks, dtype=torch.int64, device="cuda")
+    x = torch.randn(ks * 4096, dtype=torch.complex64, device="cuda")
+    y = execute_batched(plans, x, off)
+    torch.cuda.synchronize()
+    assert torch.equal(y[:ks], plans[0].execute_strided(x[:ks].clone()))
+    del y
+    torch.cuda.empty_cache()
+    free0, _ = torch.cuda.mem_get_info()
+    plans[0].close()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 - free0 >= 2 * ks * 4096 * 8            # the two staging halves
+    fresh = [Plan(i.M, i.J, 0) for i in insts[:3]]
+    packed = torch.tensor([0, ks, 2 * ks, 3 * ks], dtype=torch.int64, device="cuda")
+    z = execute_batched(fresh, x[:3 * ks], packed)
+    torch.cuda.synchronize()
+    for i, p in enumerate(fresh):
+        assert torch.equal(z[i * ks:(i + 1) * ks], p.execute_strided(x[i * ks:(i + 1) * ks].clone())), i
+    assert fresh[0].device_status() == 0
