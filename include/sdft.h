@@ -127,7 +127,10 @@ sdft_status sdft_plan_support_order(sdft_plan plan, uint64_t* Jc);
  * (re, im) at tw[2 * (2^(m-1) - 1 + u)]; 2 * (k - 1) doubles. Unscaled. */
 sdft_status sdft_plan_twiddles(sdft_plan plan, double* tw);
 
-/* Device bytes held by the plan (tables and status word). */
+/* Device bytes the plan allocated when it was created: its tables (with the
+ * double-float copy and the user-order positions when their flags are set) and
+ * its status word. Work queues cached later by the queue strategy are not
+ * counted. */
 sdft_status sdft_plan_device_bytes(sdft_plan plan, uint64_t* bytes);
 
 /*

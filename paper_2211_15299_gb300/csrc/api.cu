@@ -281,7 +281,8 @@ sdft_status sdft_plan_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft
       return e == cudaErrorMemoryAllocation ? SDFT_ERR_NOMEM : sdft::cuda_fail(e);
     }
     p.device = dev;
-    p.device_bytes = tw_bytes + 256;
+    p.device_bytes = tw_bytes + 256 + (p.d_tw_df ? tw_bytes : 0) +
+                     (p.d_user_pos ? sizeof(uint32_t) * p.k : 0);
   }
   *out = h;
   return SDFT_OK;

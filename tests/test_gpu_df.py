@@ -30,6 +30,7 @@ def test_df_against_oracle_and_fp64(M, s, batch):
     piv, J = _instance(rng, M, s)
     df = Plan(M, J, "c128", fp64_df=True)
     f64 = Plan(M, J, "c128")
+    assert df.device_bytes == 2 * f64.device_bytes - 256     # a second table of the same size
     Jc = O.canonical_support_by_key(J, piv)
     C = W.complex_gaussian((batch, df.k), rng)
     F = O.synthesize_levels(M, piv, Jc, C)

@@ -201,6 +201,7 @@ def test_user_order(prec):
     J = W.homogeneous_support(M, piv, rng)
     J_user = rng.permutation(J)
     plan = Plan(M, J_user, prec, user_order=True)
+    assert plan.device_bytes == Plan(M, J_user, prec).device_bytes + 4 * plan.k   # the positions
     Jc = O.canonical_support_by_key(J, piv)
     C = W.complex_gaussian((B, plan.k), rng)
     F = O.synthesize_levels(M, piv, Jc, C)
