@@ -134,10 +134,15 @@ bool pivots_along_first_path(uint32_t M, const uint64_t* J, uint64_t k, uint32_t
   for (uint32_t l = 0; l < M; ++l)
     if (mask >> l & 1) p.pivots.push_back(l);
   if (!canonical_order(J, k, s, M, qbits, p)) return false;
-  for (uint64_t t = 1; t < k; ++t) {
-    const int h = highest_bit(t);
-    const uint64_t x = p.Jc[t] ^ p.Jc[t ^ (1ull << h)];
-    if (static_cast<uint32_t>(__builtin_ctzll(x)) != p.pivots[h]) return false;
+  // For each key bit h: t in [2^h, 2^(h+1)) against t - 2^h; "first differ at
+  // bit r" is (x & (2^(r+1) - 1)) == 2^r, checked over whole runs without branches.
+  for (uint32_t h = 0; h < s; ++h) {
+    const uint64_t half = 1ull << h, want = 1ull << p.pivots[h], low = (want << 1) - 1;
+    const uint64_t* hi = p.Jc.data() + half;
+    const uint64_t* lo = p.Jc.data();
+    uint64_t bad = 0;
+    for (uint64_t t = 0; t < half; ++t) bad |= ((hi[t] ^ lo[t]) & low) ^ want;
+    if (bad) return false;
   }
   return true;
 }

@@ -106,6 +106,32 @@ def test_homogeneity_decision_matches_oracle_on_near_misses():
             assert ei.value.name == want, (M, J)
 
 
+def test_homogeneity_decision_exhaustive_small():
+    # every 4-element subset of Z_16, each in three orders (which element comes
+    # first decides the planner's fast path), and 3000 random 8-element subsets
+    # of Z_32: the planner's verdict, pivots and canonical order are the oracle's
+    from paper_2211_15299_gb300 import Plan, SdftError
+    import itertools
+    rng = np.random.default_rng(4343)
+    cases = [(4, list(c)) for c in itertools.combinations(range(16), 4)]
+    cases = [(M, order) for M, J in cases for order in (J, J[::-1], J[1:] + J[:1])]
+    cases += [(5, [int(x) for x in rng.choice(32, size=8, replace=False)]) for _ in range(3000)]
+    n_hom = 0
+    for M, J in cases:
+        Ja = np.asarray(J, dtype=np.uint64)
+        if O.is_homogeneous(Ja, M):
+            n_hom += 1
+            p = Plan(M, J, host_only=True)
+            piv = O.pivots_by_tree(Ja, M)
+            assert [int(x) for x in p.pivots] == [int(x) for x in piv], (M, J)
+            assert [int(x) for x in p.support_order] == [int(x) for x in O.canonical_support_by_key(Ja, piv)]
+        else:
+            with pytest.raises(SdftError) as ei:
+                Plan(M, J, host_only=True)
+            assert ei.value.name == "SDFT_ERR_NOT_HOMOGENEOUS", (M, J)
+    assert n_hom > 1000
+
+
 def test_host_only_plan_refuses_execution():
     from paper_2211_15299_gb300 import _native as N
     h = N.sdft_plan_create(4, [0, 1, 2, 3], N.SDFT_C64, N.SDFT_PLAN_HOST_ONLY)
