@@ -723,9 +723,14 @@ def cpu_baseline(inst, x32, y32, sample):
     Fa = x32.cpu().numpy().astype(np.complex128)
     got_all = y32.cpu().numpy().astype(np.complex128)
     alg1.alg1_batch(inst.M, inst.pivots, Jc, Fa[:64], threads=os.cpu_count())      # warm-up
-    t0 = time.perf_counter()
-    Cc, used = alg1.alg1_batch(inst.M, inst.pivots, Jc, Fa, threads=os.cpu_count())
-    dc = time.perf_counter() - t0
+    # one pass over the batch takes milliseconds: repeat it for about a second
+    # (at most 200 passes) and take the median pass
+    runs = []
+    while len(runs) < 200 and (len(runs) < 3 or sum(runs) < 1.0):
+        t0 = time.perf_counter()
+        Cc, used = alg1.alg1_batch(inst.M, inst.pivots, Jc, Fa, threads=os.cpu_count())
+        runs.append(time.perf_counter() - t0)
+    dc = statistics.median(runs)
     rel_c = float(np.linalg.norm(got_all - Cc) / np.linalg.norm(Cc))
     F = Fa[:sample]
     t0 = time.perf_counter()
@@ -737,8 +742,9 @@ def cpu_baseline(inst, x32, y32, sample):
     da = time.perf_counter() - t0
     rel_a = float(np.linalg.norm(got_all - Ca) / np.linalg.norm(Ca))
     return {"value": Fa.shape[0] * inst.k / dc, "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"all {Fa.shape[0]} instances, Algorithm 1 in the oracle's plain C (FP64, OpenMP)",
-            "seconds": dc, "rel_l2_gpu_fp32_vs_oracle": rel_c,
+            "sample": f"all {Fa.shape[0]} instances, Algorithm 1 in the oracle's plain C (FP64, OpenMP), "
+                      f"median of {len(runs)} passes",
+            "seconds": dc, "passes": len(runs), "rel_l2_gpu_fp32_vs_oracle": rel_c,
             "dense_solve": {"value": sample * inst.k / dt, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
                             "sample": f"{sample} instances, dense k x k LU solve (one factorisation)",
                             "seconds": dt, "rel_l2_gpu_fp32_vs_oracle": rel},

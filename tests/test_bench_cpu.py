@@ -6,6 +6,7 @@ import subprocess
 import sys
 
 import numpy as np
+import pytest
 
 import oracle as O
 import workloads as W
@@ -75,3 +76,22 @@ def test_reference_arm_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 
+
+
+def test_cpu_baseline_leg():
+    # the bench's cpu_baseline object on a small shared-support batch, with the
+    # oracle's own output standing in for the GPU rows
+    import torch
+    inst, _ = W.workload_shared(M=12, s=6, batch=1, coeffs=False)
+    rng = np.random.default_rng(72)
+    F = W.complex_gaussian((32, inst.k), rng)
+    Jc = O.canonical_support_by_key(inst.J, inst.pivots)
+    C = O.transform_levels(inst.M, inst.pivots, Jc, F)
+    x32 = torch.from_numpy(F.astype(np.complex64))
+    y32 = torch.from_numpy(C.astype(np.complex64))
+    d = bench.cpu_baseline(inst, x32, y32, 4)
+    assert d["kind"] == "oracle" and d["unit"] == bench.UNIT and d["cores"] >= 1
+    assert d["passes"] >= 3 and d["value"] == pytest.approx(32 * inst.k / d["seconds"])
+    assert d["rel_l2_gpu_fp32_vs_oracle"] < 1e-6
+    assert d["dense_solve"]["rel_l2_gpu_fp32_vs_oracle"] < 1e-6
+    assert d["alg1_numpy"]["rel_l2_gpu_fp32_vs_oracle"] < 1e-6
