@@ -31,6 +31,12 @@ def _current_stream(stream):
     return torch.cuda.current_stream().cuda_stream
 
 
+def _numel(t, what: str) -> int:
+    if not isinstance(t, _torch().Tensor):
+        raise TypeError(f"{what} must be a torch tensor")
+    return t.numel()
+
+
 def _check_tensor(t, dtype, numel: int, what: str):
     torch = _torch()
     if not isinstance(t, torch.Tensor):
@@ -100,7 +106,7 @@ class Plan:
     def execute_strided(self, samples, coeffs=None, stream=None, batch: Optional[int] = None):
         """`batch` packed instances (samples shaped [batch, k] or flat)."""
         if batch is None:
-            batch = samples.numel() // self.k
+            batch = _numel(samples, "samples") // self.k
         _check_tensor(samples, self.dtype, batch * self.k, "samples")
         if coeffs is None:
             coeffs = _torch().empty_like(samples)
@@ -126,7 +132,7 @@ class Plan:
     def _host(self, fn, h_in, h_out, d_in, d_out, chunk, stream, batch):
         torch = _torch()
         if batch is None:
-            batch = h_in.numel() // self.k
+            batch = _numel(h_in, "host input") // self.k
         for t, what in ((h_in, "host input"), (h_out, "host output")):
             if t is None:
                 continue
@@ -150,7 +156,7 @@ class Plan:
         """Coefficients from canonical order into the order of J as given to the
         plan (plans created with user_order=True)."""
         if batch is None:
-            batch = coeffs.numel() // self.k
+            batch = _numel(coeffs, "coeffs") // self.k
         _check_tensor(coeffs, self.dtype, batch * self.k, "coeffs")
         if out is None:
             out = _torch().empty_like(coeffs)
@@ -161,7 +167,7 @@ class Plan:
     def synthesize(self, coeffs, samples=None, stream=None, batch: Optional[int] = None):
         """Samples from coefficients (the inverse of execute_strided)."""
         if batch is None:
-            batch = coeffs.numel() // self.k
+            batch = _numel(coeffs, "coeffs") // self.k
         _check_tensor(coeffs, self.dtype, batch * self.k, "coeffs")
         if samples is None:
             samples = _torch().empty_like(coeffs)
@@ -176,7 +182,7 @@ class Plan:
     def autotune(self, samples, coeffs=None, stream=None, reps: int = 5):
         """Time both strategies on these buffers, keep the faster; returns
         (strategy name, ms levels, ms queue)."""
-        batch = samples.numel() // self.k
+        batch = _numel(samples, "samples") // self.k
         _check_tensor(samples, self.dtype, batch * self.k, "samples")
         if coeffs is None:
             coeffs = _torch().empty_like(samples)
@@ -330,6 +336,7 @@ class Sas:
     def execute(self, samples, coeffs=None, work=None, stream=None):
         """samples: (batch, mu* x 2^R) or (mu* x 2^R,) device tensor; returns (batch, k)."""
         torch = _torch()
+        _numel(samples, "samples")
         x = samples.reshape(-1, self.n_samples)
         batch = x.shape[0]
         _check_tensor(x, self.dtype, batch * self.n_samples, "samples")

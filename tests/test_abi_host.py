@@ -160,6 +160,30 @@ def test_host_only_plan_refuses_execution():
         N.sdft_plan_destroy(h)
 
 
+def test_host_tensors_are_refused_not_computed():
+    # no host fallback: every execute entry point of the binding refuses tensors
+    # in host memory before anything runs, and host-only objects refuse to run
+    import torch
+    from paper_2211_15299_gb300 import Plan, Sas, SdftError, execute_batched
+    p = Plan(10, [0, 1, 2, 3], host_only=True)
+    x = torch.zeros(4, dtype=torch.complex64)
+    for call in (lambda: p.execute(x), lambda: p.execute_strided(x), lambda: p.synthesize(x),
+                 lambda: p.to_user_order(x)):
+        with pytest.raises(ValueError, match="CUDA device"):
+            call()
+    with pytest.raises(TypeError):
+        p.execute_strided(x.numpy())
+    with pytest.raises(TypeError, match="CUDA int64"):
+        execute_batched([p], x, torch.tensor([0, 4]))
+    sas = Sas(10, [0, 1, 2, 5, 7], host_only=True)
+    with pytest.raises(ValueError, match="CUDA device"):
+        sas.execute(torch.zeros(sas.n_samples, dtype=torch.complex64))
+    h = torch.zeros(4, dtype=torch.complex64).pin_memory() if torch.cuda.is_available() else None
+    if h is not None:
+        with pytest.raises(SdftError):
+            p.execute_host(h)
+
+
 def test_plan_tables_match_oracle():
     from paper_2211_15299_gb300 import Plan
     rng = np.random.default_rng(31)
