@@ -22,8 +22,10 @@ namespace {
 thread_local int g_last_cuda_error = 0;
 std::mutex g_mu;
 std::set<std::pair<int, const void*>> g_smem_set;
-int g_sm_count[64] = {0};
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+// Filled once and read from any thread (the caller's, a server's worker and
+// planners): atomics, so the first-use checks below are race-free.
+std::atomic<int> g_sm_count[64];            // static storage: zero-initialised
+std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 }  // namespace
@@ -45,10 +47,10 @@ uint64_t wait_timeout_ns() {
 int sm_count() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-  int v = g_sm_count[dev];
+  int v = g_sm_count[dev].load(std::memory_order_relaxed);
   if (v == 0) {
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
-    g_sm_count[dev] = v;
+    g_sm_count[dev].store(v, std::memory_order_relaxed);
   }
   return v;
 }
@@ -67,24 +69,27 @@ sdft_status ensure_smem(const void* fn, int bytes) {
 
 sdft_status encode_map(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides[3],
                        const uint32_t box[4]) {
-  if (!g_encode) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = g_encode.load(std::memory_order_acquire);
+  if (!encode) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_encode) {
+    encode = g_encode.load(std::memory_order_acquire);
+    if (!encode) {
       void* fn = nullptr;
       cudaDriverEntryPointQueryResult q;
       const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                                              cudaEnableDefault, &q);
       if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cuda_fail(e);
-      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+      g_encode.store(encode, std::memory_order_release);
     }
   }
   cuuint64_t gdim[4] = {dims[0], dims[1], dims[2], dims[3]};
   cuuint64_t gstr[3] = {strides[0], strides[1], strides[2]};
   cuuint32_t bdim[4] = {box[0], box[1], box[2], box[3]};
   cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), gdim, gstr, bdim,
-                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), gdim, gstr, bdim,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     g_last_cuda_error = int(r);
     return SDFT_ERR_CUDA;
