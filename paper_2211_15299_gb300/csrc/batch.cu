@@ -548,7 +548,11 @@ sdft_status run_strided_queue(sdft_plan_s* plan, uint64_t batch, const void* in,
       if (q->entries.size() >= kStridedQueueCache) {
         // The oldest queue may still be in use by work in flight: synchronise first.
         cudaError_t e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) return cuda_fail(e);
+        if (e != cudaSuccess) {
+          free_batch(*b);
+          delete b;
+          return cuda_fail(e);
+        }
         free_batch(*q->entries.front().second);
         delete q->entries.front().second;
         q->entries.erase(q->entries.begin());

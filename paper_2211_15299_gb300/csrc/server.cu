@@ -24,6 +24,7 @@
 #include <functional>
 #include <mutex>
 #include <new>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -605,8 +606,23 @@ sdft_status sdft_server_create(sdft_prec prec, uint64_t budget_bytes, uint32_t n
     return st;
   }
   S.stats.arena_bytes = S.budget;
-  S.worker = std::thread(worker_loop, &S);
-  for (uint32_t i = 0; i < n_planners; ++i) S.planners.emplace_back(planner_loop, &S);
+  try {
+    S.worker = std::thread(worker_loop, &S);
+    for (uint32_t i = 0; i < n_planners; ++i) S.planners.emplace_back(planner_loop, &S);
+  } catch (const std::system_error&) {   // no thread: stop the ones started, as destroy does
+    {
+      std::lock_guard<std::mutex> lk(S.mu);
+      S.stop = true;
+    }
+    S.plan_cv.notify_all();
+    for (std::thread& t : S.planners)
+      if (t.joinable()) t.join();
+    S.cv.notify_one();
+    if (S.worker.joinable()) S.worker.join();
+    free_server(&S);
+    delete h;
+    return SDFT_ERR_NOMEM;
+  }
   *out = h;
   return SDFT_OK;
 }
