@@ -166,7 +166,8 @@ sdft_status sdft_execute_strided(sdft_plan plan, uint64_t batch, const void* d_s
  * itself runs the transforms and, when the call returns, has been made to wait
  * for the last copy-out, so synchronising `stream` (or an event recorded on it
  * afterwards) covers the whole call. Calls on one plan are serialised while
- * they enqueue; graph capture of `stream` captures the fork and join. Errors:
+ * they enqueue; graph capture of `stream` captures the fork and join. All
+ * arguments, host and device, are checked before anything is enqueued. Errors:
  * SDFT_ERR_ARG, SDFT_ERR_NO_DEVICE, SDFT_ERR_CUDA, and those of
  * sdft_execute_strided.
  */

@@ -366,6 +366,11 @@ static sdft_status run_host(sdft_plan plan, uint64_t batch, const void* h_in_buf
     const uintptr_t a = reinterpret_cast<uintptr_t>(h_samples), b = reinterpret_cast<uintptr_t>(h_coeffs);
     if (a != b && a < b + total && b < a + total) return SDFT_ERR_ARG;   // host buffers: identical or disjoint
   }
+  {  // the device side too, before anything is enqueued
+    sdft_status s0 = sdft::check_device(p);
+    if (s0 == SDFT_OK) s0 = sdft::check_buffers(d_samples, d_coeffs, total);
+    if (s0 != SDFT_OK) return s0;
+  }
   // chunks of about 16 MiB, each a multiple of 16 bytes so that every chunk's
   // device offset keeps the 16-byte alignment of the buffers
   const uint64_t unit = inst_bytes >= 16 ? 1 : 16 / inst_bytes;
