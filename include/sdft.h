@@ -264,7 +264,10 @@ sdft_status sdft_plan_autotune(sdft_plan plan, uint64_t batch, const void* d_sam
  * device; clears the word when `clear` is non-zero. */
 sdft_status sdft_plan_device_status(sdft_plan plan, int clear);
 
-/* Release a plan. The caller must first synchronise any work using it. */
+/* Release a plan: its tables, status word, cached work queues and host-copy
+ * streams, and every cached sdft_execute_batched list that names it. The caller
+ * must first synchronise any work using it; batches (sdft_batch_*) built on it
+ * must be destroyed first. */
 sdft_status sdft_plan_destroy(sdft_plan plan);
 
 /* ------------------------------------------------------------------------ */
