@@ -266,8 +266,8 @@ sdft_status sdft_plan_device_status(sdft_plan plan, int clear);
 
 /* Release a plan: its tables, status word, cached work queues and host-copy
  * streams, and every cached sdft_execute_batched list that names it. The caller
- * must first synchronise any work using it; batches (sdft_batch_*) built on it
- * must be destroyed first. */
+ * must first synchronise any work using it; a batch (sdft_batch_*) built on it
+ * must not run afterwards. */
 sdft_status sdft_plan_destroy(sdft_plan plan);
 
 /* ------------------------------------------------------------------------ */
