@@ -48,3 +48,20 @@ def test_large_pivots():
     F = W.complex_gaussian((2, 1 << s), rng)
     got, _ = alg1.alg1_batch(M, piv, Jc, F)
     assert rel_l2(got, O.transform_levels(M, piv, Jc, F)) < 1e-12
+
+
+@pytest.mark.parametrize("M,s", [(30, 10), (40, 6), (62, 8)])
+def test_large_N_against_closed_form(M, s):
+    # at large N the C oracle's twiddles (angles 2 pi rho / 2^(r+1) with r up to
+    # 61) must still give c_j = (N/k) sum_i f(i) exp(-2 pi i (i j mod N) / N)
+    rng = np.random.default_rng(500 + M)
+    piv = W.random_pivots(M, s, rng)
+    J = W.homogeneous_support(M, piv, rng)
+    Jc = O.canonical_support_by_key(J, piv)
+    F = W.complex_gaussian((2, 1 << s), rng)
+    got, _ = alg1.alg1_batch(M, piv, Jc, F, threads=2)
+    I = O.sample_set(M, piv)
+    pick = rng.choice(1 << s, size=8, replace=False)
+    for b in range(2):
+        ref = O.coefficients_at(M, Jc[pick], I, F[b])
+        assert rel_l2(got[b][pick], ref) < 1e-12
