@@ -388,7 +388,8 @@ typedef struct sdft_sas_s* sdft_sas;
  *           "part-H-tree"). 0 chooses R: the smallest operation count of
  *           Lemma "computation_shift_sample" (1.5 R 2^R mu* + 6 sum_v mu(v)^2)
  *           among R whose class systems have 1-norm condition <= 32
- *           (complex64) or <= 1000 (complex128), else the best-conditioned R.
+ *           (complex64) or <= 100 (complex128), else the best-conditioned R;
+ *           under these caps results stay within 1e-5 / 1e-12 (relative L2).
  *   flags : 0, SDFT_PLAN_HOST_ONLY (planning only; cannot execute), and/or
  *           SDFT_SAS_TWO_STAGE (see sdft_sas_execute).
  * The classes of J modulo 2^(r_max+1) hold mu(v) <= mu* <= 64 members. The

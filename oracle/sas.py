@@ -34,7 +34,7 @@ from typing import Dict, List, Sequence
 
 import numpy as np
 
-from .fp64 import pivots_by_tree, sample_set, transform_levels
+from .fp64 import hidft, pivots_by_tree, sample_set, transform_levels
 
 
 def split_levels(J: Sequence[int], M: int) -> List[int]:
@@ -114,25 +114,84 @@ def _z_powers(M: int, members: Sequence[int], mu: int) -> np.ndarray:
     return np.exp(2j * np.pi * p / N)
 
 
-def sas_node_values(M: int, J: Sequence[int], r: Sequence[int], F_shift) -> np.ndarray:
+def sas_node_values(M: int, J: Sequence[int], r: Sequence[int], F_shift,
+                    counter: Dict[str, int] = None) -> np.ndarray:
     """Step 1: (mu*, 2^R) values; row a is the Hi-DFT (with the N/2^R scale) of
-    the samples at I_r + a over the virtual support, in key order."""
+    the samples at I_r + a over the virtual support, in key order.
+
+    `counter` (optional): each row then runs the recursive Algorithm 1 (`hidft`)
+    and the counter accumulates "transforms" (one per shift) and
+    "transform_ops", 3 operations per butterfly (one complex product and two
+    complex sums, the accounting of Theorem "computation_Hi-DFT"'s proof, which
+    gives c1 n 2^n with c1 = 3/2 for a transform of 2^n values)."""
     V = virtual_support(J, M, r)
     F_shift = np.asarray(F_shift, dtype=np.complex128)
-    return np.stack([transform_levels(M, r, V, F_shift[a]) for a in range(F_shift.shape[0])])
+    if counter is None:
+        return np.stack([transform_levels(M, r, V, F_shift[a]) for a in range(F_shift.shape[0])])
+    scale = float(2.0 ** (M - len(r)))
+    rows = []
+    for a in range(F_shift.shape[0]):
+        local: Dict[str, int] = {}
+        rows.append(scale * hidft(F_shift[a], r, V, M, local))
+        counter["transforms"] = counter.get("transforms", 0) + 1
+        counter["transform_ops"] = counter.get("transform_ops", 0) + 3 * local.get("butterflies", 0)
+    return np.stack(rows)
 
 
-def sas_transform(M: int, J: Sequence[int], r: Sequence[int], F_shift) -> np.ndarray:
+def vandermonde_solve(z, y, counter: Dict[str, int] = None) -> np.ndarray:
+    """x with sum_u x_u z_u^a = y_a for a = 0 .. mu - 1 (the class system of eq.
+    "alg1_system", A[a, u] = z_u^a), in O(mu^2) operations by the elimination of
+    Bjorck and Pereyra (Math. Comp. 24, 1970) for this "primal" system: first
+    mu - 1 sweeps y_i <- y_i - z_k y_{i-1} (i from the bottom up to k + 1), then,
+    for k from mu - 2 down to 0, y_i <- y_i / (z_i - z_{i-k-1}) for i > k and
+    y_i <- y_i - y_{i+1} for k <= i < mu - 1. Exact in exact arithmetic for
+    distinct z (the paper cites fast Vandermonde solvers for its c2 mu^2 term).
+
+    `counter` (optional) accumulates "solve_ops": one per complex product,
+    quotient, sum or difference, 5 mu (mu - 1) / 2 in all (5 for a 2 x 2
+    system, 0 for a class of one)."""
+    z = np.asarray(z, dtype=np.complex128)
+    x = np.array(y, dtype=np.complex128)
+    n = z.size
+    ops = 0
+    for k in range(n - 1):
+        for i in range(n - 1, k, -1):
+            x[i] = x[i] - z[k] * x[i - 1]
+            ops += 2
+    for k in range(n - 2, -1, -1):
+        for i in range(k + 1, n):
+            x[i] = x[i] / (z[i] - z[i - k - 1])
+            ops += 2
+        for i in range(k, n - 1):
+            x[i] = x[i] - x[i + 1]
+            ops += 1
+    if counter is not None:
+        counter["solve_ops"] = counter.get("solve_ops", 0) + ops
+    return x
+
+
+def sas_transform(M: int, J: Sequence[int], r: Sequence[int], F_shift,
+                  counter: Dict[str, int] = None) -> np.ndarray:
     """Steps 1-2: the coefficients c_j for j in J, in the order J is given.
-    F_shift[a] holds f at I_r + a (sample order), a = 0 .. mu* - 1."""
-    Y = sas_node_values(M, J, r, F_shift)
+    F_shift[a] holds f at I_r + a (sample order), a = 0 .. mu* - 1.
+
+    Without `counter` each class system is solved by LU with partial pivoting
+    (a library solve). With `counter` the run is instrumented: step 1 counts as
+    in `sas_node_values`, each class is solved by `vandermonde_solve` (counting
+    "solve_ops"), and "solve_mu2" accumulates mu(v)^2 over the classes solved,
+    so the count can be set beside Lemma "computation_shift_sample"."""
+    Y = sas_node_values(M, J, r, F_shift, counter)
     coeff = {}
     for t, members in sas_nodes(J, r).items():
         mu = len(members)
         if mu > Y.shape[0]:
             raise ValueError("fewer shifts than the largest class")
-        A = _z_powers(M, members, mu)
-        x = np.linalg.solve(A, Y[:mu, t])
+        if counter is None:
+            A = _z_powers(M, members, mu)
+            x = np.linalg.solve(A, Y[:mu, t])
+        else:
+            x = vandermonde_solve(_z_powers(M, members, 2)[1], Y[:mu, t], counter)
+            counter["solve_mu2"] = counter.get("solve_mu2", 0) + mu * mu
         for l, v in zip(members, x):
             coeff[l] = v
     return np.asarray([coeff[int(j)] for j in J], dtype=np.complex128)
@@ -154,6 +213,8 @@ def sas_samples_direct(M: int, J: Sequence[int], c, idx) -> np.ndarray:
 
 def sas_cost(R: int, mu: Dict[int, int]) -> float:
     """Operation count of steps 1-2 by Lemma "computation_shift_sample":
-    c1 R 2^R mu* + c2 sum_v mu(v)^2 with c1 = 3/2, c2 = 6."""
+    c1 R 2^R mu* + c2 sum_v mu(v)^2 with c1 = 3/2, c2 = 6. The first term is the
+    count an instrumented `sas_transform` makes of its mu* transforms; the
+    second bounds the count of its O(mu^2) class solves (`vandermonde_solve`)."""
     mu_star = max(mu.values()) if mu else 0
     return 1.5 * R * (1 << R) * mu_star + 6.0 * sum(m * m for m in mu.values())

@@ -230,24 +230,95 @@ def test_union_of_homogeneous_alias_bound(base):
         assert rel_l2(got, c) < 1e-14 * max(conds) + 1e-12
 
 
-@pytest.mark.parametrize("sizes", [(8, 8), (5, 6, 7), (16, 3)])
-def test_generalized_progressions_have_few_pivots(sizes):
-    # Lemma "gap-complexity", eq. "gap-pivot-bound": a proper GAP of dimension d
-    # with n split levels satisfies 2^n <= n^d 2^d |J|; SAS recovers its coefficients
-    d = len(sizes)
-    for seed in range(4):
-        rng = W.rng_for(0, 7000 + 17 * seed + sum(sizes))
-        M = 20
-        J = [int(j) for j in W.generalized_arithmetic_progression(M, sizes, rng)]
-        n = len(O.split_levels(J, M))
-        assert 2 ** n <= n ** d * 2 ** d * len(J), (n, len(J))
-    c = W.complex_gaussian(len(J), rng)
-    levels = O.split_levels(J, M)
-    R = min(len(levels), int(np.ceil(np.log2(len(J)))) + 1)
+# ---- operation counts: Lemma "computation_shift_sample" and the worked example ----
+
+def _golden_opcount():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "sas_example_sec9_opcount.txt")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = [x.strip() for x in line.split("|")]
+            rows.append((int(f[0]), [int(x) for x in f[1].split()], int(f[2]), int(f[3]), int(f[4]),
+                         int(f[5]), int(f[6])))
+    return rows
+
+
+def _counted(M, J, R, c):
     r = O.sas_pivots(J, M, R)
     mu = O.sas_mu(J, r)
     idx = O.sas_sample_sets(M, r, max(mu.values()))
-    F = O.sas_samples_direct(M, J, c, idx)
-    got = O.sas_transform(M, J, r, F)
-    conds = [np.linalg.cond(O.sas.__dict__["_z_powers"](M, m, len(m))) for m in O.sas_nodes(J, r).values()]
-    assert rel_l2(got, c) < 1e-14 * max(conds) + 1e-12
+    f = _full_signal(M, J, c)
+    cnt = {}
+    got = O.sas_transform(M, J, r, f[idx.astype(np.int64)], counter=cnt)
+    return r, mu, idx, got, cnt
+
+
+def test_worked_example_operation_count_is_the_papers():
+    # Section IX: two size-4 Hi-DFTs at 12 operations each, one 2 x 2 system at
+    # 5 operations: 29 operations, 8 samples (tests/golden/sas_example_sec9_opcount.txt)
+    for M, J, R, t_ops, s_ops, total, samples in _golden_opcount():
+        c = W.complex_gaussian(len(J), np.random.default_rng(5))
+        r, mu, idx, got, cnt = _counted(M, J, R, c)
+        assert cnt["transform_ops"] == t_ops
+        assert cnt["solve_ops"] == s_ops
+        assert cnt["transform_ops"] + cnt["solve_ops"] == total
+        assert idx.size == samples
+        assert rel_l2(got, c) < 1e-12
+
+
+def test_vandermonde_solve_against_a_library_solve():
+    # the O(mu^2) class solve equals an LU solve of the same system and leaves
+    # no residual; 5 mu (mu - 1) / 2 operations
+    rng = np.random.default_rng(17)
+    for mu in range(1, 9):
+        for _ in range(5):
+            M = int(rng.integers(mu.bit_length() + 2, 14))
+            members = sorted(int(x) for x in rng.choice(1 << M, size=mu, replace=False))
+            A = O.sas.__dict__["_z_powers"](M, members, mu)
+            y = W.complex_gaussian(mu, rng)
+            cnt = {}
+            z = O.sas.__dict__["_z_powers"](M, members, 2)[1]       # z_u = exp(2 pi i l_u / N)
+            x = O.vandermonde_solve(z, y, cnt)
+            ref = np.linalg.solve(A, y)
+            cond = np.linalg.cond(A)
+            assert rel_l2(x, ref) < 1e-12 * cond + 1e-14, (mu, cond)
+            assert rel_l2(A @ x, y) < 1e-12 * cond + 1e-14
+            assert cnt["solve_ops"] == 5 * mu * (mu - 1) // 2
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_lemma_count_matches_the_instrumented_run(seed):
+    # Lemma "computation_shift_sample": the mu* transforms of 2^R values cost
+    # c1 R 2^R mu* (c1 = 3/2, counted butterfly by butterfly), the class solves
+    # at most c2 sum mu(v)^2 (c2 = 6; the O(mu^2) solver needs 5 mu (mu - 1) / 2);
+    # sas_cost adds exactly these two terms for the classes the run solved
+    rng = np.random.default_rng(300 + seed)
+    M = int(rng.integers(7, 12))
+    k = int(rng.integers(4, 60))
+    J = sorted(int(x) for x in rng.choice(1 << M, size=k, replace=False))
+    c = W.complex_gaussian(k, rng)
+    levels = O.split_levels(J, M)
+    for R in range(max(1, len(levels) - 3), len(levels) + 1):
+        r, mu, idx, got, cnt = _counted(M, J, R, c)
+        mu_star = max(mu.values())
+        assert cnt["transforms"] == mu_star
+        assert cnt["transform_ops"] == 1.5 * R * (1 << R) * mu_star
+        assert cnt["solve_mu2"] == sum(m * m for m in mu.values())
+        assert cnt["solve_ops"] <= 6 * cnt["solve_mu2"]
+        assert O.sas_cost(R, mu) == cnt["transform_ops"] + 6 * cnt["solve_mu2"]
+        # the instrumented run computes the same coefficients as the plain one
+        plain = O.sas_transform(M, J, r, _full_signal(M, J, c)[idx.astype(np.int64)])
+        conds = [np.linalg.cond(O.sas.__dict__["_z_powers"](M, m, len(m))) for m in O.sas_nodes(J, r).values()]
+        assert rel_l2(got, plain) < 1e-12 * max(conds) + 1e-13
+
+
+def test_planted_constant_mistake_fails_the_worked_example():
+    # c1 = 2 (the alternative the lemma's proof mentions) would give 16 operations
+    # per size-4 transform and 37 in all, not the paper's 29
+    M, J, R, t_ops, s_ops, total, samples = _golden_opcount()[0]
+    mu = O.sas_mu(J, O.sas_pivots(J, M, R))
+    mu_star = max(mu.values())
+    wrong = 2.0 * R * (1 << R) * mu_star + s_ops
+    assert wrong != total
+    assert 1.5 * R * (1 << R) * mu_star + s_ops == total

@@ -88,3 +88,24 @@ def test_sas_errors():
     with pytest.raises(SdftError) as ei:
         _sas(6, [0, 1, 2, 3], R=5)               # only 2 split levels
     assert ei.value.name == "SDFT_ERR_ARG"
+
+
+def test_random_subset_at_the_theorems_pivot_count():
+    # Theorem "hom_rand_subset": with n = floor(log2 k - log2 log2 k) pivots of the
+    # homogeneous set K, the planner takes K's first n pivots and the classes
+    # stay below Lemma "bound_mu_r_star"'s bound. The class systems there are
+    # ill-conditioned (exact arithmetic is assumed by the theorem), so numeric
+    # parity runs on the planner's own R (tests/test_gpu_sas.py).
+    log2k = 10
+    rng = W.rng_for(0, 4321)
+    J, piv = W.bernoulli_subset_of_homogeneous(18, log2k + 3, 1 << log2k, rng)
+    n = int(np.floor(log2k - np.log2(log2k)))
+    for prec in ("c64", "c128"):
+        from paper_2211_15299_gb300 import Sas
+        p = Sas(18, [int(j) for j in J], prec, R=n, host_only=True)
+        assert [int(x) for x in p.pivots] == [int(x) for x in piv[:n]]
+        r = O.sas_pivots([int(j) for j in J], 18, n)
+        assert p.mu_star == max(O.sas_mu([int(j) for j in J], r).values())
+        assert p.mu_star < (4 + 3 * np.log(2)) * log2k
+        auto = Sas(18, [int(j) for j in J], prec, host_only=True)
+        assert auto.max_cond <= (32.0 if prec == "c64" else 100.0)

@@ -259,21 +259,3 @@ def union_of_homogeneous(M: int, l: Sequence[int], etas: Sequence[int], K_rng: n
             parts.append(np.sort(K[sel]))
     J = np.unique(np.concatenate(parts)).astype(np.uint64)
     return J, parts
-
-
-def generalized_arithmetic_progression(M: int, sizes: Sequence[int], rng: np.random.Generator,
-                                       max_tries: int = 100) -> np.ndarray:
-    """A proper GAP {a + sum_i n_i s_i : 0 <= n_i < sizes[i]} in Z_N (Definition
-    "gap") with a uniform start and random differences, redrawn until all
-    prod(sizes) sums are distinct."""
-    N = 1 << M
-    k = int(np.prod(sizes))
-    for _ in range(max_tries):
-        a = int(rng.integers(0, N))
-        steps = [int(rng.integers(1, N)) for _ in sizes]
-        J = np.zeros(1, dtype=np.int64) + a
-        for n_i, s_i in zip(sizes, steps):
-            J = (J[:, None] + (np.arange(n_i, dtype=np.int64) * s_i)[None, :]).reshape(-1) % N
-        if np.unique(J).size == k:
-            return np.sort(J).astype(np.uint64)
-    raise ValueError("no proper progression found")
