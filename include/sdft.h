@@ -198,9 +198,13 @@ sdft_status sdft_plan_to_user_order(sdft_plan plan, uint64_t batch, const void* 
  * a gather into the batch's own packing and a scatter back; the first call for a
  * given list of plans builds that batch and its staging buffers (2 x total
  * values) and caches them (allocates and may synchronise the device: make that
- * call before capturing a graph; the 8 most recent lists are kept, and
- * sdft_plan_destroy of any plan in a list frees that list's batch); calls with
- * the same list must not overlap on the GPU. sdft_batch_execute on the batch's own layout saves the two copies.
+ * call before capturing a graph). The 8 most recently built unpinned lists are
+ * kept: building a ninth frees the oldest unpinned one, and a CUDA graph
+ * captured on a freed list would replay on freed memory, so pin every list a
+ * graph is captured on (sdft_execute_batched_pin). sdft_plan_destroy of any
+ * plan in a list frees that list, pinned or not. Calls with the same list must
+ * not overlap on the GPU. sdft_batch_execute on the batch's own layout saves
+ * the two copies.
  * Offsets that do not match the plans' k are reported as 0x104 in the status
  * word of plans[0] (sdft_plan_device_status) and those instances are skipped;
  * offsets must lie inside the caller's buffers. Buffers 16-byte aligned,
@@ -210,6 +214,23 @@ sdft_status sdft_plan_to_user_order(sdft_plan plan, uint64_t batch, const void* 
  */
 sdft_status sdft_execute_batched(const sdft_plan* plans, uint64_t n, const void* d_samples,
                                  const uint64_t* d_offsets, void* d_coeffs, void* stream);
+
+/*
+ * sdft_execute_batched_pin - pin != 0: build (if not cached yet; allocates and
+ * may synchronise the device) and pin the cached list of these plans, so that
+ * building other lists never frees it; pin == 0: unpin it (it becomes the
+ * candidate for eviction it would have been by age; nothing is built). Pinned
+ * lists do not count toward the 8 kept unpinned lists. Plans as for
+ * sdft_execute_batched. Errors: SDFT_ERR_ARG, SDFT_ERR_NO_DEVICE,
+ * SDFT_ERR_PRECISION, SDFT_ERR_NOMEM, SDFT_ERR_CUDA.
+ * sdft_execute_batched_cache_info - whether the list of these plans is cached
+ * and pinned (0 or 1; plans may be NULL with n = 0), and the number of cached
+ * lists (any output may be NULL). Host-only, no device work.
+ * The paper has no counterpart: these manage the library's own cache.
+ */
+sdft_status sdft_execute_batched_pin(const sdft_plan* plans, uint64_t n, int pin);
+sdft_status sdft_execute_batched_cache_info(const sdft_plan* plans, uint64_t n, int* cached, int* pinned,
+                                            uint64_t* n_lists);
 
 /* The same for synthesis (sdft_synthesize_strided): h_coeffs in, h_samples out,
  * through the device buffers d_coeffs and d_samples. */
@@ -238,10 +259,13 @@ sdft_status sdft_synthesize_strided(sdft_plan plan, uint64_t batch, const void* 
  *     later-level tiles follow their instance's previous level, so the
  *     intermediate is read back from L2; the first call with a given batch size
  *     builds and caches the queue (allocates: make that call before capturing
- *     a CUDA graph). The cached queue's dependency counters are shared, so
- *     with this strategy calls on one plan with the same batch size must not
- *     overlap on the GPU (the default strategy has no such state). Single-level
- *     plans ignore the strategy. */
+ *     a CUDA graph). A plan keeps the queues of its 4 most recent batch sizes:
+ *     a fifth size synchronises the device and frees the oldest, and a CUDA
+ *     graph captured on a freed queue must not be replayed. The cached
+ *     queue's dependency counters are shared, so with this strategy calls on
+ *     one plan with the same batch size must not overlap on the GPU (the
+ *     default strategy has no such state). Single-level plans ignore the
+ *     strategy. */
 typedef enum { SDFT_STRATEGY_LEVELS = 1, SDFT_STRATEGY_QUEUE = 2 } sdft_strategy;
 sdft_status sdft_plan_set_strategy(sdft_plan plan, sdft_strategy strategy);
 
@@ -298,7 +322,12 @@ sdft_status sdft_batch_info(sdft_batch batch, uint64_t* total, uint64_t* offsets
  * aligned, identical (in place) or disjoint. Asynchronous, allocates nothing,
  * and may be captured into a CUDA graph. A launch uses the batch's dependency
  * counters: launches of one batch must not overlap on the GPU (one stream, or
- * one batch per stream).
+ * one batch per stream). The launch is cooperative: CTA c takes items c,
+ * c + G, ... and later-level items wait for tiles of other CTAs, so it relies
+ * on all G CTAs being resident. By default G is every co-resident CTA of the
+ * device; to run several batch launches at once on other streams, give them
+ * disjoint shares (sdft_batch_set_schedule's grid), else waits may run out
+ * (SDFT_ERR_TIMEOUT in the status word).
  */
 sdft_status sdft_batch_execute(sdft_batch batch, const void* d_samples, void* d_coeffs,
                                void* stream);
@@ -314,9 +343,9 @@ sdft_status sdft_batch_execute(sdft_batch batch, const void* d_samples, void* d_
  * 32-bit counters (256 KiB) built into the library, present on every device
  * that loads it until the process exits. Batches needing more counters (more
  * than 65536 multi-level instance levels) are rejected with
- * SDFT_ERR_UNSUPPORTED. The first call on a device looks up that array's
- * device address (with the device current); make that first call before any
- * stream capture. All calls share the array and it keeps the last call's
+ * SDFT_ERR_UNSUPPORTED. sdft_batch_create looks up that array's device address
+ * on the batch's device (with that device current) and keeps it in the batch,
+ * so this call does no lookup either. All calls share the array and it keeps the last call's
  * counts, so each call clears the part it uses first; calls whose work
  * overlaps on the GPU (other streams, other threads) race on it and must be
  * serialised by the caller. Buffers as for sdft_batch_execute.
@@ -534,6 +563,15 @@ int sdft_last_cuda_error(void);
 
 /* Library version, major * 10000 + minor * 100 + patch. */
 int sdft_version(void);
+
+/* Range checks of the debug build (compiled with SDFT_BOUNDS_CHECK=1): every
+ * TMA tile coordinate, twiddle-table range and work-queue record is checked
+ * before use; a violation is counted, recorded as 0x105 in the launch's status
+ * word and the access made harmless (no trap). *enabled = 1 in that build, 0
+ * otherwise (then *count = 0); *count = violations on the current device since
+ * the last clear (clear != 0 resets them). Synchronous. Outputs may be NULL.
+ * The paper has no counterpart: a checking aid of this library. */
+sdft_status sdft_debug_bounds_violations(int* enabled, uint64_t* count, int clear);
 
 #ifdef __cplusplus
 }

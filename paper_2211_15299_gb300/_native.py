@@ -64,6 +64,9 @@ SIGNATURES = {
     "sdft_execute_strided": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "sdft_execute_strided_host": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
     "sdft_execute_batched": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp]),
+    "sdft_execute_batched_pin": (c_int, [c_vp, c_u64, c_int]),
+    "sdft_debug_bounds_violations": (c_int, [ctypes.POINTER(c_int), P_u64, c_int]),
+    "sdft_execute_batched_cache_info": (c_int, [c_vp, c_u64, ctypes.POINTER(c_int), ctypes.POINTER(c_int), P_u64]),
     "sdft_plan_to_user_order": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "sdft_synthesize_strided_host": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
     "sdft_synthesize": (c_int, [c_vp, c_vp, c_vp, c_vp]),
@@ -224,6 +227,29 @@ def sdft_execute_batched(plans, d_samples, d_offsets, d_coeffs, stream=None) -> 
     arr = (c_vp * len(plans))(*[int(p) for p in plans])
     _check(_lib.sdft_execute_batched(arr, len(plans), _ptr(d_samples), _ptr(d_offsets), _ptr(d_coeffs),
                                      _stream(stream)), "sdft_execute_batched")
+
+
+def sdft_debug_bounds_violations(clear: bool = False):
+    """(enabled, count): range-check violations of the debug build on the current device."""
+    en, cnt = c_int(0), c_u64(0)
+    _check(_lib.sdft_debug_bounds_violations(ctypes.byref(en), ctypes.byref(cnt), 1 if clear else 0),
+           "sdft_debug_bounds_violations")
+    return bool(en.value), int(cnt.value)
+
+
+def sdft_execute_batched_pin(plans, pin: bool) -> None:
+    """Pin (build if needed) or unpin the cached sdft_execute_batched list of plans."""
+    arr = (c_vp * len(plans))(*[int(p) for p in plans])
+    _check(_lib.sdft_execute_batched_pin(arr, len(plans), 1 if pin else 0), "sdft_execute_batched_pin")
+
+
+def sdft_execute_batched_cache_info(plans=()):
+    """(cached, pinned, number of cached lists) for the list of plans."""
+    arr = (c_vp * len(plans))(*[int(p) for p in plans]) if len(plans) else None
+    cached, pinned, n = c_int(0), c_int(0), c_u64(0)
+    _check(_lib.sdft_execute_batched_cache_info(arr, len(plans), ctypes.byref(cached), ctypes.byref(pinned),
+                                                ctypes.byref(n)), "sdft_execute_batched_cache_info")
+    return bool(cached.value), bool(pinned.value), int(n.value)
 
 
 def sdft_synthesize_strided_host(plan: int, batch: int, h_coeffs, h_samples, d_coeffs, d_samples, chunk: int = 0,

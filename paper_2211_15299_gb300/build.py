@@ -24,6 +24,10 @@ LIB = os.path.join(LIBDIR, "libsdft.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+# SDFT_BOUNDS_CHECK=1 in the environment builds the debug library with range
+# checks in every kernel (see sdft_debug_bounds_violations in include/sdft.h).
+if os.environ.get("SDFT_BOUNDS_CHECK", "0") not in ("", "0"):
+    NVCC_FLAGS = NVCC_FLAGS + ["-DSDFT_BOUNDS_CHECK=1"]
 SOURCES = ["plan.cpp", "api.cu", "batch.cu", "level_f32.cu", "level_f64.cu", "queue_f32.cu", "queue_f64.cu", "server.cu",
            "sas.cu", "inverse_f32.cu", "inverse_f64.cu", "level_df.cu"]
 

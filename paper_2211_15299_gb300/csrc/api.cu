@@ -30,6 +30,15 @@ std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 }  // namespace
 
+#if SDFT_BOUNDS_CHECK
+// Readers of the per-translation-unit violation counters of the debug build.
+static std::vector<uint64_t (*)(int)>& violation_readers() {
+  static std::vector<uint64_t (*)(int)> v;
+  return v;
+}
+void register_violation_reader(uint64_t (*reader)(int clear)) { violation_readers().push_back(reader); }
+#endif
+
 sdft_status cuda_fail(cudaError_t e) {
   g_last_cuda_error = int(e);
   return SDFT_ERR_CUDA;
@@ -558,5 +567,23 @@ const char* sdft_status_string(sdft_status s) {
 int sdft_last_cuda_error(void) { return sdft::g_last_cuda_error; }
 
 int sdft_version(void) { return 100; }
+
+sdft_status sdft_debug_bounds_violations(int* enabled, uint64_t* count, int clear) {
+#if SDFT_BOUNDS_CHECK
+  uint64_t total = 0;
+  for (auto* r : sdft::violation_readers()) {
+    const uint64_t v = r(clear);
+    if (v == ~0ull) return SDFT_ERR_CUDA;
+    total += v;
+  }
+  if (enabled) *enabled = 1;
+  if (count) *count = total;
+#else
+  (void)clear;
+  if (enabled) *enabled = 0;
+  if (count) *count = 0;
+#endif
+  return SDFT_OK;
+}
 
 }  // extern "C"

@@ -56,6 +56,7 @@ struct Batch {
   std::vector<sdft_plan> plans;      // caller's order (the plans outlive the batch)
   int schedule = SDFT_SCHEDULE_AUTO; // item order (sdft_schedule)
   int grid_req = 0;                  // CTAs requested (0: every co-resident CTA)
+  uint32_t* noalloc_counters = nullptr;  // device address of the library's fixed counter array
 };
 
 }  // namespace sdft
@@ -397,6 +398,7 @@ static sdft_status encode_batch_maps(const Batch& B, const void* in, void* out, 
       const uint32_t box[4] = {32, 1u << m.r, 1, 1};
       sdft_status s = encode_map(&prm.maps[slot], m.load ? in : out, dims, strides, box);
       if (s != SDFT_OK) return s;
+      q_set_limits(prm, slot, dims);
     } else {
       const uint32_t Q = m.hi - m.lo;
       const uint64_t zs = B.total >> m.hi;
@@ -405,8 +407,12 @@ static sdft_status encode_batch_maps(const Batch& B, const void* in, void* out, 
       const uint32_t box[4] = {32, 1u << m.lg, 1u << Q, 1};
       sdft_status s = encode_map(&prm.maps[slot], out, dims, strides, box);
       if (s != SDFT_OK) return s;
+      q_set_limits(prm, slot, dims);
     }
   }
+  prm.a.n_counters = uint32_t(B.n_counters);
+  prm.a.n_insts = B.n;
+  prm.a.total = B.total;
   return SDFT_OK;
 }
 
@@ -449,24 +455,18 @@ static sdft_status run_batch(Batch& B, const void* in, void* out, cudaStream_t s
 constexpr uint64_t kNoAllocCounters = 65536;
 static __device__ __align__(256) uint32_t g_noalloc_counters[kNoAllocCounters];
 
-// Device address of the array for the current device, looked up once per
-// device (cudaGetSymbolAddress needs that device current). In host code the
-// array's name is only a host-side stand-in, so kernels get this address.
+// Device address of the array on the current device (cudaGetSymbolAddress needs
+// that device current). In host code the array's name is only a host-side
+// stand-in, so kernels get this address. It is looked up when a batch is
+// created (sdft_batch_create, which allocates anyway: with lazy module loading
+// the first lookup on a device loads this file's module) and kept in the
+// batch, so the execute call does no lookup; a batch does not outlive its
+// device context, so the address cannot go stale under it.
 static sdft_status noalloc_counters(uint32_t** out) {
-  static std::mutex mu;
-  static uint32_t* addr[64] = {nullptr};
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_counters);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (dev < 0 || dev >= 64) return SDFT_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_counters);
-    if (e != cudaSuccess) return cuda_fail(e);
-    addr[dev] = static_cast<uint32_t*>(p);
-  }
-  *out = addr[dev];
+  *out = static_cast<uint32_t*>(p);
   return SDFT_OK;
 }
 
@@ -482,9 +482,9 @@ static sdft_status run_batch_noalloc(const Batch& B, const void* in, void* out, 
   if (a != b && a < b + bytes && b < a + bytes) return SDFT_ERR_ARG;
   if (B.n_counters > kNoAllocCounters) return SDFT_ERR_UNSUPPORTED;
   if (B.items.empty()) return SDFT_OK;
-  uint32_t* counters = nullptr;
-  sdft_status s = noalloc_counters(&counters);
-  if (s != SDFT_OK) return s;
+  uint32_t* counters = B.noalloc_counters;
+  if (!counters) return SDFT_ERR_NO_DEVICE;
+  sdft_status s;
   QParams prm;
   std::memset(&prm, 0, sizeof(prm));
   s = encode_batch_maps(B, in, out, prm);
@@ -524,8 +524,11 @@ sdft_status run_strided_queue(sdft_plan_s* plan, uint64_t batch, const void* in,
   }
   StridedQueues* q = static_cast<StridedQueues*>(p.queues);
   Batch* b = nullptr;
+  // The lock covers the enqueue as well: another thread's eviction (below)
+  // synchronises the device before freeing a queue, which only protects work
+  // that has been enqueued already.
+  std::lock_guard<std::mutex> lk(q->mu);
   {
-    std::lock_guard<std::mutex> lk(q->mu);
     for (auto& e : q->entries)
       if (e.first == batch) b = e.second;
     if (!b) {
@@ -601,6 +604,7 @@ __global__ void __launch_bounds__(256) k_repack(const C* __restrict__ src, C* __
 
 struct BatchedEntry {
   std::vector<uint64_t> serials;
+  bool pinned = false;                 // never evicted implicitly (sdft_execute_batched_pin)
   Batch* b = nullptr;
   void* d_stage = nullptr;             // 2 x total values: samples, then coefficients
   uint64_t* d_k = nullptr;             // k per instance (caller order)
@@ -669,15 +673,24 @@ static sdft_status batched_entry(const sdft_plan* plans, uint64_t n, BatchedEntr
     free_batched(E);
     return e == cudaErrorMemoryAllocation ? SDFT_ERR_NOMEM : cuda_fail(e);
   }
-  if (g_batched.size() >= kBatchedCache) {
+  // Keep at most kBatchedCache unpinned lists: evict the oldest unpinned one.
+  // A CUDA graph captured on an evicted list would replay on freed memory, so
+  // lists that graphs were captured on must be pinned.
+  size_t unpinned = 0;
+  for (const auto& x : g_batched) unpinned += x.pinned ? 0 : 1;
+  if (unpinned >= kBatchedCache) {
     // the oldest entry may still be in use by work in flight: synchronise first
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
       free_batched(E);
       return cuda_fail(e);
     }
-    free_batched(g_batched.front());
-    g_batched.erase(g_batched.begin());
+    for (size_t i = 0; i < g_batched.size(); ++i)
+      if (!g_batched[i].pinned) {
+        free_batched(g_batched[i]);
+        g_batched.erase(g_batched.begin() + i);
+        break;
+      }
   }
   g_batched.push_back(std::move(E));
   *out = &g_batched.back();
@@ -713,6 +726,39 @@ sdft_status run_batched(const sdft_plan* plans, uint64_t n, const void* in, cons
                                             d_offsets, E->d_k, E->d_boff, E->d_items, E->n_items, status, 0);
   e = cudaGetLastError();
   return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
+}
+
+sdft_status pin_batched(const sdft_plan* plans, uint64_t n, int pin) {
+  std::lock_guard<std::mutex> lk(g_batched_mu);
+  if (!pin) {                          // unpin a cached list; nothing to build
+    std::vector<uint64_t> key(n);
+    for (uint64_t i = 0; i < n; ++i) key[i] = plans[i]->p.serial;
+    for (auto& E : g_batched)
+      if (E.serials == key) E.pinned = false;
+    return SDFT_OK;
+  }
+  BatchedEntry* E = nullptr;
+  sdft_status s = batched_entry(plans, n, &E);
+  if (s != SDFT_OK) return s;
+  E->pinned = true;
+  return SDFT_OK;
+}
+
+void batched_cache_info(const sdft_plan* plans, uint64_t n, int* cached, int* pinned, uint64_t* n_lists) {
+  std::lock_guard<std::mutex> lk(g_batched_mu);
+  int c = 0, p = 0;
+  if (plans && n) {
+    std::vector<uint64_t> key(n);
+    for (uint64_t i = 0; i < n; ++i) key[i] = plans[i]->p.serial;
+    for (const auto& E : g_batched)
+      if (E.serials == key) {
+        c = 1;
+        p = E.pinned ? 1 : 0;
+      }
+  }
+  if (cached) *cached = c;
+  if (pinned) *pinned = p;
+  if (n_lists) *n_lists = g_batched.size();
 }
 
 void forget_batched(uint64_t serial) {
@@ -773,6 +819,8 @@ sdft_status sdft_batch_create(const sdft_plan* plans, uint64_t n, sdft_batch* ou
   } catch (const std::bad_alloc&) {
     s = SDFT_ERR_NOMEM;
   }
+  // the allocation-free entry point's counter array: its address on this device
+  if (s == SDFT_OK && !host_only) s = sdft::noalloc_counters(&h->b.noalloc_counters);
   if (s != SDFT_OK) {
     sdft::free_batch(h->b);
     delete h;
@@ -820,6 +868,45 @@ sdft_status sdft_execute_batched(const sdft_plan* plans, uint64_t n, const void*
   } catch (const std::bad_alloc&) {
     return SDFT_ERR_NOMEM;
   }
+}
+
+// Argument checks shared by the calls that name a list of plans.
+static sdft_status check_plan_list(const sdft_plan* plans, uint64_t n) {
+  if (!plans || n == 0 || n > 0xffffffffull) return SDFT_ERR_ARG;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (!plans[i]) return SDFT_ERR_ARG;
+    if (plans[i]->p.deferred || plans[i]->p.device < 0) return SDFT_ERR_NO_DEVICE;
+    if (plans[i]->p.prec != plans[0]->p.prec) return SDFT_ERR_PRECISION;
+  }
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return sdft::cuda_fail(e);
+  for (uint64_t i = 0; i < n; ++i)
+    if (plans[i]->p.device != dev) return SDFT_ERR_ARG;
+  return SDFT_OK;
+}
+
+sdft_status sdft_execute_batched_pin(const sdft_plan* plans, uint64_t n, int pin) {
+  sdft_status s = check_plan_list(plans, n);
+  if (s != SDFT_OK) return s;
+  try {
+    return sdft::pin_batched(plans, n, pin);
+  } catch (const std::bad_alloc&) {
+    return SDFT_ERR_NOMEM;
+  }
+}
+
+sdft_status sdft_execute_batched_cache_info(const sdft_plan* plans, uint64_t n, int* cached, int* pinned,
+                                            uint64_t* n_lists) {
+  if ((plans == nullptr) != (n == 0)) return SDFT_ERR_ARG;
+  for (uint64_t i = 0; i < n; ++i)
+    if (!plans[i]) return SDFT_ERR_ARG;
+  try {
+    sdft::batched_cache_info(plans, n, cached, pinned, n_lists);
+  } catch (const std::bad_alloc&) {
+    return SDFT_ERR_NOMEM;
+  }
+  return SDFT_OK;
 }
 
 sdft_status sdft_batch_device_status(sdft_batch batch, int clear) {

@@ -27,7 +27,57 @@
 #include "ptx.cuh"
 #include "sdft.h"
 
+// Debug build with range checks (compiled with -DSDFT_BOUNDS_CHECK=1, see
+// build.py): every TMA tile coordinate, twiddle-table range and work-queue
+// record is checked against the extent it must lie in before it is used. A
+// violation adds one to a device counter, records kBadBounds in the status word
+// and makes the access harmless (coordinate 0, entry range of table 0); no
+// kernel traps. sdft_debug_bounds_violations reads (and clears) the counts.
+#ifndef SDFT_BOUNDS_CHECK
+#define SDFT_BOUNDS_CHECK 0
+#endif
+
 namespace sdft {
+
+constexpr int kBadBounds = 0x105;     // status: a range check of the debug build failed
+
+#if SDFT_BOUNDS_CHECK
+// One counter per translation unit (a static device variable of this header);
+// each registers a host reader of its own copy when the library loads.
+static __device__ unsigned long long g_bounds_violations = 0;
+void register_violation_reader(uint64_t (*reader)(int clear));
+namespace {
+inline uint64_t read_violations_here(int clear) {
+  unsigned long long v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_bounds_violations, sizeof(v)) != cudaSuccess) return ~0ull;
+  if (clear) {
+    const unsigned long long z = 0;
+    cudaMemcpyToSymbol(g_bounds_violations, &z, sizeof(z));
+  }
+  return v;
+}
+struct ViolationReaderRegistration {
+  ViolationReaderRegistration() { register_violation_reader(&read_violations_here); }
+};
+static ViolationReaderRegistration g_violation_reader_registration;
+}  // namespace
+#endif
+
+// `ok` false: count a violation (debug build) and record it in `status`.
+// Returns `ok` in the debug build and true otherwise (the check compiles away).
+__device__ __forceinline__ bool in_bounds(bool ok, int* status) {
+#if SDFT_BOUNDS_CHECK
+  if (!ok) {
+    atomicAdd(&g_bounds_violations, 1ull);
+    if (status) atomicCAS(status, 0, kBadBounds);
+  }
+  return ok;
+#else
+  (void)ok;
+  (void)status;
+  return true;
+#endif
+}
 
 template <class R> struct KT;
 template <> struct KT<float> {
@@ -65,6 +115,12 @@ constexpr uint32_t kTileBytes = 32768;
 constexpr int kBadSmem = 0x101;   // less dynamic shared memory than the layout needs
 constexpr int kBadMap = 0x102;    // tensor map parameter not 64-byte aligned
 constexpr int kBadTable = 0x103;  // twiddle table not 16-byte aligned
+// Bound on the wait for a CTA's own copies already in flight after a failed
+// wait: an issued copy lands within microseconds on a working GPU, so this
+// bound is generous and independent of the (possibly short) bound whose expiry
+// caused the abort; the CTA only releases its shared memory once they landed.
+constexpr uint64_t kDrainNs = 2000000000ull;
+__host__ __device__ constexpr uint64_t drain_bound(uint64_t t) { return t > kDrainNs ? t : kDrainNs; }
 constexpr int kBufs = 3;                                             // tile buffers per work-queue CTA
 // Tile buffers per level-kernel CTA. Two keep the level kernel at the speed of a
 // copy-only variant of itself (TMA in and out, no passes) on the 2^12-point
@@ -90,39 +146,47 @@ __host__ __device__ constexpr uint32_t xor_part(uint32_t X) {
 }
 
 // ---- butterflies -----------------------------------------------------------------
-// complex64: the twiddle product in scalar FMAs, the two complex sums as packed
-// FP32x2 operations (each lane rounds exactly as the scalar operation would).
+// Three fused multiply-adds per output component pair: the first output
+// a' = a + w b takes two chained FMAs per component (the twiddle product is
+// never rounded on its own), the second is b' = 2a - a' (one FMA per component,
+// 2a exact). Six FMA-pipe operations per butterfly instead of eight for a
+// separate product and two sums; b' carries a''s rounding error, so both
+// outputs stay within a few units in the last place of max(|a|, |w b|).
 __device__ __forceinline__ void bfly(float2& a, float2& b, const float2 w) {
-  float2 t;
-  t.x = fmaf(-w.y, b.y, w.x * b.x);
-  t.y = fmaf(w.y, b.x, w.x * b.y);
-  b = __ffma2_rn(t, make_float2(-1.f, -1.f), a);   // a - t
-  a = __fadd2_rn(a, t);
+  float2 n;
+  n.x = fmaf(w.x, b.x, fmaf(-w.y, b.y, a.x));
+  n.y = fmaf(w.x, b.y, fmaf(w.y, b.x, a.y));
+  b.x = fmaf(2.f, a.x, -n.x);
+  b.y = fmaf(2.f, a.y, -n.y);
+  a = n;
 }
+// The last stage: both outputs scaled by sc (a power of two: exact); the
+// twiddles arrive pre-scaled, so only a is scaled here.
 __device__ __forceinline__ void bfly_scaled(float2& a, float2& b, const float2 w, const float sc) {
-  float2 t;
-  t.x = fmaf(-w.y, b.y, w.x * b.x);
-  t.y = fmaf(w.y, b.x, w.x * b.y);
-  const float2 s2 = make_float2(sc, sc);
-  const float2 as = __fmul2_rn(a, s2);                // exact: sc is a power of two
-  b = __ffma2_rn(t, make_float2(-1.f, -1.f), as);
-  a = __fadd2_rn(as, t);
+  const float2 as = __fmul2_rn(a, make_float2(sc, sc));
+  float2 n;
+  n.x = fmaf(w.x, b.x, fmaf(-w.y, b.y, as.x));
+  n.y = fmaf(w.x, b.y, fmaf(w.y, b.x, as.y));
+  b.x = fmaf(2.f, as.x, -n.x);
+  b.y = fmaf(2.f, as.y, -n.y);
+  a = n;
 }
 __device__ __forceinline__ void bfly(double2& a, double2& b, const double2 w) {
-  const double tr = fma(-w.y, b.y, w.x * b.x);
-  const double ti = fma(w.y, b.x, w.x * b.y);
-  b.x = a.x - tr;
-  b.y = a.y - ti;
-  a.x = a.x + tr;
-  a.y = a.y + ti;
+  const double nx = fma(w.x, b.x, fma(-w.y, b.y, a.x));
+  const double ny = fma(w.x, b.y, fma(w.y, b.x, a.y));
+  b.x = fma(2.0, a.x, -nx);
+  b.y = fma(2.0, a.y, -ny);
+  a.x = nx;
+  a.y = ny;
 }
 __device__ __forceinline__ void bfly_scaled(double2& a, double2& b, const double2 w, const double sc) {
-  const double tr = fma(-w.y, b.y, w.x * b.x);
-  const double ti = fma(w.y, b.x, w.x * b.y);
-  b.x = fma(a.x, sc, -tr);
-  b.y = fma(a.y, sc, -ti);
-  a.x = fma(a.x, sc, tr);
-  a.y = fma(a.y, sc, ti);
+  const double ax = a.x * sc, ay = a.y * sc;
+  const double nx = fma(w.x, b.x, fma(-w.y, b.y, ax));
+  const double ny = fma(w.x, b.y, fma(w.y, b.x, ay));
+  b.x = fma(2.0, ax, -nx);
+  b.y = fma(2.0, ay, -ny);
+  a.x = nx;
+  a.y = ny;
 }
 
 // Adjoint butterflies (synthesis): (a, b) -> (a + b, conj(w) (a - b)); the
@@ -701,8 +765,24 @@ struct LevelArgs {
   double inv_n;            // 1/N, used by the adjoint kernel
   int* status;             // device status word
   uint64_t timeout_ns;     // bound on every mbarrier wait
+  int64_t lim1, lim3;      // tile origins lie in [0, lim1) x [0, lim3) (range checks)
+  uint64_t tw_tables;      // tables in `tw` (range checks)
   typename KT<R>::C tw0[16];  // tw0[i] = level-0 table entry i + 1 (stage bits 0..3), i < 15
 };
+
+// Range checks of a level launch (debug build): the table entries the passes
+// of stage bits [PLO, PHI) read, [max(1, 2^PLO), 2^PHI) absolute, lie in every
+// table's [tw_first, tw_first + tw_len).
+template <class R, int PLO, int PHI>
+__device__ __forceinline__ bool level_tables_in_bounds(const LevelArgs<R>& a) {
+  const uint64_t lo = PLO == 0 ? 1u : (1ull << PLO), hi = 1ull << PHI;
+  return in_bounds(a.tw_first <= lo && hi <= a.tw_first + a.tw_len && a.tw_tables >= 1, a.status);
+}
+// A tile origin outside the tensor becomes (0, 0) (debug build).
+template <class R>
+__device__ __forceinline__ void level_coords_in_bounds(const LevelArgs<R>& a, int& c1, int& c3) {
+  if (!in_bounds(c1 >= 0 && c1 < a.lim1 && c3 >= 0 && c3 < a.lim3, a.status)) c1 = c3 = 0;
+}
 
 // Pointer arithmetic on the shared-memory symbol itself (no round trip through
 // an integer), so that accesses through the result stay shared-space loads and
@@ -741,6 +821,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
       if (tid == 0) atomicCAS(args.status, 0, bad);
       return;
     }
+    if (!level_tables_in_bounds<R, PLO, PHI>(args)) return;   // debug build only
   }
   // CTA c takes tiles c, c + G, c + 2G, ...: the tiles in flight at any moment
   // are neighbours in memory (on the strided later levels this was measured 6 %
@@ -777,6 +858,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     const uint32_t bar = bar0 + 8 * b;
     int c1, c3;
     coords(load_cur, c1, c3);
+    level_coords_in_bounds(args, c1, c3);
     advance(load_cur);
     ptx::mbar_arrive_expect_tx(bar, kTileBytes);
     ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &src, bar, 0, c1, 0, c3);
@@ -807,7 +889,8 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   uint64_t j = 0;
   for (; j < n; ++j, advance(cur), b = (b + 1 == uint32_t(kLevelBufs)) ? 0u : b + 1) {
     char* buf = smem + b * kTileBytes;
-    const uint64_t tab = args.tw_stride ? cur.a : 0;
+    uint64_t tab = args.tw_stride ? cur.a : 0;
+    if (!in_bounds(tab < args.tw_tables, args.status)) tab = 0;
     if (tab != cur_tab) {  // uniform across the CTA; the previous tile's passes are done
       twt = tw + tab * args.tw_stride;
       load_reg_twiddles<R, PLO, PHI>(twt, tid, wreg);
@@ -839,6 +922,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     if (tid == 0) {
       int c1, c3;
       coords(cur, c1, c3);
+      level_coords_in_bounds(args, c1, c3);
       ptx::tma_store_4d(&dst, ptx::smem_addr(buf), 0, c1, 0, c3);
       ptx::bulk_commit();
     }
@@ -850,7 +934,8 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
       const uint64_t last = (j + kLevelBufs - 2 > uint64_t(kLevelBufs - 1)) ? j + kLevelBufs - 2
                                                                              : uint64_t(kLevelBufs - 1);
       for (uint64_t q = j; q <= last && q < n; ++q)
-        ptx::mbar_wait_bounded(bar0 + 8 * uint32_t(q % kLevelBufs), uint32_t((q / kLevelBufs) & 1), args.timeout_ns);
+        ptx::mbar_wait_bounded(bar0 + 8 * uint32_t(q % kLevelBufs), uint32_t((q / kLevelBufs) & 1),
+                               drain_bound(args.timeout_ns));
       atomicExch(args.status, int(SDFT_ERR_TIMEOUT));
     }
     ptx::bulk_wait<0>();

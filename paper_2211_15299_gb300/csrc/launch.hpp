@@ -46,5 +46,9 @@ void free_strided_queues(Plan& p);
 // Release the cached sdft_execute_batched batches whose plan list names the plan
 // with this serial (the caller has synchronised before destroying the plan).
 void forget_batched(uint64_t serial);
+// Pin (never evict implicitly) or unpin the cached sdft_execute_batched list of
+// these plans, building it if needed; report whether a list is cached.
+sdft_status pin_batched(const sdft_plan* plans, uint64_t n, int pin);
+void batched_cache_info(const sdft_plan* plans, uint64_t n, int* cached, int* pinned, uint64_t* n_lists);
 
 }  // namespace sdft

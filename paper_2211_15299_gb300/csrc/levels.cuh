@@ -119,6 +119,9 @@ sdft_status level0_setup(const Plan& p, uint64_t batch, const void* src, void* d
   a.inv_n = std::ldexp(1.0, -int(p.M));
   a.status = p.d_status;
   a.timeout_ns = wait_timeout_ns();
+  a.lim1 = int64_t(rows);
+  a.lim3 = 1;
+  a.tw_tables = 1;
   return SDFT_OK;
 }
 
@@ -154,6 +157,9 @@ sdft_status later_setup(const Plan& p, uint64_t batch, size_t j, const void* src
   a.inv_n = std::ldexp(1.0, -int(p.M));
   a.status = p.d_status;
   a.timeout_ns = wait_timeout_ns();
+  a.lim1 = int64_t(1) << (L.lo - CB);
+  a.lim3 = int64_t(Z);
+  a.tw_tables = L.n_gb;
   return SDFT_OK;
 }
 

@@ -59,6 +59,9 @@ struct QArgs {
   int* status;
   uint64_t timeout_ns;
   uint32_t need_bias;       // added to every dependency target (0; non-zero only to test timeouts)
+  uint32_t n_counters;      // counters in `counters` (range checks)
+  uint64_t n_insts;         // records in `insts` (range checks)
+  uint64_t total;           // values in each packed buffer (range checks)
 };
 
 // Item records are copied by the producer into a shared-memory ring three items
@@ -90,8 +93,14 @@ constexpr int q_stage_lo(int TB, int PLO) {
 // (maps in parameter space are baked into a captured CUDA graph).
 struct QParams {
   CUtensorMap maps[kMaxMaps];
+  int32_t lim1[kMaxMaps], lim3[kMaxMaps];   // tile origins of map m lie in [0, lim1[m]) x [0, lim3[m]) (range checks)
   QArgs a;
 };
+// Record the coordinate extents of map `slot` (dims as given to encode_map).
+inline void q_set_limits(QParams& prm, size_t slot, const uint64_t dims[4]) {
+  prm.lim1[slot] = int32_t(dims[1] > 0x7fffffffull ? 0x7fffffffull : dims[1]);
+  prm.lim3[slot] = int32_t(dims[3] > 0x7fffffffull ? 0x7fffffffull : dims[3]);
+}
 
 // Variant ids.
 constexpr int kVSmall = 0;
@@ -219,6 +228,7 @@ __device__ __forceinline__ void run_small(const QArgs& a, const QItem& it, uint3
   using C = typename KT<R>::C;
   if (tid >= it.count) return;
   const QInst ins = a.insts[it.inst + tid];
+  if (!in_bounds(ins.s <= kSmallMax && ins.off + (1ull << ins.s) <= a.total, a.status)) return;   // debug build
   const C* in = static_cast<const C*>(a.in) + ins.off;
   C* out = static_cast<C*>(a.out) + ins.off;
   const C* tw = static_cast<const C*>(ins.tw);
@@ -283,6 +293,23 @@ __device__ __forceinline__ const QItem& q_meta(char* smem, uint64_t j) {
   return reinterpret_cast<const QItem*>(smem + kBufs * kTileBytes + 64)[j % kMetaSlots];
 }
 
+// Range checks of a work-item record (debug build): map slots, tile origins
+// against the maps' extents, counters, instance records. A failing item is
+// turned into a no-op by the producer (its tile is neither loaded nor stored).
+template <class R>
+__device__ __forceinline__ bool q_item_in_bounds(const QParams& prm, const QItem& it) {
+  const QArgs& a = prm.a;
+  if (it.variant == kVNop) return true;
+  if (it.variant == kVSmall) return in_bounds(it.count >= 1 && uint64_t(it.inst) + it.count <= a.n_insts, a.status);
+  const uint32_t ld = it.map, sv = it.variant < 16 ? uint32_t(it.map) + 1u : uint32_t(it.map);
+  bool ok = it.tw != nullptr && ld < uint32_t(kMaxMaps) && sv < uint32_t(kMaxMaps);
+  ok = ok && it.c1 >= 0 && it.c3 >= 0 && it.c1 < prm.lim1[ld] && it.c3 < prm.lim3[ld] && it.c1 < prm.lim1[sv] &&
+       it.c3 < prm.lim3[sv];
+  ok = ok && (it.dep == kNone || it.dep < a.n_counters) && (it.sig == kNone || it.sig < a.n_counters);
+  ok = ok && uint64_t(it.inst) + (it.variant < 15 ? uint64_t(it.count) : 1u) <= a.n_insts;
+  return in_bounds(ok, a.status);
+}
+
 // The producer warp's loop (lane 0). CTA c takes items c, c + G, ... Iteration
 // j: (1) once item i = j - 3 is computed (empty[i % 3]), store it from its
 // buffer, commit one bulk group, and publish item i - 1's counter (its store
@@ -341,6 +368,8 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
     }
     if (j < n) {
       ptx::cp_async_wait<2>();         // record j has landed
+      if (!q_item_in_bounds<R>(prm, q_meta(smem, j)))      // debug build only
+        const_cast<QItem&>(q_meta(smem, j)).variant = kVNop;
       const QItem& it = q_meta(smem, j);
       const uint32_t full = bars + kQFull + 8 * b;
       if (q_is_tma(it)) {
@@ -419,7 +448,7 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
   if (failed) {
     // let every issued load land before the CTA's shared memory is released
     for (int q = 0; q < kBufs; ++q)
-      if (inflight >> q & 1u) ptx::mbar_wait_bounded(bars + kQFull + 8 * q, (load_par >> q) & 1u, tmo);
+      if (inflight >> q & 1u) ptx::mbar_wait_bounded(bars + kQFull + 8 * q, (load_par >> q) & 1u, drain_bound(tmo));
     atomicExch(prm.a.status, int(SDFT_ERR_TIMEOUT));
   }
   ptx::bulk_wait<0>();

@@ -293,11 +293,16 @@ __global__ void __launch_bounds__(256) k_sas_decode(const typename KT<R>::C* __r
                                                     typename KT<R>::C* __restrict__ out,
                                                     const SasOut* __restrict__ meta,
                                                     const typename KT<R>::C* __restrict__ winv, uint64_t k,
-                                                    uint64_t nk, uint32_t mu_star, uint64_t batch) {
+                                                    uint64_t nk, uint32_t mu_star, uint64_t batch,
+                                                    uint64_t winv_len, int* status) {
   using C = typename KT<R>::C;
   const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= k) return;
   const SasOut m = meta[i];
+  // debug build: the class column, its size and its inverse row in range
+  if (!in_bounds(m.t < nk && m.mu >= 1 && m.mu <= mu_star && m.u < m.mu &&
+                     uint64_t(m.woff) + uint64_t(m.u + 1) * m.mu <= winv_len, status))
+    return;
   const C* wrow = winv + m.woff + uint32_t(m.u) * m.mu;
   for (uint64_t b0 = blockIdx.y; b0 < batch; b0 += uint64_t(gridDim.y) * kSasDecodeB) {
     R re[kSasDecodeB], im[kSasDecodeB];
@@ -388,8 +393,9 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     load_buf = (load_buf + 1 == uint32_t(kLevelBufs)) ? 0u : load_buf + 1;
     const uint32_t bar = bar0 + 8 * b;
     ptx::mbar_arrive_expect_tx(bar, kTileBytes);
-    const int row = int(int64_t(blockIdx.x + j * G) * fa.a.b_step1);
-    ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &src, bar, 0, row, 0, 0);
+    int row = int(int64_t(blockIdx.x + j * G) * fa.a.b_step1), c3 = 0;
+    level_coords_in_bounds(fa.a, row, c3);
+    ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &src, bar, 0, row, 0, c3);
   };
   if (tid == 0) {
     for (int b = 0; b < kLevelBufs; ++b) ptx::mbar_init(bar0 + 8 * b, 1);
@@ -429,7 +435,8 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     C* ob = fa.out + (blockIdx.x + j * G) * fa.k;
     for (uint64_t i = tid; i < fa.k; i += NT) {
       const C w = ws[i];
-      const uint32_t t = cs[i];
+      uint32_t t = cs[i];
+      if (!in_bounds(t < (1u << TB), fa.a.status)) t = 0;   // debug build
       const C v = *reinterpret_cast<const C*>(buf + row_part<R>(t) + xor_part<R>(t));
       C o;
       o.x = fma(w.x, v.x, fma(-w.y, v.y, R(0)));
@@ -442,7 +449,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
                                                                            : uint64_t(kLevelBufs - 1);
     for (uint64_t q = j; q <= last && q < n; ++q)
       ptx::mbar_wait_bounded(bar0 + 8 * uint32_t(q % kLevelBufs), uint32_t((q / kLevelBufs) & 1),
-                             fa.a.timeout_ns);
+                             drain_bound(fa.a.timeout_ns));
     atomicExch(fa.a.status, int(SDFT_ERR_TIMEOUT));
   }
 }
@@ -638,11 +645,12 @@ sdft_status sdft_sas_execute(sdft_sas sas, uint64_t batch, const void* d_samples
   if (S.prec == SDFT_C64)
     k_sas_decode<float><<<grid, block, 0, st>>>(static_cast<const float2*>(d_work), static_cast<float2*>(d_coeffs),
                                                 S.d_meta, static_cast<const float2*>(S.d_winv), S.k, nk, S.mu_star,
-                                                batch);
+                                                batch, S.winv.size(), S.vplan->p.d_status);
   else
     k_sas_decode<double><<<grid, block, 0, st>>>(static_cast<const double2*>(d_work),
                                                  static_cast<double2*>(d_coeffs), S.d_meta,
-                                                 static_cast<const double2*>(S.d_winv), S.k, nk, S.mu_star, batch);
+                                                 static_cast<const double2*>(S.d_winv), S.k, nk, S.mu_star, batch,
+                                                 S.winv.size(), S.vplan->p.d_status);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
 }

@@ -183,6 +183,8 @@ sdft_status init_maps(Server& S) {
     sdft_status s = encode_map(&S.maps.maps[2 * r], S.d_arena, dims, strides, box);
     if (s == SDFT_OK) s = encode_map(&S.maps.maps[2 * r + 1], S.d_arena, dims, strides, box);
     if (s != SDFT_OK) return s;
+    q_set_limits(S.maps, 2 * r, dims);
+    q_set_limits(S.maps, 2 * r + 1, dims);
   }
   uint32_t slot = 18;
   const uint64_t elems = S.budget / es;
@@ -196,6 +198,7 @@ sdft_status init_maps(Server& S) {
       const uint32_t box[4] = {32, 1u << lg, 1u << Q, 1};
       sdft_status s = encode_map(&S.maps.maps[slot], S.d_arena, dims, strides, box);
       if (s != SDFT_OK) return s;
+      q_set_limits(S.maps, slot, dims);
       S.later_slot[lo][hi] = slot++;
     }
   }
@@ -372,6 +375,9 @@ sdft_status launch_slot(Server& S, Slot& sl) {
   prm.a.status = S.d_status;
   prm.a.timeout_ns = wait_timeout_ns();
   prm.a.need_bias = 0;
+  prm.a.n_counters = n_ctr;
+  prm.a.n_insts = sl.reqs.size();
+  prm.a.total = S.budget / es;
   const int grid = int(std::min<uint64_t>(uint64_t(S.grid), n_items));
   s = S.prec == SDFT_C64 ? launch_queue_f32(prm, grid, sl.stream) : launch_queue_f64(prm, grid, sl.stream);
   if (s != SDFT_OK) return s;

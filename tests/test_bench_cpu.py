@@ -19,8 +19,16 @@ import bench  # noqa: E402
 def test_committed_traffic_matches_kernel_source():
     # the committed DRAM figure is used only while the kernel source it was
     # captured on is unchanged; an unknown workload has none
+    import hashlib
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        entry = json.load(fh)["20/12/4096"]
+    with open(os.path.join(ROOT, "paper_2211_15299_gb300", "csrc", "kernels.cuh"), "rb") as fh:
+        current = hashlib.sha256(fh.read()).hexdigest()[:16]
     v = bench._committed_traffic(20, 12, 4096)
-    assert isinstance(v, int) and v > 0
+    if entry["kernels_cuh_sha"] == current:
+        assert v == entry["dram_bytes_per_launch"] and v > 0
+    else:
+        assert v is None
     assert bench._committed_traffic(20, 12, 4095) is None
 
 

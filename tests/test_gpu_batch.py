@@ -315,3 +315,53 @@ def test_execute_batched_cache_released_with_its_plans():
     for i, p in enumerate(fresh):
         assert torch.equal(z[i * ks:(i + 1) * ks], p.execute_strided(x[i * ks:(i + 1) * ks].clone())), i
     assert fresh[0].device_status() == 0
+
+
+def test_execute_batched_pinned_list_survives_eviction():
+    """A pinned execute_batched list (the one a CUDA graph was captured on) is
+    never freed by building other lists; unpinned, it is evicted by age like any
+    other. The graph is replayed only while its list is pinned."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Plan, execute_batched, _native as N
+    rng = np.random.default_rng(7600)
+    pool = [Plan(i.M, i.J, 0) for i in _instances(rng, [5, 6, 7, 8, 9, 10, 11, 12, 13, 4, 3])]
+    base = [pool[0], pool[7], pool[8]]                   # the list the graph is captured on
+    ks = [p.k for p in base]
+    packed = np.concatenate([[0], np.cumsum(ks)]).astype(np.int64)
+    d_off = torch.from_numpy(packed).cuda()
+    xs = torch.randn(int(packed[-1]), dtype=torch.complex64, device="cuda")
+    out = torch.empty_like(xs)
+    N.sdft_execute_batched_pin([p.handle for p in base], True)
+    assert N.sdft_execute_batched_cache_info([p.handle for p in base])[:2] == (True, True)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        execute_batched(base, xs, d_off, out, stream=s.cuda_stream)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        execute_batched(base, xs, d_off, out, stream=s.cuda_stream)
+    # nine other lists: more than the eight unpinned lists kept
+    others = [[pool[i], pool[(i + 1) % len(pool)]] for i in range(1, 10)]
+    for lst in others:
+        k2 = [p.k for p in lst]
+        off2 = torch.tensor([0, k2[0], k2[0] + k2[1]], dtype=torch.int64, device="cuda")
+        execute_batched(lst, torch.randn(sum(k2), dtype=torch.complex64, device="cuda"), off2)
+    torch.cuda.synchronize()
+    assert N.sdft_execute_batched_cache_info([p.handle for p in base])[:2] == (True, True)
+    assert N.sdft_execute_batched_cache_info([p.handle for p in others[0]])[0] is False   # oldest unpinned: freed
+    assert N.sdft_execute_batched_cache_info([p.handle for p in others[-1]])[0] is True
+    xs.copy_(torch.randn_like(xs))
+    g.replay()                                           # its list is still pinned and cached
+    torch.cuda.synchronize()
+    for i, p in enumerate(base):
+        a, b = int(packed[i]), int(packed[i + 1])
+        assert torch.equal(out[a:b], p.execute_strided(xs[a:b].clone())), i
+    del g                                                # no replay after this point
+    N.sdft_execute_batched_pin([p.handle for p in base], False)
+    assert N.sdft_execute_batched_cache_info([p.handle for p in base])[:2] == (True, False)
+    k2 = [pool[10].k, pool[9].k]
+    off2 = torch.tensor([0, k2[0], k2[0] + k2[1]], dtype=torch.int64, device="cuda")
+    execute_batched([pool[10], pool[9]], torch.randn(sum(k2), dtype=torch.complex64, device="cuda"), off2)
+    torch.cuda.synchronize()
+    assert N.sdft_execute_batched_cache_info([p.handle for p in base])[0] is False    # now the oldest: freed
+    assert pool[0].device_status() == 0
