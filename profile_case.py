@@ -1,7 +1,7 @@
 """Run one transform configuration a few times (for profilers) and report the
 device status word; exits non-zero if the status is not 0.
 
-    python -m paper_2211_15299_gb300.profile_case --log2n 20 --log2k 12 --batch 4096 --reps 4
+    python profile_case.py --log2n 20 --log2k 12 --batch 4096 --reps 4
 """
 from __future__ import annotations
 
@@ -9,7 +9,7 @@ import argparse
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

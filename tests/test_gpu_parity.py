@@ -89,8 +89,6 @@ SIZES = [(1, 0, 5), (3, 1, 7), (6, 2, 9), (8, 3, 33), (9, 4, 65), (10, 5, 37), (
 @pytest.mark.parametrize("M,s,batch", SIZES)
 @pytest.mark.parametrize("prec", [0, 1])
 def test_sizes_against_oracle(M, s, batch, prec):
-    if prec == 1 and s > 15:
-        pytest.skip("complex128 sizes capped at 2^15 here")
     rng = np.random.default_rng(1000 * s + M + 17 * prec)
     plan, piv, Jc, C, F = _case(M, s, batch, rng, prec)
     got, f_in = _run(plan, F)
@@ -108,6 +106,19 @@ def test_three_levels_complex64(s):
     got, f_in = _run(plan, F)
     ref = O.transform_levels(s + 3, piv, Jc, f_in)
     assert rel_l2(got, ref) < TOL[0]
+
+
+@pytest.mark.parametrize("s", [19, 20])
+def test_three_levels_complex128(s):
+    # complex128 tiles hold 2^11 values and later levels 8 stage bits: s = 19
+    # runs levels [0, 11) and [11, 19); s = 20 adds a third level [19, 20).
+    # The FP64 pipe against the oracle at 1e-12, element by element.
+    rng = np.random.default_rng(5252 + s)
+    plan, piv, Jc, C, F = _case(s + 2, s, 1, rng, 1)
+    got, f_in = _run(plan, F)
+    ref = O.transform_levels(s + 2, piv, Jc, f_in)
+    assert rel_l2(got, ref) < TOL[1]
+    assert rel_l2(got, C) < TOL[1]
 
 
 def test_inplace():
@@ -157,36 +168,72 @@ def test_config2_full_size(prec):
 
 @pytest.mark.parametrize("contiguous", [True, False])
 def test_config3_full_size(contiguous):
-    """N = 2^30, k = 2^20, batch 64, complex64: two levels of butterflies."""
+    """N = 2^30, k = 2^20, batch 64, complex64 (two levels of butterflies): every
+    instance synthesised by the oracle from seeded coefficients and compared
+    element by element with them; four against the oracle's transform of the
+    same rounded samples; Parseval for all; closed-form spot checks."""
     torch = _torch()
     from paper_2211_15299_gb300 import Plan
     inst, _ = W.workload_large(contiguous=contiguous, coeffs=False)
     rng = W.rng_for(3, 100 + int(contiguous))
     plan = Plan(inst.M, inst.J, 0)
     Jc = O.canonical_support_by_key(inst.J, inst.pivots)
-    B, k, nchk = 64, inst.k, 3
-    C = W.complex_gaussian((nchk, k), rng)
+    B, k = 64, inst.k
+    C = W.complex_gaussian((B, k), rng)
     F = np.empty((B, k), dtype=np.complex64)
-    F[:nchk] = O.synthesize_levels(inst.M, inst.pivots, Jc, C)
-    F[nchk:] = W.complex_gaussian((B - nchk, k), rng) * (1.0 / (1 << inst.M)) * np.sqrt(k)
+    for b0 in range(0, B, 16):                      # the oracle's synthesis, 16 at a time
+        F[b0:b0 + 16] = O.synthesize_levels(inst.M, inst.pivots, Jc, C[b0:b0 + 16])
+    # the synthesis itself at a few sample points by the direct sum
+    I = O.sample_set(inst.M, inst.pivots)
+    pts = rng.choice(k, size=32, replace=False)
+    direct = O.brute_force_samples(inst.M, Jc, C[5], I[pts])
+    assert rel_l2(F[5, pts], direct) < 1e-6
     x = torch.from_numpy(F).cuda()
     y = plan.execute_strided(x)
     torch.cuda.synchronize()
     assert plan.device_status() == 0
-    got = y[:nchk].cpu().numpy().astype(np.complex128)
-    for b in range(nchk):
-        assert rel_l2(got[b], C[b]) < 1e-5
+    got = y.cpu().numpy()
+    for b in range(B):                              # every instance against its coefficients
+        assert rel_l2(got[b], C[b]) < 1e-5, b
+    for b in (0, 21, 42, 63):                       # element by element against the oracle
+        ref = O.transform_levels(inst.M, inst.pivots, Jc, F[b:b + 1].astype(np.complex128))[0]
+        assert rel_l2(got[b], ref) < TOL[0], b
     # Parseval for every instance: ||c||^2 = (N^2 / k) ||f||^2 (F(J, I) is sqrt(k)-scaled unitary)
     fn = torch.linalg.vector_norm(x.to(torch.complex128), dim=1).cpu().numpy()
     cn = torch.linalg.vector_norm(y.to(torch.complex128), dim=1).cpu().numpy()
     assert np.allclose(cn, fn * (1 << inst.M) / np.sqrt(k), rtol=1e-5)
-    # spot checks by the closed form in two instances that were not synthesised
-    I = O.sample_set(inst.M, inst.pivots)
+    # spot checks by the closed form on the same rounded samples
     for b in (17, 63):
         idx = rng.choice(k, size=8, replace=False)
         spot = O.coefficients_at(inst.M, Jc[idx], I, F[b].astype(np.complex128))
-        row = y[b].cpu().numpy().astype(np.complex128)
+        row = got[b].astype(np.complex128)
         assert np.abs(row[idx] - spot).max() / (np.linalg.norm(row) / np.sqrt(k)) < 1e-5
+
+
+def test_config4_full_uneven_workload():
+    """The 10,000-instance uneven workload (each instance its own support, N from
+    2^12 to 2^24, k from 2^4 to 2^16) in one batch launch, every instance against
+    the oracle's transform of the same rounded samples at 1e-5."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Batch, Plan
+    insts = W.workload_uneven(count=10000)
+    plans = [Plan(i.M, i.J, 0) for i in insts]
+    b = Batch(plans)
+    rng = W.rng_for(4, 31)
+    x = torch.from_numpy(W.complex_gaussian(b.total, rng).astype(np.complex64)).cuda()
+    y = b.execute(x)
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    xs, ys = x.cpu().numpy(), y.cpu().numpy()
+    worst = 0.0
+    for i, (inst, p) in enumerate(zip(insts, plans)):
+        o, kk = int(b.offsets[i]), p.k
+        Jc = O.canonical_support_by_key(inst.J, inst.pivots)
+        ref = O.transform_levels(inst.M, inst.pivots, Jc, xs[o:o + kk][None].astype(np.complex128))[0]
+        err = rel_l2(ys[o:o + kk], ref)
+        worst = max(worst, err)
+        assert err < TOL[0], (i, inst.M, inst.s, err)
+    assert worst > 0.0
 
 
 @pytest.mark.parametrize("prec", [0, 1])
