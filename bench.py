@@ -189,6 +189,19 @@ def run_ours(args):
     def step(s=None):
         plan32.execute_strided(x32, y32, stream=(s or stream).cuda_stream)
 
+    # the tile parameters (stages per pass) chosen by the library's autotuner on
+    # this workload; both choices are also timed the bench's way, below
+    from paper_2211_15299_gb300 import _native as N
+    N.sdft_plan_autotune(plan32.handle, batch, x32, y32, stream.cuda_stream, 5)
+    tuned_spp = N.sdft_plan_get_stages_per_pass(plan32.handle)
+    by_spp = {}
+    for spp in (4, 3):
+        N.sdft_plan_set_stages_per_pass(plan32.handle, spp)
+        by_spp[spp] = 1e3 * statistics.mean(time_graph(step, max(5, args.steps // 2), args.warmup, flush, stream))
+    N.sdft_plan_set_stages_per_pass(plan32.handle, tuned_spp)
+    tuning = {"stages_per_pass": tuned_spp, "chosen_by": "sdft_plan_autotune",
+              "ms_by_stages_per_pass": {str(k): v for k, v in by_spp.items()}}
+
     _barrier(ws)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -217,7 +230,8 @@ def run_ours(args):
 
     if args.only_fp32:
         if rank == 0:
-            print(json.dumps({"value": value, "unit": UNIT, "ms_per_step": ms_per_step, "roofline": roofline}))
+            print(json.dumps({"value": value, "unit": UNIT, "ms_per_step": ms_per_step, "roofline": roofline,
+                              "tuning": tuning}))
         return
     # FP64: batched and plain per-instance (one call per instance), device-timed
     x64 = x32.to(torch.complex128)
@@ -311,10 +325,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"shared support N=2^{M} k=2^{s} batch {batch} complex64 (strided, one plan)",
-                   "log2N": M, "log2k": s, "batch": batch, "pivots": [int(p) for p in inst.pivots],
-                   "l2": "flushed between steps (256 MiB write, untimed)",
-                   "parallelism": f"replicas x{ws}"},
+        "config": _config(M, s, batch, ws),
+        "pivots": [int(p) for p in inst.pivots],
+        "tuning": tuning,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(8 * coeffs_per_step),
                 "d2h_bytes_per_step": int(8 * coeffs_per_step)},
         "gpu_launches": int(args.steps * n_levels),
@@ -334,6 +347,14 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _config(M, s, batch, ws):
+    """The workload of the headline line, the same in both arms."""
+    return {"workload": f"shared support N=2^{M} k=2^{s} batch {batch} complex64 (strided, one plan)",
+            "log2N": M, "log2k": s, "batch": batch,
+            "l2": "flushed between steps (256 MiB write, untimed)",
+            "parallelism": f"replicas x{ws}"}
 
 
 def _committed_traffic(M, s, batch):
@@ -417,18 +438,24 @@ def run_large(args):
             plan.execute_strided(x, y, stream=(s or stream).cuda_stream)
 
         coeffs = args.large_batch * inst.k
-        # both strategies, each graph-replayed with the L2 flush between steps
-        # (the queue strategy's first call builds its queue, so it runs before
-        # capture); the leg reports the faster
+        # both strategies x three or four stages per pass, each graph-replayed
+        # with the L2 flush between steps (the queue strategy's first call builds
+        # its queue, so it runs before capture); the leg reports the fastest
+        from paper_2211_15299_gb300 import _native as N
         by = {}
         for name in ("levels", "queue"):
             plan.set_strategy(name)
-            step()
-            torch.cuda.synchronize()
-            t = time_graph(step, args.steps, args.warmup, flush, stream)
-            by[name] = statistics.mean(t)
+            for spp in (4, 3):
+                N.sdft_plan_set_stages_per_pass(plan.handle, spp)
+                step()
+                torch.cuda.synchronize()
+                t = time_graph(step, args.steps, args.warmup, flush, stream)
+                by[f"{name}/{spp}"] = statistics.mean(t)
         best = min(by, key=by.get)
         mean = by[best]
+        plan.set_strategy(best.split("/")[0])
+        N.sdft_plan_set_stages_per_pass(plan.handle, int(best.split("/")[1]))
+        step()
         # the oracle on the host cores: 16 of the instances (the last strategy's output)
         torch.cuda.synchronize()
         nrow = min(16, args.large_batch)
@@ -437,8 +464,9 @@ def run_large(args):
                       "sample": f"{nrow} of the {args.large_batch} instances, Algorithm 1 in the oracle's plain C "
                                 "(FP64, OpenMP)", "seconds": dt, "rel_l2_gpu_vs_oracle": rel}
         res["contiguous" if contiguous else "spread"] = {
-            "coeffs_per_s": coeffs / mean, "ms_per_step": 1e3 * mean, "strategy": best,
-            "ms_by_strategy": {k: 1e3 * v for k, v in by.items()}, "cpu_oracle": cpu_oracle,
+            "coeffs_per_s": coeffs / mean, "ms_per_step": 1e3 * mean, "strategy": best.split("/")[0],
+            "stages_per_pass": int(best.split("/")[1]),
+            "ms_by_strategy_and_stages_per_pass": {k: 1e3 * v for k, v in by.items()}, "cpu_oracle": cpu_oracle,
             "alg_GBps": 16 * coeffs / mean / 1e9, "frac_of_peak": 16 * coeffs / mean / 1e9 / _peaks()[0],
             "pivots": [int(p) for p in inst.pivots]}
         assert plan.device_status() == 0
@@ -486,6 +514,8 @@ def run_uneven(args):
     schedule, grid, ms_tuned = b.autotune(x, y, reps=3)
     t_tune = time.perf_counter() - t0
     n_items, n_ctr, grid = b.stats()
+    from paper_2211_15299_gb300 import _native as N
+    spp_tuned = N.sdft_batch_get_stages_per_pass(b.handle)
 
     def step(s=None):
         b.execute(x, y, stream=(s or stream).cuda_stream)
@@ -515,7 +545,8 @@ def run_uneven(args):
             "ms_per_step": 1e3 * mean, "alg_GBps": (16 * total + tw_bytes) / mean / 1e9,
             "alg_bytes_per_step": 16 * total + tw_bytes, "work_items": n_items,
             "dependency_counters": n_ctr, "grid": grid, "plan_build_s": t_plan,
-            "autotune": {"schedule": schedule, "grid": grid, "ms_per_run": ms_tuned, "seconds": t_tune},
+            "autotune": {"schedule": schedule, "grid": grid, "stages_per_pass": spp_tuned, "ms_per_run": ms_tuned,
+                         "seconds": t_tune},
             "launches_per_step": 1, "graph": "one CUDA graph replay per step"}
 
 
@@ -788,8 +819,7 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": f"shared support N=2^{M} k=2^{s} batch {args.batch} complex64 (strided, one plan)",
-                      "log2N": M, "log2k": s, "batch": args.batch},
+           "config": _config(M, s, args.batch, ws),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                             "sample": f"the whole workload ({args.batch} instances) per step, Algorithm 1 in the "
                                       "oracle's plain C (FP64, OpenMP over instances)"},

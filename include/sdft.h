@@ -270,15 +270,40 @@ typedef enum { SDFT_STRATEGY_LEVELS = 1, SDFT_STRATEGY_QUEUE = 2 } sdft_strategy
 sdft_status sdft_plan_set_strategy(sdft_plan plan, sdft_strategy strategy);
 
 /*
- * sdft_plan_autotune - time both strategies on `batch` instances in the given
- * buffers (each run `reps` times after one warm-up, CUDA events on `stream`),
- * keep the faster one for the plan and report the mean times in milliseconds
- * (any output pointer may be NULL). Synchronises `stream`. The buffers are
- * overwritten. Single-level plans report SDFT_STRATEGY_LEVELS and time it only.
+ * sdft_plan_autotune - time every strategy x stages-per-pass choice on `batch`
+ * instances in the given buffers (each run `reps` times after one warm-up,
+ * CUDA events on `stream`), keep the fastest for the plan (strategy, and
+ * stages per pass: sdft_plan_get_stages_per_pass) and report each strategy's
+ * best mean time in milliseconds (any output pointer may be NULL). The choice
+ * is also stored in the library's tuning cache under (precision, log2 k,
+ * floor(log2 batch)) (see sdft_autotune_cache_save). Synchronises `stream`.
+ * The buffers are overwritten. Single-level plans report
+ * SDFT_STRATEGY_LEVELS and time it only.
  */
 sdft_status sdft_plan_autotune(sdft_plan plan, uint64_t batch, const void* d_samples, void* d_coeffs,
                                void* stream, int reps, sdft_strategy* chosen, float* ms_levels,
                                float* ms_queue);
+
+/* Apply the tuning cache's choice for this plan at this batch size (same key
+ * as sdft_plan_autotune), without timing: *found = 1 if there was one (else
+ * the plan is left as it is and *found = 0). Errors: SDFT_ERR_ARG (also for a
+ * cached entry this plan cannot take). */
+sdft_status sdft_plan_apply_tuning(sdft_plan plan, uint64_t batch, int* found);
+
+/*
+ * Stages per pass of a plan's butterfly kernels: every tile holds 2^12
+ * (complex64) or 2^11 (complex128) values in shared memory, and each thread
+ * runs `stages_per_pass` consecutive stages of Algorithm 1's network on
+ * 2^stages_per_pass of them in registers per pass over the tile. 4 (the
+ * default; 16 values per thread, 256 threads per complex64 tile) or, for
+ * complex64 plans, 3 (8 values per thread, 512 threads, one pass more per
+ * 12 stages). Every choice gives the same bits. sdft_plan_autotune chooses it
+ * with the strategy. A change synchronises the device if the plan holds
+ * cached work queues (they are rebuilt on next use). The paper has no
+ * counterpart (Algorithm 1 is stated as a recursion). Errors: SDFT_ERR_ARG.
+ */
+sdft_status sdft_plan_set_stages_per_pass(sdft_plan plan, uint32_t stages_per_pass);
+sdft_status sdft_plan_get_stages_per_pass(sdft_plan plan, uint32_t* stages_per_pass);
 
 /* Device status word of a plan: SDFT_OK, SDFT_ERR_TIMEOUT, or a launch
  * self-check code above 0xff (0x101: dynamic shared memory smaller than the
@@ -353,6 +378,18 @@ sdft_status sdft_batch_execute(sdft_batch batch, const void* d_samples, void* d_
 sdft_status sdft_batch_execute_noalloc(sdft_batch batch, const void* d_samples, void* d_coeffs,
                                        void* stream);
 
+/* Stages per pass of a batch's queue kernel (as for plans: 4, or 3 for
+ * complex64; the same bits either way). Rebuilds the batch's item list (its
+ * grid follows the kernel's occupancy): synchronise work using the batch
+ * first, and re-capture graphs. */
+sdft_status sdft_batch_set_stages_per_pass(sdft_batch batch, uint32_t stages_per_pass);
+sdft_status sdft_batch_get_stages_per_pass(sdft_batch batch, uint32_t* stages_per_pass);
+
+/* Apply the tuning cache's choice for this batch (key: precision,
+ * floor(log2 n), floor(log2 total values)) without timing; *found as for
+ * sdft_plan_apply_tuning. Rebuilds the item list when the choice differs. */
+sdft_status sdft_batch_apply_tuning(sdft_batch batch, int* found);
+
 /* Device status word of a batch (as for plans). */
 sdft_status sdft_batch_device_status(sdft_batch batch, int clear);
 
@@ -382,11 +419,13 @@ typedef enum {
 sdft_status sdft_batch_set_schedule(sdft_batch batch, sdft_schedule schedule, uint32_t grid);
 
 /*
- * sdft_batch_autotune - time the batch under four queue shapes (lanes or round
- * robin, on all co-resident CTAs or on half of them; one warm-up and `reps`
- * timed runs each, CUDA events on `stream`, the buffers overwritten), keep the
- * fastest and report it (any output may be NULL; `ms_best` is the mean time of
- * one run). Synchronises `stream`. As for sdft_batch_set_schedule, graphs
+ * sdft_batch_autotune - time the batch under every queue shape (lanes or round
+ * robin, on all co-resident CTAs or on half of them) and stages-per-pass
+ * choice (4, and 3 for complex64); one warm-up and `reps` timed runs each,
+ * CUDA events on `stream`, the buffers overwritten. Keeps the fastest, reports
+ * it (any output may be NULL; `ms_best` is the mean time of one run; the
+ * stages per pass: sdft_batch_get_stages_per_pass) and stores it in the
+ * tuning cache. Synchronises `stream`. As for sdft_batch_set_schedule, graphs
  * captured before must be re-captured.
  */
 sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d_coeffs, void* stream, int reps,
@@ -550,6 +589,28 @@ sdft_status sdft_server_device_status(sdft_server srv, int clear);
 
 /* Stop accepting requests, finish the queued ones, release everything. */
 sdft_status sdft_server_destroy(sdft_server srv);
+
+/* ------------------------------------------------------------------------ */
+/* Tuning cache                                                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The autotuners (sdft_plan_autotune, sdft_batch_autotune) store their choice
+ * in one process-wide cache; sdft_plan_apply_tuning / sdft_batch_apply_tuning
+ * apply a stored choice without timing. _save writes the cache as a JSON
+ * object, one member per key ("plan/c64/s20/b6": plan of complex64, log2 k =
+ * 20, batch in [64, 128); "batch/c64/n13/t26": uneven batch of 2^13..2^14 - 1
+ * instances and 2^26..2^27 - 1 values), each an object with the fields
+ * strategy, schedule, grid, stages_per_pass and ms (the time measured).
+ * _load merges such a file into the cache (SDFT_ERR_ARG for a file that
+ * cannot be read or parsed; the cache is then unchanged). _clear empties it;
+ * _size reports its entries. Host-only; thread-safe. The paper has no
+ * counterpart.
+ */
+sdft_status sdft_autotune_cache_save(const char* path);
+sdft_status sdft_autotune_cache_load(const char* path);
+sdft_status sdft_autotune_cache_clear(void);
+sdft_status sdft_autotune_cache_size(uint64_t* entries);
 
 /* ------------------------------------------------------------------------ */
 /* Diagnostics                                                               */

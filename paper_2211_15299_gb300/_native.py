@@ -66,6 +66,16 @@ SIGNATURES = {
     "sdft_execute_batched": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp]),
     "sdft_execute_batched_pin": (c_int, [c_vp, c_u64, c_int]),
     "sdft_debug_bounds_violations": (c_int, [ctypes.POINTER(c_int), P_u64, c_int]),
+    "sdft_plan_set_stages_per_pass": (c_int, [c_vp, c_u32]),
+    "sdft_plan_get_stages_per_pass": (c_int, [c_vp, P_u32]),
+    "sdft_plan_apply_tuning": (c_int, [c_vp, c_u64, ctypes.POINTER(c_int)]),
+    "sdft_batch_set_stages_per_pass": (c_int, [c_vp, c_u32]),
+    "sdft_batch_get_stages_per_pass": (c_int, [c_vp, P_u32]),
+    "sdft_batch_apply_tuning": (c_int, [c_vp, ctypes.POINTER(c_int)]),
+    "sdft_autotune_cache_save": (c_int, [ctypes.c_char_p]),
+    "sdft_autotune_cache_load": (c_int, [ctypes.c_char_p]),
+    "sdft_autotune_cache_clear": (c_int, []),
+    "sdft_autotune_cache_size": (c_int, [P_u64]),
     "sdft_execute_batched_cache_info": (c_int, [c_vp, c_u64, ctypes.POINTER(c_int), ctypes.POINTER(c_int), P_u64]),
     "sdft_plan_to_user_order": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "sdft_synthesize_strided_host": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
@@ -227,6 +237,56 @@ def sdft_execute_batched(plans, d_samples, d_offsets, d_coeffs, stream=None) -> 
     arr = (c_vp * len(plans))(*[int(p) for p in plans])
     _check(_lib.sdft_execute_batched(arr, len(plans), _ptr(d_samples), _ptr(d_offsets), _ptr(d_coeffs),
                                      _stream(stream)), "sdft_execute_batched")
+
+
+def sdft_plan_set_stages_per_pass(plan: int, stages_per_pass: int) -> None:
+    _check(_lib.sdft_plan_set_stages_per_pass(plan, int(stages_per_pass)), "sdft_plan_set_stages_per_pass")
+
+
+def sdft_plan_get_stages_per_pass(plan: int) -> int:
+    v = c_u32(0)
+    _check(_lib.sdft_plan_get_stages_per_pass(plan, ctypes.byref(v)), "sdft_plan_get_stages_per_pass")
+    return int(v.value)
+
+
+def sdft_plan_apply_tuning(plan: int, batch: int) -> bool:
+    found = c_int(0)
+    _check(_lib.sdft_plan_apply_tuning(plan, int(batch), ctypes.byref(found)), "sdft_plan_apply_tuning")
+    return bool(found.value)
+
+
+def sdft_batch_set_stages_per_pass(batch: int, stages_per_pass: int) -> None:
+    _check(_lib.sdft_batch_set_stages_per_pass(batch, int(stages_per_pass)), "sdft_batch_set_stages_per_pass")
+
+
+def sdft_batch_get_stages_per_pass(batch: int) -> int:
+    v = c_u32(0)
+    _check(_lib.sdft_batch_get_stages_per_pass(batch, ctypes.byref(v)), "sdft_batch_get_stages_per_pass")
+    return int(v.value)
+
+
+def sdft_batch_apply_tuning(batch: int) -> bool:
+    found = c_int(0)
+    _check(_lib.sdft_batch_apply_tuning(batch, ctypes.byref(found)), "sdft_batch_apply_tuning")
+    return bool(found.value)
+
+
+def sdft_autotune_cache_save(path: str) -> None:
+    _check(_lib.sdft_autotune_cache_save(os.fsencode(path)), "sdft_autotune_cache_save")
+
+
+def sdft_autotune_cache_load(path: str) -> None:
+    _check(_lib.sdft_autotune_cache_load(os.fsencode(path)), "sdft_autotune_cache_load")
+
+
+def sdft_autotune_cache_clear() -> None:
+    _check(_lib.sdft_autotune_cache_clear(), "sdft_autotune_cache_clear")
+
+
+def sdft_autotune_cache_size() -> int:
+    v = c_u64(0)
+    _check(_lib.sdft_autotune_cache_size(ctypes.byref(v)), "sdft_autotune_cache_size")
+    return int(v.value)
 
 
 def sdft_debug_bounds_violations(clear: bool = False):

@@ -478,43 +478,109 @@ sdft_status sdft_plan_set_strategy(sdft_plan plan, sdft_strategy strategy) {
   return SDFT_OK;
 }
 
+// Stages per pass of a plan's level kernels; a change drops the plan's cached
+// work queues (their grid follows the kernel's occupancy), after the device
+// has finished any work that uses them.
+static sdft_status set_plan_spp(sdft::Plan& p, uint32_t spp) {
+  if (spp != 4 && !(spp == 3 && p.prec == SDFT_C64)) return SDFT_ERR_ARG;
+  if (p.spp == spp) return SDFT_OK;
+  if (p.queues) {
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return sdft::cuda_fail(e);
+    sdft::free_strided_queues(p);
+  }
+  p.spp = spp;
+  return SDFT_OK;
+}
+
+sdft_status sdft_plan_set_stages_per_pass(sdft_plan plan, uint32_t stages_per_pass) {
+  if (!plan) return SDFT_ERR_ARG;
+  return set_plan_spp(plan->p, stages_per_pass);
+}
+
+sdft_status sdft_plan_get_stages_per_pass(sdft_plan plan, uint32_t* stages_per_pass) {
+  if (!plan || !stages_per_pass) return SDFT_ERR_ARG;
+  *stages_per_pass = plan->p.spp;
+  return SDFT_OK;
+}
+
+sdft_status sdft_plan_apply_tuning(sdft_plan plan, uint64_t batch, int* found) {
+  if (!plan) return SDFT_ERR_ARG;
+  sdft::Tuning t;
+  const bool hit = sdft::tuning_lookup(sdft::plan_tuning_key(plan->p.prec, plan->p.s, batch), &t);
+  if (found) *found = hit ? 1 : 0;
+  if (!hit) return SDFT_OK;
+  if (t.strategy != SDFT_STRATEGY_LEVELS && t.strategy != SDFT_STRATEGY_QUEUE) return SDFT_ERR_ARG;
+  sdft_status s = set_plan_spp(plan->p, uint32_t(t.spp));
+  if (s != SDFT_OK) return s;
+  plan->p.strategy = t.strategy;
+  return SDFT_OK;
+}
+
 sdft_status sdft_plan_autotune(sdft_plan plan, uint64_t batch, const void* d_samples, void* d_coeffs,
                                void* stream, int reps, sdft_strategy* chosen, float* ms_levels,
                                float* ms_queue) {
   if (!plan || reps <= 0) return SDFT_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const bool multi = plan->p.levels.size() > 1;
-  const int cands[2] = {SDFT_STRATEGY_LEVELS, SDFT_STRATEGY_QUEUE};
-  float ms[2] = {0.f, 0.f};
+  sdft::Plan& p = plan->p;
+  const bool multi = p.levels.size() > 1;
+  // strategy (one launch per level, or the work queue) x stages per pass (four;
+  // three as well for complex64)
+  struct Cand {
+    int strategy;
+    uint32_t spp;
+    float ms;
+  };
+  std::vector<Cand> cands;
+  for (int strat : {int(SDFT_STRATEGY_LEVELS), int(SDFT_STRATEGY_QUEUE)}) {
+    if (strat == SDFT_STRATEGY_QUEUE && !multi) continue;
+    for (uint32_t spp : {4u, 3u})
+      if (spp == 4 || p.prec == SDFT_C64) cands.push_back(Cand{strat, spp, 0.f});
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) return sdft::cuda_fail(e);
   sdft_status s = SDFT_OK;
-  const int saved = plan->p.strategy;
-  for (int c = 0; c < (multi ? 2 : 1) && s == SDFT_OK; ++c) {
-    plan->p.strategy = cands[c];
+  const int saved = p.strategy;
+  const uint32_t saved_spp = p.spp;
+  for (Cand& c : cands) {
+    p.strategy = c.strategy;
+    s = set_plan_spp(p, c.spp);
+    if (s != SDFT_OK) break;
     s = sdft::run_strided(plan, batch, d_samples, d_coeffs, st);    // warm-up (builds a queue if needed)
     if (s == SDFT_OK) e = cudaEventRecord(e0, st);
     for (int r = 0; r < reps && s == SDFT_OK && e == cudaSuccess; ++r)
       s = sdft::run_strided(plan, batch, d_samples, d_coeffs, st);
     if (s == SDFT_OK && e == cudaSuccess) e = cudaEventRecord(e1, st);
     if (s == SDFT_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
-    if (s == SDFT_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms[c], e0, e1);
+    if (s == SDFT_OK && e == cudaSuccess) e = cudaEventElapsedTime(&c.ms, e0, e1);
     if (e != cudaSuccess && s == SDFT_OK) s = sdft::cuda_fail(e);
-    ms[c] /= float(reps);
+    if (s != SDFT_OK) break;
+    c.ms /= float(reps);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != SDFT_OK) {
-    plan->p.strategy = saved;
+    p.strategy = saved;
+    set_plan_spp(p, saved_spp);
     return s;
   }
-  const int best = (multi && ms[1] < ms[0]) ? SDFT_STRATEGY_QUEUE : SDFT_STRATEGY_LEVELS;
-  plan->p.strategy = best;
-  if (chosen) *chosen = sdft_strategy(best);
-  if (ms_levels) *ms_levels = ms[0];
-  if (ms_queue) *ms_queue = multi ? ms[1] : 0.f;
+  const Cand* best = &cands[0];
+  float best_lv = -1.f, best_q = -1.f;
+  for (const Cand& c : cands) {
+    if (c.ms < best->ms) best = &c;
+    float& slot = c.strategy == SDFT_STRATEGY_LEVELS ? best_lv : best_q;
+    if (slot < 0.f || c.ms < slot) slot = c.ms;
+  }
+  p.strategy = best->strategy;
+  s = set_plan_spp(p, best->spp);
+  if (s != SDFT_OK) return s;
+  sdft::tuning_store(sdft::plan_tuning_key(p.prec, p.s, batch),
+                     sdft::Tuning{best->strategy, 0, 0, int(best->spp), best->ms});
+  if (chosen) *chosen = sdft_strategy(best->strategy);
+  if (ms_levels) *ms_levels = best_lv;
+  if (ms_queue) *ms_queue = best_q < 0.f ? 0.f : best_q;
   return SDFT_OK;
 }
 

@@ -57,6 +57,7 @@ struct Batch {
   int schedule = SDFT_SCHEDULE_AUTO; // item order (sdft_schedule)
   int grid_req = 0;                  // CTAs requested (0: every co-resident CTA)
   uint32_t* noalloc_counters = nullptr;  // device address of the library's fixed counter array
+  int spp = 4;                       // stages per pass of the queue kernel (3 or 4; 3: complex64 only)
 };
 
 }  // namespace sdft
@@ -116,7 +117,7 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
   B.prec = prec;
   B.n = n;
   if (B.device >= 0) {
-    B.grid = prec == SDFT_C64 ? queue_grid_f32() : queue_grid_f64();
+    B.grid = prec == SDFT_C64 ? queue_grid_f32(B.spp) : queue_grid_f64(B.spp);
     if (B.grid <= 0) return SDFT_ERR_CUDA;
     if (B.grid_req > 0 && B.grid_req < B.grid) B.grid = B.grid_req;
   } else {
@@ -445,7 +446,7 @@ static sdft_status run_batch(Batch& B, const void* in, void* out, cudaStream_t s
     if (e != cudaSuccess) return cuda_fail(e);
   }
   const int grid = int(std::min<uint64_t>(uint64_t(B.grid), B.items.size()));
-  return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, st) : launch_queue_f64(prm, grid, st);
+  return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, B.spp, st) : launch_queue_f64(prm, grid, B.spp, st);
 }
 
 // ---- allocation-free execution ------------------------------------------------
@@ -503,7 +504,7 @@ static sdft_status run_batch_noalloc(const Batch& B, const void* in, void* out, 
     if (e != cudaSuccess) return cuda_fail(e);
   }
   const int grid = int(std::min<uint64_t>(uint64_t(B.grid), B.items.size()));
-  return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, st) : launch_queue_f64(prm, grid, st);
+  return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, B.spp, st) : launch_queue_f64(prm, grid, B.spp, st);
 }
 
 // Cached queues of strided multi-level execution, keyed by batch size.
@@ -535,6 +536,7 @@ sdft_status run_strided_queue(sdft_plan_s* plan, uint64_t batch, const void* in,
       b = new (std::nothrow) Batch();
       if (!b) return SDFT_ERR_NOMEM;
       b->device = p.device;
+      b->spp = int(p.spp);
       sdft_status s;
       try {
         std::vector<sdft_plan> plans(batch, plan);
@@ -946,16 +948,23 @@ static sdft_status rebuild_batch(sdft::Batch& B) {
   }
 }
 
+// Item order, CTAs and stages per pass together (one rebuild; the grid and so
+// the item list depend on the kernel's occupancy).
+static sdft_status set_schedule_spp(sdft::Batch& B, int schedule, int grid, int spp) {
+  if (B.schedule == schedule && B.grid_req == grid && B.spp == spp && B.d_items) return SDFT_OK;
+  B.schedule = schedule;
+  B.grid_req = grid;
+  B.spp = spp;
+  return rebuild_batch(B);
+}
+
 sdft_status sdft_batch_set_schedule(sdft_batch batch, sdft_schedule schedule, uint32_t grid) {
   if (!batch) return SDFT_ERR_ARG;
   if (schedule != SDFT_SCHEDULE_AUTO && schedule != SDFT_SCHEDULE_LANES && schedule != SDFT_SCHEDULE_ROUND_ROBIN)
     return SDFT_ERR_ARG;
   if (grid > (1u << 20)) return SDFT_ERR_ARG;
   sdft::Batch& B = batch->b;
-  if (B.schedule == int(schedule) && B.grid_req == int(grid) && B.d_items) return SDFT_OK;
-  B.schedule = int(schedule);
-  B.grid_req = int(grid);
-  return rebuild_batch(B);
+  return set_schedule_spp(B, int(schedule), int(grid), B.spp);
 }
 
 sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d_coeffs, void* stream, int reps,
@@ -964,17 +973,20 @@ sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d
   sdft::Batch& B = batch->b;
   if (B.device < 0) return SDFT_ERR_NO_DEVICE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int full = B.prec == SDFT_C64 ? sdft::queue_grid_f32() : sdft::queue_grid_f64();
-  if (full <= 0) return SDFT_ERR_CUDA;
   struct Cand {
-    int schedule, grid;
+    int schedule, grid, spp;
   };
-  // Item order x CTAs: every co-resident CTA, or half of them (fewer
-  // intermediates in flight, more L1 per resident CTA).
-  const Cand cands[4] = {{SDFT_SCHEDULE_LANES, 0},
-                         {SDFT_SCHEDULE_ROUND_ROBIN, 0},
-                         {SDFT_SCHEDULE_LANES, full / 2},
-                         {SDFT_SCHEDULE_ROUND_ROBIN, full / 2}};
+  // Stages per pass (four; three as well for complex64) x item order x CTAs:
+  // every co-resident CTA, or half of them (fewer intermediates in flight,
+  // more L1 per resident CTA).
+  std::vector<Cand> cands;
+  for (int spp : {4, 3}) {
+    if (spp == 3 && B.prec != SDFT_C64) continue;
+    const int full = B.prec == SDFT_C64 ? sdft::queue_grid_f32(spp) : sdft::queue_grid_f64(spp);
+    if (full <= 0) return SDFT_ERR_CUDA;
+    for (int sched : {int(SDFT_SCHEDULE_LANES), int(SDFT_SCHEDULE_ROUND_ROBIN)})
+      for (int g : {0, full / 2}) cands.push_back(Cand{sched, g, spp});
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -986,7 +998,7 @@ sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d
   float best = -1.f;
   Cand pick = cands[0];
   for (const Cand& c : cands) {
-    s = sdft_batch_set_schedule(batch, sdft_schedule(c.schedule), uint32_t(c.grid));
+    s = set_schedule_spp(B, c.schedule, c.grid, c.spp);
     if (s != SDFT_OK) break;
     s = sdft::run_batch(B, d_samples, d_coeffs, st);     // warm-up
     if (s != SDFT_OK) break;
@@ -1007,12 +1019,41 @@ sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != SDFT_OK) return s;
-  s = sdft_batch_set_schedule(batch, sdft_schedule(pick.schedule), uint32_t(pick.grid));
+  s = set_schedule_spp(B, pick.schedule, pick.grid, pick.spp);
   if (s != SDFT_OK) return s;
+  sdft::tuning_store(sdft::batch_tuning_key(B.prec, B.n, B.total),
+                     sdft::Tuning{0, pick.schedule, pick.grid, pick.spp, best});
   if (chosen) *chosen = sdft_schedule(pick.schedule);
   if (chosen_grid) *chosen_grid = uint32_t(B.grid);
   if (ms_best) *ms_best = best;
   return SDFT_OK;
+}
+
+sdft_status sdft_batch_set_stages_per_pass(sdft_batch batch, uint32_t stages_per_pass) {
+  if (!batch) return SDFT_ERR_ARG;
+  sdft::Batch& B = batch->b;
+  if (stages_per_pass != 4 && !(stages_per_pass == 3 && B.prec == SDFT_C64)) return SDFT_ERR_ARG;
+  return set_schedule_spp(B, B.schedule, B.grid_req, int(stages_per_pass));
+}
+
+sdft_status sdft_batch_get_stages_per_pass(sdft_batch batch, uint32_t* stages_per_pass) {
+  if (!batch || !stages_per_pass) return SDFT_ERR_ARG;
+  *stages_per_pass = uint32_t(batch->b.spp);
+  return SDFT_OK;
+}
+
+sdft_status sdft_batch_apply_tuning(sdft_batch batch, int* found) {
+  if (!batch) return SDFT_ERR_ARG;
+  sdft::Batch& B = batch->b;
+  sdft::Tuning t;
+  const bool hit = sdft::tuning_lookup(sdft::batch_tuning_key(B.prec, B.n, B.total), &t);
+  if (found) *found = hit ? 1 : 0;
+  if (!hit) return SDFT_OK;
+  if (t.spp != 4 && !(t.spp == 3 && B.prec == SDFT_C64)) return SDFT_ERR_ARG;
+  if (t.schedule != SDFT_SCHEDULE_AUTO && t.schedule != SDFT_SCHEDULE_LANES && t.schedule != SDFT_SCHEDULE_ROUND_ROBIN)
+    return SDFT_ERR_ARG;
+  if (t.grid < 0 || t.grid > (1 << 20)) return SDFT_ERR_ARG;
+  return set_schedule_spp(B, t.schedule, t.grid, t.spp);
 }
 
 sdft_status sdft_batch_destroy(sdft_batch batch) {

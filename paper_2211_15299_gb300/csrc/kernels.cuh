@@ -396,28 +396,29 @@ __device__ __forceinline__ dfc ldg_c(const dfc* p) {
 }
 
 // ---- pass schedule ------------------------------------------------------------------
-// Stage bits [PLO, PHI) of a tile run in passes. Pass p covers the 4-bit window
-// starting at the first stage bit not yet done (or the top window of the tile)
-// and runs the stages of that window that are still pending.
-constexpr int pass_done(int TB, int PLO, int PHI, int p) {
+// Stage bits [PLO, PHI) of a tile run in passes of W stage bits (2^W elements
+// per thread). Pass p covers the W-bit window starting at the first stage bit
+// not yet done (or the top window of the tile) and runs the stages of that
+// window that are still pending.
+constexpr int pass_done(int TB, int W, int PLO, int PHI, int p) {
   int d = PLO;
   for (int i = 0; i < p; ++i) {
-    const int b = (d + 4 <= TB) ? d : TB - 4;
-    d = (b + 4 < PHI) ? b + 4 : PHI;
+    const int b = (d + W <= TB) ? d : TB - W;
+    d = (b + W < PHI) ? b + W : PHI;
   }
   return d;
 }
-constexpr int pass_b(int TB, int PLO, int PHI, int p) {
-  const int d = pass_done(TB, PLO, PHI, p);
-  return (d + 4 <= TB) ? d : TB - 4;
+constexpr int pass_b(int TB, int W, int PLO, int PHI, int p) {
+  const int d = pass_done(TB, W, PLO, PHI, p);
+  return (d + W <= TB) ? d : TB - W;
 }
-constexpr int pass_shi(int TB, int PLO, int PHI, int p) {
-  const int b = pass_b(TB, PLO, PHI, p);
-  return (b + 4 < PHI) ? b + 4 : PHI;
+constexpr int pass_shi(int TB, int W, int PLO, int PHI, int p) {
+  const int b = pass_b(TB, W, PLO, PHI, p);
+  return (b + W < PHI) ? b + W : PHI;
 }
-constexpr int n_passes(int TB, int PLO, int PHI) {
+constexpr int n_passes(int TB, int W, int PLO, int PHI) {
   int p = 0;
-  while (pass_done(TB, PLO, PHI, p) < PHI) ++p;
+  while (pass_done(TB, W, PLO, PHI, p) < PHI) ++p;
   return p;
 }
 // Distinct twiddles a thread needs in one pass: stage bit m1 uses 2^(m1-B).
@@ -426,21 +427,24 @@ constexpr int pass_ntw(int B, int SLO, int SHI) {
   for (int m1 = SLO; m1 < SHI; ++m1) n += 1 << (m1 - B);
   return n;
 }
-// Twiddle sources per pass: a B = 0 pass (the same 15 entries for every thread)
-// reads kernel parameters; the top pass (B = TB - 4, the largest table region)
-// holds its entries in registers across tiles; any other pass reads its small
+// Twiddle sources per pass: a B = 0 pass (the same 2^W - 1 entries for every
+// thread) reads kernel parameters; the top pass (B = TB - W, the largest table
+// region) holds its entries in registers across tiles; any other pass reads its
 // table region through the L1 cache, or (level kernel) from a shared-memory
 // copy made when the table changes.
 enum TwSrc { kTwParam = 0, kTwReg = 1, kTwGlobal = 2, kTwShared = 3 };
-constexpr int pass_src(int TB, int B) { return B == 0 ? kTwParam : (B == TB - 4 ? kTwReg : kTwGlobal); }
-constexpr int reg_twiddles(int TB, int PLO, int PHI) {
+constexpr int pass_src(int TB, int W, int B) { return B == 0 ? kTwParam : (B == TB - W ? kTwReg : kTwGlobal); }
+constexpr int reg_twiddles(int TB, int W, int PLO, int PHI) {
   int n = 0;
-  for (int p = 0; p < n_passes(TB, PLO, PHI); ++p) {
-    const int b = pass_b(TB, PLO, PHI, p);
-    if (pass_src(TB, b) == kTwReg) n += pass_ntw(b, pass_done(TB, PLO, PHI, p), pass_shi(TB, PLO, PHI, p));
+  for (int p = 0; p < n_passes(TB, W, PLO, PHI); ++p) {
+    const int b = pass_b(TB, W, PLO, PHI, p);
+    if (pass_src(TB, W, b) == kTwReg) n += pass_ntw(b, pass_done(TB, W, PLO, PHI, p), pass_shi(TB, W, PLO, PHI, p));
   }
   return n;
 }
+// Threads per tile: one per 2^W elements.
+template <class R, int W>
+constexpr uint32_t tile_threads() { return 1u << (KT<R>::TB - W); }
 
 // One complex value from shared memory (byte address).
 template <class R>
@@ -467,21 +471,23 @@ __device__ __forceinline__ dfc ld_shared_c<dfloat>(uint32_t addr) {
   return v;
 }
 
-// Stage range [lo, hi) of the pass that reads its twiddles from memory
-// (neither kernel parameters nor registers); {0, 0} if there is none.
-constexpr int mid_pass_lo(int TB, int PLO, int PHI) {
-  for (int p = 0; p < n_passes(TB, PLO, PHI); ++p)
-    if (pass_src(TB, pass_b(TB, PLO, PHI, p)) == kTwGlobal) return pass_done(TB, PLO, PHI, p);
+// Stage range [lo, hi) covered by the passes that read their twiddles from
+// memory (neither kernel parameters nor registers): lo of the first, hi of the
+// last; {0, 0} if there is none.
+constexpr int mid_pass_lo(int TB, int W, int PLO, int PHI) {
+  for (int p = 0; p < n_passes(TB, W, PLO, PHI); ++p)
+    if (pass_src(TB, W, pass_b(TB, W, PLO, PHI, p)) == kTwGlobal) return pass_done(TB, W, PLO, PHI, p);
   return 0;
 }
-constexpr int mid_pass_hi(int TB, int PLO, int PHI) {
-  for (int p = 0; p < n_passes(TB, PLO, PHI); ++p)
-    if (pass_src(TB, pass_b(TB, PLO, PHI, p)) == kTwGlobal) return pass_shi(TB, PLO, PHI, p);
-  return 0;
+constexpr int mid_pass_hi(int TB, int W, int PLO, int PHI) {
+  int hi = 0;
+  for (int p = 0; p < n_passes(TB, W, PLO, PHI); ++p)
+    if (pass_src(TB, W, pass_b(TB, W, PLO, PHI, p)) == kTwGlobal) hi = pass_shi(TB, W, PLO, PHI, p);
+  return hi;
 }
 
-// ---- one pass: stages with stage bits [SLO, SHI) on 16 elements per thread --------
-// The thread covers tile-index bits [B, B+4); its other bits (F) come from tid.
+// ---- one pass: stages with stage bits [SLO, SHI) on 2^W elements per thread -------
+// The thread covers tile-index bits [B, B+W); its other bits (F) come from tid.
 // Stage bit m1 on the element pair (e, e | 2^q), q = m1 - B, uses the table
 // entry 2^m1 + u with u = (F mod 2^B) + ((e mod 2^q) << B); `w` holds exactly
 // those entries in order (m1 ascending, then e mod 2^q).
@@ -491,27 +497,28 @@ constexpr int mid_pass_hi(int TB, int PLO, int PHI) {
 // the absolute-indexed table region.
 // BAR = 1: the pass ends with named barrier 1 over the NT compute threads
 // instead of a CTA barrier (a kernel with a separate producer warp).
-template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SRC, int BAR = 0, bool FIRST = false,
+template <class R, int W, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SRC, int BAR = 0, bool FIRST = false,
           bool RAWOUT = false>
 __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc,
                                           uint32_t wsm = 0) {
   using C = typename KT<R>::C;
-  static_assert(B >= 0 && B + 4 <= KT<R>::TB, "pass bits out of tile");
-  static_assert(SLO >= B && SHI <= B + 4 && SLO < SHI, "stage bits out of pass");
+  static_assert(B >= 0 && B + W <= KT<R>::TB, "pass bits out of tile");
+  static_assert(SLO >= B && SHI <= B + W && SLO < SHI, "stage bits out of pass");
   constexpr uint32_t LOWM = (1u << B) - 1u;
-  const uint32_t F = (tid & LOWM) | ((tid >> B) << (B + 4));
+  constexpr int NE = 1 << W;
+  const uint32_t F = (tid & LOWM) | ((tid >> B) << (B + W));
   const uint32_t rF = row_part<R>(F), xF = xor_part<R>(F);
-  C v[16];
+  C v[NE];
   if constexpr (B == 0 && KT<R>::ES == 8) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < NE / 2; ++c) {
       const float4 t = *reinterpret_cast<const float4*>(buf + rF + (xF ^ (uint32_t(c) << 4)));
       v[2 * c] = make_float2(t.x, t.y);
       v[2 * c + 1] = make_float2(t.z, t.w);
     }
   } else {
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
+    for (int e = 0; e < NE; ++e) {
       const uint32_t E = uint32_t(e) << B;
       v[e] = load_elem<R, FIRST>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)));
     }
@@ -521,7 +528,7 @@ __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w,
     const int q = m1 - B;
     const int off = pass_ntw(B, SLO, m1);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
+    for (int e = 0; e < NE; ++e) {
       if ((e >> q) & 1) continue;
       const int eh = e | (1 << q);
       C wt;
@@ -539,12 +546,12 @@ __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w,
   }
   if constexpr (B == 0 && KT<R>::ES == 8) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
+    for (int c = 0; c < NE / 2; ++c)
       *reinterpret_cast<float4*>(buf + rF + (xF ^ (uint32_t(c) << 4))) =
           make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
   } else {
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
+    for (int e = 0; e < NE; ++e) {
       const uint32_t E = uint32_t(e) << B;
       store_elem<R, RAWOUT>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)), v[e]);
     }
@@ -553,38 +560,40 @@ __device__ __forceinline__ void tile_pass(char* buf, const typename KT<R>::C* w,
   if constexpr (BAR == 0)
     __syncthreads();
   else
-    ptx::named_bar_sync(1, KT<R>::NT);
+    ptx::named_bar_sync(1, tile_threads<R, W>());
 }
 
 // Load the register twiddles of every B > 0 pass from a table indexed
 // absolutely (entry 2^m1 + u), in the order tile_pass consumes them.
-template <class R, int PLO, int PHI, int P = 0, int ROFF = 0>
+template <class R, int W, int PLO, int PHI, int P = 0, int ROFF = 0>
 __device__ __forceinline__ void load_reg_twiddles(const typename KT<R>::C* __restrict__ tw, uint32_t tid,
                                                   typename KT<R>::C* wreg) {
   constexpr int TB = KT<R>::TB;
-  if constexpr (P < n_passes(TB, PLO, PHI)) {
-    constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
-    if constexpr (pass_src(TB, B) == kTwReg) {
+  if constexpr (P < n_passes(TB, W, PLO, PHI)) {
+    constexpr int B = pass_b(TB, W, PLO, PHI, P), SLO = pass_done(TB, W, PLO, PHI, P),
+                  SHI = pass_shi(TB, W, PLO, PHI, P);
+    if constexpr (pass_src(TB, W, B) == kTwReg) {
       const typename KT<R>::C* base = tw + (tid & ((1u << B) - 1u));
 #pragma unroll
       for (int m1 = SLO; m1 < SHI; ++m1)
 #pragma unroll
         for (int v = 0; v < (1 << (m1 - B)); ++v)
           wreg[ROFF + pass_ntw(B, SLO, m1) + v] = ldg_c(base + (1u << m1) + (uint32_t(v) << B));
-      load_reg_twiddles<R, PLO, PHI, P + 1, ROFF + pass_ntw(B, SLO, SHI)>(tw, tid, wreg);
+      load_reg_twiddles<R, W, PLO, PHI, P + 1, ROFF + pass_ntw(B, SLO, SHI)>(tw, tid, wreg);
     } else {
-      load_reg_twiddles<R, PLO, PHI, P + 1, ROFF>(tw, tid, wreg);
+      load_reg_twiddles<R, W, PLO, PHI, P + 1, ROFF>(tw, tid, wreg);
     }
   }
 }
 
 // Prefetch into L1 the entries a thread will read in every pass that takes
 // its twiddles from memory (register-held top pass and L1-read middle pass).
-template <class R, int PLO, int PHI, int P = 0>
+template <class R, int W, int PLO, int PHI, int P = 0>
 __device__ __forceinline__ void prefetch_twiddles(const typename KT<R>::C* __restrict__ tw, uint32_t tid) {
   constexpr int TB = KT<R>::TB;
-  if constexpr (P < n_passes(TB, PLO, PHI)) {
-    constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
+  if constexpr (P < n_passes(TB, W, PLO, PHI)) {
+    constexpr int B = pass_b(TB, W, PLO, PHI, P), SLO = pass_done(TB, W, PLO, PHI, P),
+                  SHI = pass_shi(TB, W, PLO, PHI, P);
     if constexpr (B > 0) {
       const typename KT<R>::C* base = tw + (tid & ((1u << B) - 1u));
 #pragma unroll
@@ -592,7 +601,7 @@ __device__ __forceinline__ void prefetch_twiddles(const typename KT<R>::C* __res
 #pragma unroll
         for (int v = 0; v < (1 << (m1 - B)); ++v) ptx::prefetch_l1(base + (1u << m1) + (uint32_t(v) << B));
     }
-    prefetch_twiddles<R, PLO, PHI, P + 1>(tw, tid);
+    prefetch_twiddles<R, W, PLO, PHI, P + 1>(tw, tid);
   }
 }
 
@@ -604,35 +613,36 @@ struct NoHook {
 // at `wsm` instead of global memory. `hook` runs after the first pass's
 // barrier (the level kernel issues its next load there).
 // P0SM: the first pass (B = 0) also reads the shared-memory copy at `wsm`.
-template <class R, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0, bool MIDSM = false, class Hook = NoHook,
-          int BAR = 0, bool P0SM = false>
+template <class R, int W, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0, bool MIDSM = false,
+          class Hook = NoHook, int BAR = 0, bool P0SM = false>
 __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* wreg, const typename KT<R>::C* w0,
                                            const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc,
                                            uint32_t wsm = 0, const Hook& hook = Hook()) {
   constexpr int TB = KT<R>::TB;
-  if constexpr (P < n_passes(TB, PLO, PHI)) {
-    constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
+  if constexpr (P < n_passes(TB, W, PLO, PHI)) {
+    constexpr int B = pass_b(TB, W, PLO, PHI, P), SLO = pass_done(TB, W, PLO, PHI, P),
+                  SHI = pass_shi(TB, W, PLO, PHI, P);
     constexpr bool FINAL = (SHI == PHI);
     // double-float: values arrive as complex128 only in the plan's first level and
     // leave as complex128 only from its last; between levels they stay split
     constexpr bool RAWIN = P == 0 && PLO == 0, RAWOUT = FINAL && LAST;
-    constexpr int SRC = pass_src(TB, B);
+    constexpr int SRC = pass_src(TB, W, B);
     if constexpr (SRC == kTwParam) {
       if constexpr (P0SM)
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc, wsm);
+        tile_pass<R, W, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc, wsm);
       else
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, w0, tid, sc);
+        tile_pass<R, W, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, w0, tid, sc);
     } else if constexpr (SRC == kTwGlobal) {
       if constexpr (MIDSM)
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc, wsm);
+        tile_pass<R, W, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc, wsm);
       else
-        tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc);
+        tile_pass<R, W, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc);
     } else {
-      tile_pass<R, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, wreg + ROFF, tid, sc);
+      tile_pass<R, W, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, wreg + ROFF, tid, sc);
     }
     if constexpr (P == 0) hook();
     constexpr int RNEXT = (SRC == kTwReg) ? ROFF + pass_ntw(B, SLO, SHI) : ROFF;
-    run_passes<R, PLO, PHI, LAST, P + 1, RNEXT, MIDSM, Hook, BAR, P0SM>(buf, wreg, w0, twg, tid, sc, wsm, hook);
+    run_passes<R, W, PLO, PHI, LAST, P + 1, RNEXT, MIDSM, Hook, BAR, P0SM>(buf, wreg, w0, twg, tid, sc, wsm, hook);
   }
 }
 
@@ -642,27 +652,28 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
 // pass holds the plan's last stage, whose table entries carry the factor N/k;
 // its second outputs are scaled by sc_top = k/N. FINSC: the pass holds stage 1,
 // the last one applied; both its outputs are scaled by sc_fin = 1/N.
-template <class R, int B, int SLO, int SHI, bool TOPSC, bool FINSC, bool FENCE, int SRC, bool FIRST = false,
+template <class R, int W, int B, int SLO, int SHI, bool TOPSC, bool FINSC, bool FENCE, int SRC, bool FIRST = false,
           bool RAWOUT = false>
 __device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C* w, uint32_t tid, R sc_top,
                                               R sc_fin, uint32_t wsm = 0) {
   using C = typename KT<R>::C;
-  static_assert(B >= 0 && B + 4 <= KT<R>::TB, "pass bits out of tile");
-  static_assert(SLO >= B && SHI <= B + 4 && SLO < SHI, "stage bits out of pass");
+  static_assert(B >= 0 && B + W <= KT<R>::TB, "pass bits out of tile");
+  static_assert(SLO >= B && SHI <= B + W && SLO < SHI, "stage bits out of pass");
   constexpr uint32_t LOWM = (1u << B) - 1u;
-  const uint32_t F = (tid & LOWM) | ((tid >> B) << (B + 4));
+  constexpr int NE = 1 << W;
+  const uint32_t F = (tid & LOWM) | ((tid >> B) << (B + W));
   const uint32_t rF = row_part<R>(F), xF = xor_part<R>(F);
-  C v[16];
+  C v[NE];
   if constexpr (B == 0 && KT<R>::ES == 8) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < NE / 2; ++c) {
       const float4 t = *reinterpret_cast<const float4*>(buf + rF + (xF ^ (uint32_t(c) << 4)));
       v[2 * c] = make_float2(t.x, t.y);
       v[2 * c + 1] = make_float2(t.z, t.w);
     }
   } else {
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
+    for (int e = 0; e < NE; ++e) {
       const uint32_t E = uint32_t(e) << B;
       v[e] = load_elem<R, FIRST>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)));
     }
@@ -673,7 +684,7 @@ __device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C
     const int off = pass_ntw(B, SLO, m1);
     const bool top = TOPSC && m1 == SHI - 1, fin = FINSC && m1 == SLO;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
+    for (int e = 0; e < NE; ++e) {
       if ((e >> q) & 1) continue;
       const int eh = e | (1 << q);
       C wt;
@@ -691,12 +702,12 @@ __device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C
   }
   if constexpr (B == 0 && KT<R>::ES == 8) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
+    for (int c = 0; c < NE / 2; ++c)
       *reinterpret_cast<float4*>(buf + rF + (xF ^ (uint32_t(c) << 4))) =
           make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
   } else {
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
+    for (int e = 0; e < NE; ++e) {
       const uint32_t E = uint32_t(e) << B;
       store_elem<R, RAWOUT>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)), v[e]);
     }
@@ -706,11 +717,11 @@ __device__ __forceinline__ void tile_pass_inv(char* buf, const typename KT<R>::C
 }
 
 // Register-twiddle offset of pass P (entries of the earlier register passes).
-constexpr int reg_off(int TB, int PLO, int PHI, int P) {
+constexpr int reg_off(int TB, int W, int PLO, int PHI, int P) {
   int n = 0;
   for (int p = 0; p < P; ++p) {
-    const int b = pass_b(TB, PLO, PHI, p);
-    if (pass_src(TB, b) == kTwReg) n += pass_ntw(b, pass_done(TB, PLO, PHI, p), pass_shi(TB, PLO, PHI, p));
+    const int b = pass_b(TB, W, PLO, PHI, p);
+    if (pass_src(TB, W, b) == kTwReg) n += pass_ntw(b, pass_done(TB, W, PLO, PHI, p), pass_shi(TB, W, PLO, PHI, p));
   }
   return n;
 }
@@ -718,34 +729,35 @@ constexpr int reg_off(int TB, int PLO, int PHI, int P) {
 // The passes of a tile in reverse order (P = n-1 .. 0). LAST: the level holds
 // the plan's last stage; PLO == 0: the level holds stage 1. `hook` runs after
 // the first pass applied.
-template <class R, int PLO, int PHI, bool LAST, bool MIDSM, int P, class Hook>
+template <class R, int W, int PLO, int PHI, bool LAST, bool MIDSM, int P, class Hook>
 __device__ __forceinline__ void run_passes_inv(char* buf, const typename KT<R>::C* wreg,
                                                const typename KT<R>::C* w0,
                                                const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc_top,
                                                R sc_fin, uint32_t wsm, const Hook& hook) {
   constexpr int TB = KT<R>::TB;
-  constexpr int NP = n_passes(TB, PLO, PHI);
+  constexpr int NP = n_passes(TB, W, PLO, PHI);
   if constexpr (P >= 0) {
-    constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
+    constexpr int B = pass_b(TB, W, PLO, PHI, P), SLO = pass_done(TB, W, PLO, PHI, P),
+                  SHI = pass_shi(TB, W, PLO, PHI, P);
     constexpr bool TOPSC = LAST && P == NP - 1, FINSC = PLO == 0 && P == 0, FENCE = P == 0;
     // double-float: complex128 in at the first level applied (the plan's last),
     // out at the last applied (level 0); split values between levels
     constexpr bool FIRST = P == NP - 1 && LAST, RAWOUT = P == 0 && PLO == 0;
-    constexpr int SRC = pass_src(TB, B);
+    constexpr int SRC = pass_src(TB, W, B);
     if constexpr (SRC == kTwParam) {
-      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST, RAWOUT>(buf, w0, tid, sc_top, sc_fin);
+      tile_pass_inv<R, W, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST, RAWOUT>(buf, w0, tid, sc_top, sc_fin);
     } else if constexpr (SRC == kTwGlobal) {
       if constexpr (MIDSM)
-        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, kTwShared, FIRST, RAWOUT>(buf, twg, tid, sc_top, sc_fin,
-                                                                                 wsm);
+        tile_pass_inv<R, W, B, SLO, SHI, TOPSC, FINSC, FENCE, kTwShared, FIRST, RAWOUT>(buf, twg, tid, sc_top,
+                                                                                    sc_fin, wsm);
       else
-        tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST, RAWOUT>(buf, twg, tid, sc_top, sc_fin);
+        tile_pass_inv<R, W, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST, RAWOUT>(buf, twg, tid, sc_top, sc_fin);
     } else {
-      tile_pass_inv<R, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST, RAWOUT>(buf, wreg + reg_off(TB, PLO, PHI, P),
-                                                                             tid, sc_top, sc_fin);
+      tile_pass_inv<R, W, B, SLO, SHI, TOPSC, FINSC, FENCE, SRC, FIRST, RAWOUT>(
+          buf, wreg + reg_off(TB, W, PLO, PHI, P), tid, sc_top, sc_fin);
     }
     if constexpr (P == NP - 1) hook();
-    run_passes_inv<R, PLO, PHI, LAST, MIDSM, P - 1, Hook>(buf, wreg, w0, twg, tid, sc_top, sc_fin, wsm, hook);
+    run_passes_inv<R, W, PLO, PHI, LAST, MIDSM, P - 1, Hook>(buf, wreg, w0, twg, tid, sc_top, sc_fin, wsm, hook);
   }
 }
 
@@ -767,6 +779,7 @@ struct LevelArgs {
   uint64_t timeout_ns;     // bound on every mbarrier wait
   int64_t lim1, lim3;      // tile origins lie in [0, lim1) x [0, lim3) (range checks)
   uint64_t tw_tables;      // tables in `tw` (range checks)
+  uint64_t chunk;          // later levels: consecutive b per chunk of the tile walk (0: interleaved walk)
   typename KT<R>::C tw0[16];  // tw0[i] = level-0 table entry i + 1 (stage bits 0..3), i < 15
 };
 
@@ -798,12 +811,13 @@ __device__ __forceinline__ char* align1024(char* p) {
 // once its store has finished reading shared memory, so the next tile's load is
 // in flight behind the tile being computed.
 // INV: the adjoint (synthesis) passes instead of the forward ones.
-template <class R, int PLO, int PHI, bool LAST, bool INV = false>
-__global__ void __launch_bounds__(KT<R>::NT, 2)
+template <class R, int W, int PLO, int PHI, bool LAST, bool INV = false>
+__global__ void __launch_bounds__(tile_threads<R, W>(), 2)
     k_level(const __grid_constant__ CUtensorMap src, const __grid_constant__ CUtensorMap dst,
             const __grid_constant__ LevelArgs<R> args) {
   using C = typename KT<R>::C;
-  constexpr int NREG = reg_twiddles(KT<R>::TB, PLO, PHI);
+  constexpr int NREG = reg_twiddles(KT<R>::TB, W, PLO, PHI);
+  constexpr uint32_t NT = tile_threads<R, W>();
   extern __shared__ char smem_raw[];
   char* smem = align1024(smem_raw);
   const uint32_t bar0 = ptx::smem_addr(smem + kLevelBufs * kTileBytes);
@@ -823,22 +837,60 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     }
     if (!level_tables_in_bounds<R, PLO, PHI>(args)) return;   // debug build only
   }
-  // CTA c takes tiles c, c + G, c + 2G, ...: the tiles in flight at any moment
-  // are neighbours in memory (on the strided later levels this was measured 6 %
-  // faster than contiguous ranges per CTA, although the group-block table then
-  // changes from one tile to the next).
+  // Tile i = a * nB + b (a: the table, b: the instance or row block). Two walks:
+  //  * chunk == 0 (level 0, one table): CTA c takes tiles c, c + G, c + 2G, ...,
+  //    so the tiles in flight at any moment are neighbours in memory;
+  //  * chunk > 0 (later levels, one table per group block a): chunks of `chunk`
+  //    consecutive b on one a, chunk q = bB * nA + a; CTA c takes chunks
+  //    c, c + G, ... and their tiles in order. A CTA then reloads its group
+  //    block's table once per chunk instead of once per tile, and the CTAs in
+  //    flight cover whole rows of one instance block (all a for the same b).
   const uint64_t G = gridDim.x;
   const uint64_t t0 = blockIdx.x;
-  if (t0 >= args.n_tiles) return;
-  const uint64_t n = (args.n_tiles - t0 + G - 1) / G;
+  const uint64_t CH = args.chunk;
+  const uint64_t nA = args.n_tiles / args.nB;
+  const uint64_t nBB = CH ? (args.nB + CH - 1) / CH : 0;
+  if (CH ? t0 >= nA * nBB : t0 >= args.n_tiles) return;
+  uint64_t n = 0;
+  if (CH) {
+    for (uint64_t q = t0; q < nA * nBB; q += G) {
+      const uint64_t bB = q / nA;
+      n += (bB + 1) * CH <= args.nB ? CH : args.nB - bB * CH;
+    }
+  } else {
+    n = (args.n_tiles - t0 + G - 1) / G;
+  }
 
-  // Tile i = a * nB + b: walk (a, b) by G incrementally instead of dividing.
+  // The walk advanced incrementally (no 64-bit division per tile).
   struct Cursor {
     uint64_t a, b;
+    uint64_t bB, t, len;   // chunked walk: chunk (a, bB), position t of len
   };
-  auto cursor_at = [&](uint64_t i) { return Cursor{i / args.nB, i % args.nB}; };
-  const uint64_t step_a = G / args.nB, step_b = G % args.nB;
+  auto cursor_at = [&](uint64_t i) {
+    if (CH) {
+      const uint64_t bB = i / nA;
+      return Cursor{i % nA, bB * CH, bB, 0, (bB + 1) * CH <= args.nB ? CH : args.nB - bB * CH};
+    }
+    return Cursor{i / args.nB, i % args.nB, 0, 0, 0};
+  };
+  const uint64_t step_a = CH ? G % nA : G / args.nB, step_b = CH ? G / nA : G % args.nB;
   auto advance = [&](Cursor& c) {
+    if (CH) {
+      if (++c.t < c.len) {
+        ++c.b;
+        return;
+      }
+      c.a += step_a;
+      c.bB += step_b;
+      if (c.a >= nA) {
+        c.a -= nA;
+        ++c.bB;
+      }
+      c.t = 0;
+      c.b = c.bB * CH;
+      c.len = (c.bB + 1) * CH <= args.nB ? CH : (c.bB * CH < args.nB ? args.nB - c.bB * CH : 0);
+      return;
+    }
     c.a += step_a;
     c.b += step_b;
     if (c.b >= args.nB) {
@@ -875,7 +927,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   const R sc = R(args.scale);
   const C* tw = static_cast<const C*>(args.tw) - args.tw_first;
   C wreg[NREG > 0 ? NREG : 1];
-  constexpr int MLO = mid_pass_lo(KT<R>::TB, PLO, PHI), MHI = mid_pass_hi(KT<R>::TB, PLO, PHI);
+  constexpr int MLO = mid_pass_lo(KT<R>::TB, W, PLO, PHI), MHI = mid_pass_hi(KT<R>::TB, W, PLO, PHI);
   // a middle pass whose region fits the shared copy reads it from there
   constexpr bool MIDSM = MLO < MHI && (1u << MHI) * sizeof(C) <= kMidTwBytes;
   C* midtw = reinterpret_cast<C*>(smem + kLevelBufs * kTileBytes + 64);
@@ -893,9 +945,9 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     if (!in_bounds(tab < args.tw_tables, args.status)) tab = 0;
     if (tab != cur_tab) {  // uniform across the CTA; the previous tile's passes are done
       twt = tw + tab * args.tw_stride;
-      load_reg_twiddles<R, PLO, PHI>(twt, tid, wreg);
+      load_reg_twiddles<R, W, PLO, PHI>(twt, tid, wreg);
       if constexpr (MIDSM) {   // the middle pass's entries into shared memory (barrier below)
-        for (uint32_t e = (1u << MLO) + tid; e < (1u << MHI); e += KT<R>::NT) midtw[e] = twt[e];
+        for (uint32_t e = (1u << MLO) + tid; e < (1u << MHI); e += NT) midtw[e] = twt[e];
       }
       cur_tab = tab;
     }
@@ -915,10 +967,10 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
       }
     };
     if constexpr (INV)
-      run_passes_inv<R, PLO, PHI, LAST, MIDSM, n_passes(KT<R>::TB, PLO, PHI) - 1>(
+      run_passes_inv<R, W, PLO, PHI, LAST, MIDSM, n_passes(KT<R>::TB, W, PLO, PHI) - 1>(
           buf, wreg, args.tw0, twt, tid, R(1.0 / args.scale), R(args.inv_n), midtw_addr, refill);
     else
-      run_passes<R, PLO, PHI, LAST, 0, 0, MIDSM>(buf, wreg, args.tw0, twt, tid, sc, midtw_addr, refill);
+      run_passes<R, W, PLO, PHI, LAST, 0, 0, MIDSM>(buf, wreg, args.tw0, twt, tid, sc, midtw_addr, refill);
     if (tid == 0) {
       int c1, c3;
       coords(cur, c1, c3);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "plan.hpp"
 
@@ -50,5 +51,19 @@ void forget_batched(uint64_t serial);
 // these plans, building it if needed; report whether a list is cached.
 sdft_status pin_batched(const sdft_plan* plans, uint64_t n, int pin);
 void batched_cache_info(const sdft_plan* plans, uint64_t n, int* cached, int* pinned, uint64_t* n_lists);
+
+// Autotuner choices (autotune.cpp): strategy (plans), item order and grid
+// (batches), stages per pass, and the time measured for them.
+struct Tuning {
+  int strategy = 0;
+  int schedule = 0;
+  int grid = 0;
+  int spp = 4;
+  float ms = 0.f;
+};
+std::string plan_tuning_key(sdft_prec prec, uint32_t s, uint64_t batch);
+std::string batch_tuning_key(sdft_prec prec, uint64_t n, uint64_t total);
+void tuning_store(const std::string& key, const Tuning& t);
+bool tuning_lookup(const std::string& key, Tuning* out);
 
 }  // namespace sdft

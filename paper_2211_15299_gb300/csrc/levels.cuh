@@ -7,49 +7,77 @@
 
 namespace sdft {
 
-template <class R, int PLO, int PHI, bool LAST, bool INV = false>
+template <class R, int W, int PLO, int PHI, bool LAST, bool INV = false>
 sdft_status launch_level(int grid, const CUtensorMap& src, const CUtensorMap& dst, const LevelArgs<R>& a,
                          cudaStream_t st) {
-  auto fn = k_level<R, PLO, PHI, LAST, INV>;
+  auto fn = k_level<R, W, PLO, PHI, LAST, INV>;
   sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(kLevelSmem));
   if (s != SDFT_OK) return s;
-  fn<<<grid, KT<R>::NT, kLevelSmem, st>>>(src, dst, a);
+  fn<<<grid, tile_threads<R, W>(), kLevelSmem, st>>>(src, dst, a);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
 }
 
 // Level 0: stage bits [0, PHI).
-template <class R, bool INV = false, int PHI = 5>
-sdft_status dispatch_first(int phi, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
-                           const LevelArgs<R>& a, cudaStream_t st) {
+template <class R, int W, bool INV = false, int PHI = 5>
+sdft_status dispatch_first_w(int phi, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
+                             const LevelArgs<R>& a, cudaStream_t st) {
   constexpr int TB = KT<R>::TB;
   if constexpr (PHI > TB) {
     return SDFT_ERR_UNSUPPORTED;
   } else {
     if (phi == PHI) {
       if constexpr (PHI == TB) {
-        if (!last) return launch_level<R, 0, PHI, false, INV>(grid, src, dst, a, st);
+        if (!last) return launch_level<R, W, 0, PHI, false, INV>(grid, src, dst, a, st);
       }
       if (!last) return SDFT_ERR_UNSUPPORTED;
-      return launch_level<R, 0, PHI, true, INV>(grid, src, dst, a, st);
+      return launch_level<R, W, 0, PHI, true, INV>(grid, src, dst, a, st);
     }
-    return dispatch_first<R, INV, PHI + 1>(phi, last, grid, src, dst, a, st);
+    return dispatch_first_w<R, W, INV, PHI + 1>(phi, last, grid, src, dst, a, st);
   }
 }
 
 // Later levels: virtual stage bits [TB - Q, TB).
-template <class R, bool INV = false, int Q = 1>
-sdft_status dispatch_later(int q, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
-                           const LevelArgs<R>& a, cudaStream_t st) {
+template <class R, int W, bool INV = false, int Q = 1>
+sdft_status dispatch_later_w(int q, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
+                             const LevelArgs<R>& a, cudaStream_t st) {
   constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
   if constexpr (Q > TB - CB) {
     return SDFT_ERR_UNSUPPORTED;
   } else {
     if (q == Q)
-      return last ? launch_level<R, TB - Q, TB, true, INV>(grid, src, dst, a, st)
-                  : launch_level<R, TB - Q, TB, false, INV>(grid, src, dst, a, st);
-    return dispatch_later<R, INV, Q + 1>(q, last, grid, src, dst, a, st);
+      return last ? launch_level<R, W, TB - Q, TB, true, INV>(grid, src, dst, a, st)
+                  : launch_level<R, W, TB - Q, TB, false, INV>(grid, src, dst, a, st);
+    return dispatch_later_w<R, W, INV, Q + 1>(q, last, grid, src, dst, a, st);
   }
+}
+
+// Stages per pass (W, 2^W values per thread): 4 everywhere; the forward
+// complex64 level kernels also come with 3 (twice the threads per tile, one
+// more pass), chosen per plan (sdft_plan_set_stages_per_pass, the autotuner).
+// Those are compiled in a unit of their own (level_f32w3.cu).
+template <class R, bool INV>
+constexpr bool has_w3() { return std::is_same<R, float>::value && !INV; }
+sdft_status dispatch_first_f32w3(int phi, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
+                                 const LevelArgs<float>& a, cudaStream_t st);
+sdft_status dispatch_later_f32w3(int q, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
+                                 const LevelArgs<float>& a, cudaStream_t st);
+
+template <class R, bool INV = false>
+sdft_status dispatch_first(int w, int phi, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
+                           const LevelArgs<R>& a, cudaStream_t st) {
+  if constexpr (has_w3<R, INV>()) {
+    if (w == 3) return dispatch_first_f32w3(phi, last, grid, src, dst, a, st);
+  }
+  return dispatch_first_w<R, 4, INV>(phi, last, grid, src, dst, a, st);
+}
+template <class R, bool INV = false>
+sdft_status dispatch_later(int w, int q, bool last, int grid, const CUtensorMap& src, const CUtensorMap& dst,
+                           const LevelArgs<R>& a, cudaStream_t st) {
+  if constexpr (has_w3<R, INV>()) {
+    if (w == 3) return dispatch_later_f32w3(q, last, grid, src, dst, a, st);
+  }
+  return dispatch_later_w<R, 4, INV>(q, last, grid, src, dst, a, st);
 }
 
 template <class R, int S = 0>
@@ -125,6 +153,10 @@ sdft_status level0_setup(const Plan& p, uint64_t batch, const void* src, void* d
   return SDFT_OK;
 }
 
+// Instances (row blocks) per chunk of a later level's tile walk: a CTA keeps a
+// group block's twiddle table for this many consecutive tiles.
+constexpr uint64_t kLaterChunk = 8;
+
 // Tensor maps and kernel arguments of later level j (stage bits [lo, hi) on
 // group blocks: 2^lg column groups x 2^Q rows spaced 2^lo elements apart).
 template <class R>
@@ -160,6 +192,7 @@ sdft_status later_setup(const Plan& p, uint64_t batch, size_t j, const void* src
   a.lim1 = int64_t(1) << (L.lo - CB);
   a.lim3 = int64_t(Z);
   a.tw_tables = L.n_gb;
+  a.chunk = kLaterChunk;
   return SDFT_OK;
 }
 
@@ -212,7 +245,7 @@ sdft_status launch_plan(const Plan& p, uint64_t batch, const void* in, void* out
     LevelArgs<R> a;
     sdft_status s = level0_setup<R>(p, batch, in, out, ms, md, a);
     if (s != SDFT_OK) return s;
-    s = dispatch_first<R>(int(p.levels[0].hi), p.levels[0].last, level_grid(a.n_tiles), ms, md, a, st);
+    s = dispatch_first<R>(int(p.spp), int(p.levels[0].hi), p.levels[0].last, level_grid(a.n_tiles), ms, md, a, st);
     if (s != SDFT_OK) return s;
   }
   // Later levels in place on the output.
@@ -222,7 +255,7 @@ sdft_status launch_plan(const Plan& p, uint64_t batch, const void* in, void* out
     LevelArgs<R> a;
     sdft_status s = later_setup<R>(p, batch, j, out, out, m, m2, a);
     if (s != SDFT_OK) return s;
-    s = dispatch_later<R>(int(L.hi - L.lo), L.last, level_grid(a.n_tiles), m, m, a, st);
+    s = dispatch_later<R>(int(p.spp), int(L.hi - L.lo), L.last, level_grid(a.n_tiles), m, m, a, st);
     if (s != SDFT_OK) return s;
   }
   return SDFT_OK;
@@ -267,7 +300,7 @@ sdft_status launch_plan_inv(const Plan& p, uint64_t batch, const void* in, void*
     LevelArgs<R> a;
     sdft_status s = later_setup<R>(p, batch, j, src_base, out, ms, md, a);
     if (s != SDFT_OK) return s;
-    s = dispatch_later<R, true>(int(L.hi - L.lo), L.last, level_grid(a.n_tiles), ms, md, a, st);
+    s = dispatch_later<R, true>(4, int(L.hi - L.lo), L.last, level_grid(a.n_tiles), ms, md, a, st);
     if (s != SDFT_OK) return s;
     src_base = out;
   }
@@ -275,7 +308,7 @@ sdft_status launch_plan_inv(const Plan& p, uint64_t batch, const void* in, void*
   LevelArgs<R> a;
   sdft_status s = level0_setup<R>(p, batch, src_base, out, ms, md, a);
   if (s != SDFT_OK) return s;
-  return dispatch_first<R, true>(int(p.levels[0].hi), p.levels[0].last, level_grid(a.n_tiles), ms, md, a, st);
+  return dispatch_first<R, true>(4, int(p.levels[0].hi), p.levels[0].last, level_grid(a.n_tiles), ms, md, a, st);
 }
 
 }  // namespace sdft

@@ -53,6 +53,7 @@ struct Plan {
   std::vector<uint64_t> Jc;       // canonical order
   std::vector<uint64_t> I;        // sample order
   std::vector<Level> levels;      // empty when s <= kSmallMax (register path)
+  uint32_t spp = 4;               // stages per pass of the level kernels (3 or 4; 3: complex64 forward only)
   uint64_t tw_elems = 0;          // complex entries in the device table buffer
   int device = -1;
   void* d_tw = nullptr;           // device twiddles (float2 or double2)

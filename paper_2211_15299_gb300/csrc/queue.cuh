@@ -69,24 +69,28 @@ struct QArgs {
 constexpr int kMetaSlots = 6;
 static_assert(sizeof(QItem) % 16 == 0, "items are copied in 16-byte pieces");
 // Per tile buffer, a shared-memory copy of the table entries its first and
-// middle passes read (copied by the producer with the tile, on its barrier).
-template <class R>
-constexpr uint32_t q_tw_bytes() { return 256 * KT<R>::ES; }
+// middle passes read (copied by the producer with the tile, on its barrier):
+// entries below 2^8 with four stages per pass, below 2^9 with three (the two
+// middle passes of a 2^12-value tile).
+template <class R, int W>
+constexpr uint32_t q_tw_entries() { return W == 3 ? 512u : 256u; }
+template <class R, int W>
+constexpr uint32_t q_tw_bytes() { return q_tw_entries<R, W>() * KT<R>::ES; }
 constexpr uint32_t kQTwOff = kBufs * kTileBytes + 64 + kMetaSlots * sizeof(QItem);
 static_assert(kQTwOff % 16 == 0, "table copies need 16-byte alignment");
-template <class R>
-constexpr uint32_t q_smem() { return kQTwOff + kBufs * q_tw_bytes<R>() + 1024; }
+template <class R, int W>
+constexpr uint32_t q_smem() { return kQTwOff + kBufs * q_tw_bytes<R, W>() + 1024; }
 
 // Entries [lo, hi) of an item's table staged in shared memory, for a tile
 // whose stages are [PLO, TB): the first pass's entries (PLO = 0) and the
-// memory-read pass's, when they fit the copy; hi = 0: none.
-constexpr int q_stage_hi(int TB, int PLO) {
-  const int mlo = mid_pass_lo(TB, PLO, TB), mhi = mid_pass_hi(TB, PLO, TB);
-  if (mlo >= mhi || (1 << mhi) > 256) return PLO == 0 ? 16 : 0;
+// memory-read passes', when they fit the copy; hi = 0: none.
+constexpr int q_stage_hi(int TB, int W, int PLO, int cap) {
+  const int mlo = mid_pass_lo(TB, W, PLO, TB), mhi = mid_pass_hi(TB, W, PLO, TB);
+  if (mlo >= mhi || (1 << mhi) > cap) return PLO == 0 ? (1 << W) : 0;
   return 1 << mhi;
 }
-constexpr int q_stage_lo(int TB, int PLO) {
-  return PLO == 0 ? 0 : (q_stage_hi(TB, PLO) ? (1 << mid_pass_lo(TB, PLO, TB)) : 0);
+constexpr int q_stage_lo(int TB, int W, int PLO, int cap) {
+  return PLO == 0 ? 0 : (q_stage_hi(TB, W, PLO, cap) ? (1 << mid_pass_lo(TB, W, PLO, TB)) : 0);
 }
 
 // Kernel parameters: the arguments and the tensor maps over the packed buffers
@@ -113,16 +117,17 @@ constexpr int q_variant_later(int Q, bool last) { return 16 + 2 * (Q - 1) + (las
 // Elements of the tile with index T belong to instance (T >> SB) of the tile
 // (SB >= TB: one instance). tab[g] is the absolute-indexed table of the g-th
 // instance among the thread's elements (g = E >> SB), sc[g] its N/k.
-template <class R, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SB>
+template <class R, int W, int B, int SLO, int SHI, bool SCALE, bool FENCE, int SB>
 __device__ __forceinline__ void tile_pass_q(char* buf, const typename KT<R>::C* const* tab, const R* sc,
                                             uint32_t tid) {
   using C = typename KT<R>::C;
   constexpr uint32_t LOWM = (1u << B) - 1u;
-  const uint32_t F = (tid & LOWM) | ((tid >> B) << (B + 4));
+  constexpr int NE = 1 << W;
+  const uint32_t F = (tid & LOWM) | ((tid >> B) << (B + W));
   const uint32_t rF = row_part<R>(F), xF = xor_part<R>(F);
-  C v[16];
+  C v[NE];
 #pragma unroll
-  for (int e = 0; e < 16; ++e) {
+  for (int e = 0; e < NE; ++e) {
     const uint32_t E = uint32_t(e) << B;
     v[e] = *reinterpret_cast<const C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E)));
   }
@@ -130,7 +135,7 @@ __device__ __forceinline__ void tile_pass_q(char* buf, const typename KT<R>::C* 
   for (int m1 = SLO; m1 < SHI; ++m1) {
     const int q = m1 - B;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
+    for (int e = 0; e < NE; ++e) {
       if ((e >> q) & 1) continue;
       const int eh = e | (1 << q);
       const int g = (SB >= 32) ? 0 : int((uint32_t(e) << B) >> SB);
@@ -142,29 +147,30 @@ __device__ __forceinline__ void tile_pass_q(char* buf, const typename KT<R>::C* 
     }
   }
 #pragma unroll
-  for (int e = 0; e < 16; ++e) {
+  for (int e = 0; e < NE; ++e) {
     const uint32_t E = uint32_t(e) << B;
     *reinterpret_cast<C*>(buf + rF + row_part<R>(E) + (xF ^ xor_part<R>(E))) = v[e];
   }
   if constexpr (FENCE) ptx::fence_proxy_async_smem();
-  ptx::named_bar_sync(1, KT<R>::NT);     // the compute threads only (not the producer warp)
+  ptx::named_bar_sync(1, tile_threads<R, W>());     // the compute threads only (not the producer warp)
 }
 
-template <class R, int PLO, int PHI, bool LAST, int SB, int P = 0>
+template <class R, int W, int PLO, int PHI, bool LAST, int SB, int P = 0>
 __device__ __forceinline__ void run_passes_q(char* buf, const QArgs& a, const QItem& it, uint32_t tid) {
   using C = typename KT<R>::C;
   constexpr int TB = KT<R>::TB;
-  if constexpr (P < n_passes(TB, PLO, PHI)) {
-    constexpr int B = pass_b(TB, PLO, PHI, P), SLO = pass_done(TB, PLO, PHI, P), SHI = pass_shi(TB, PLO, PHI, P);
+  if constexpr (P < n_passes(TB, W, PLO, PHI)) {
+    constexpr int B = pass_b(TB, W, PLO, PHI, P), SLO = pass_done(TB, W, PLO, PHI, P),
+                  SHI = pass_shi(TB, W, PLO, PHI, P);
     constexpr bool FINAL = (SHI == PHI);
-    constexpr int NG = (SB >= 32 || B + 4 <= SB) ? 1 : (1 << (B + 4 - SB));
+    constexpr int NG = (SB >= 32 || B + W <= SB) ? 1 : (1 << (B + W - SB));
     const C* tab[NG];
     R sc[NG];
     if constexpr (SB >= 32) {
       tab[0] = static_cast<const C*>(it.tw);
       sc[0] = R(it.scale);
     } else {
-      const uint32_t F = (tid & ((1u << B) - 1u)) | ((tid >> B) << (B + 4));
+      const uint32_t F = (tid & ((1u << B) - 1u)) | ((tid >> B) << (B + W));
       const uint32_t g0 = (SB >= TB) ? 0u : (F >> SB);
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
@@ -175,22 +181,22 @@ __device__ __forceinline__ void run_passes_q(char* buf, const QArgs& a, const QI
         sc[g] = R(ins->scale);
       }
     }
-    tile_pass_q<R, B, SLO, SHI, LAST && FINAL, FINAL, SB>(buf, tab, sc, tid);
-    run_passes_q<R, PLO, PHI, LAST, SB, P + 1>(buf, a, it, tid);
+    tile_pass_q<R, W, B, SLO, SHI, LAST && FINAL, FINAL, SB>(buf, tab, sc, tid);
+    run_passes_q<R, W, PLO, PHI, LAST, SB, P + 1>(buf, a, it, tid);
   }
 }
 
 // Level 0 with 5 <= s <= TB: tiles of whole instances.
-template <class R, int S = 5>
+template <class R, int W, int S = 5>
 __device__ __forceinline__ bool dispatch_first_q(int v, char* buf, const QArgs& a, const QItem& it, uint32_t tid) {
   if constexpr (S > KT<R>::TB) {
     return false;
   } else {
     if (v == q_variant_first(S)) {
-      run_passes_q<R, 0, S, true, S>(buf, a, it, tid);
+      run_passes_q<R, W, 0, S, true, S>(buf, a, it, tid);
       return true;
     }
-    return dispatch_first_q<R, S + 1>(v, buf, a, it, tid);
+    return dispatch_first_q<R, W, S + 1>(v, buf, a, it, tid);
   }
 }
 
@@ -245,47 +251,48 @@ __device__ __forceinline__ void run_small(const QArgs& a, const QItem& it, uint3
 // A single-table item (a 2^TB chunk, a one-instance tile, a later-level group
 // block): the passes of k_level with the top pass's twiddles loaded into
 // registers for this item (the previous item prefetched them into L1).
-template <class R, int PLO, int PHI, bool LAST>
+template <class R, int W, int PLO, int PHI, bool LAST>
 __device__ __forceinline__ void run_single(char* buf, const typename KT<R>::C* tab, R sc, uint32_t tid,
                                            uint32_t wsm) {
   using C = typename KT<R>::C;
   constexpr int TB = KT<R>::TB;
-  constexpr int NREG = reg_twiddles(TB, PLO, PHI);
+  constexpr int NREG = reg_twiddles(TB, W, PLO, PHI);
+  constexpr int CAP = int(q_tw_entries<R, W>());
   C wreg[NREG > 0 ? NREG : 1];
-  load_reg_twiddles<R, PLO, PHI>(tab, tid, wreg);
+  load_reg_twiddles<R, W, PLO, PHI>(tab, tid, wreg);
   // staged entries (q_stage_lo/hi) come from shared memory at wsm; the rest from
   // global memory (pass 0 reads entry 2^m1 + u as w0[2^m1 - 1 + u]: w0 = tab + 1)
-  constexpr bool MID = q_stage_hi(TB, PLO) > 16 || (PLO > 0 && q_stage_hi(TB, PLO) > 0);
+  constexpr bool MID = q_stage_hi(TB, W, PLO, CAP) > (1 << W) || (PLO > 0 && q_stage_hi(TB, W, PLO, CAP) > 0);
   constexpr bool P0 = PLO == 0;
-  run_passes<R, PLO, PHI, LAST, 0, 0, MID, NoHook, 1, P0>(buf, wreg, tab + 1, tab, tid, sc, wsm);
+  run_passes<R, W, PLO, PHI, LAST, 0, 0, MID, NoHook, 1, P0>(buf, wreg, tab + 1, tab, tid, sc, wsm);
 }
 
-template <class R, int Q = 1>
+template <class R, int W, int Q = 1>
 __device__ __forceinline__ void dispatch_later_single(int v, char* buf, const typename KT<R>::C* tab, R sc,
                                                       uint32_t tid, uint32_t wsm) {
   constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
   if constexpr (Q <= TB - CB) {
-    if (v == q_variant_later(Q, true)) return run_single<R, TB - Q, TB, true>(buf, tab, sc, tid, wsm);
-    if (v == q_variant_later(Q, false)) return run_single<R, TB - Q, TB, false>(buf, tab, sc, tid, wsm);
-    dispatch_later_single<R, Q + 1>(v, buf, tab, sc, tid, wsm);
+    if (v == q_variant_later(Q, true)) return run_single<R, W, TB - Q, TB, true>(buf, tab, sc, tid, wsm);
+    if (v == q_variant_later(Q, false)) return run_single<R, W, TB - Q, TB, false>(buf, tab, sc, tid, wsm);
+    dispatch_later_single<R, W, Q + 1>(v, buf, tab, sc, tid, wsm);
   }
 }
 
-template <class R, int Q = 1>
+template <class R, int W, int Q = 1>
 __device__ __forceinline__ void dispatch_later_prefetch(int v, const typename KT<R>::C* tab, uint32_t tid) {
   constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
   if constexpr (Q <= TB - CB) {
     if (v == q_variant_later(Q, true) || v == q_variant_later(Q, false))
-      return prefetch_twiddles<R, TB - Q, TB>(tab, tid);
-    dispatch_later_prefetch<R, Q + 1>(v, tab, tid);
+      return prefetch_twiddles<R, W, TB - Q, TB>(tab, tid);
+    dispatch_later_prefetch<R, W, Q + 1>(v, tab, tid);
   }
 }
 
 // Shared-memory layout after the tile buffers: full[3] and empty[3] mbarriers,
 // the abort flag, then the record ring.
 constexpr uint32_t kQFull = 0, kQEmpty = 24, kQAbort = 48;
-template <class R>
-constexpr uint32_t q_threads() { return KT<R>::NT + 32; }   // compute threads + one producer warp
+template <class R, int W>
+constexpr uint32_t q_threads() { return tile_threads<R, W>() + 32; }   // compute threads + one producer warp
 
 __device__ __forceinline__ bool q_is_tma(const QItem& it) { return it.variant != kVSmall && it.variant != kVNop; }
 
@@ -318,7 +325,7 @@ __device__ __forceinline__ bool q_item_in_bounds(const QParams& prm, const QItem
 // published before the dependency wait of the item four places later in the
 // same CTA, so items that wait on one another sit at least 4 x grid list
 // positions apart and every wait ends (all CTAs are resident).
-template <class R>
+template <class R, int W>
 __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint64_t n) {
   const uint64_t c = blockIdx.x, G = gridDim.x;
   const uint32_t bars = ptx::smem_addr(smem + kBufs * kTileBytes);
@@ -395,15 +402,15 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
         }
         const uint32_t bytes = (it.variant < 16) ? (128u << (it.map / 2)) : kTileBytes;
         // the table entries the first and middle passes read, copied with the tile
-        constexpr int TBs = KT<R>::TB;
+        constexpr int TBs = KT<R>::TB, CAP = int(q_tw_entries<R, W>());
         int slo = 0, shi = 0;
         if (it.variant == kVFirstChunk || it.variant == q_variant_first(TBs)) {
-          slo = q_stage_lo(TBs, 0);
-          shi = q_stage_hi(TBs, 0);
+          slo = q_stage_lo(TBs, W, 0, CAP);
+          shi = q_stage_hi(TBs, W, 0, CAP);
         } else if (it.variant >= 16) {
           const int plo = TBs - ((it.variant - 16) / 2 + 1);
-          slo = q_stage_lo(TBs, plo);
-          shi = q_stage_hi(TBs, plo);
+          slo = q_stage_lo(TBs, W, plo, CAP);
+          shi = q_stage_hi(TBs, W, plo, CAP);
         }
         const uint32_t tw_bytes = shi > slo ? uint32_t(shi - slo) * KT<R>::ES : 0u;
         ptx::mbar_arrive_expect_tx(full, bytes + tw_bytes);
@@ -411,7 +418,7 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
         ptx::tma_load_4d_hint(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], full, 0, it.c1, 0, it.c3,
                               ptx::policy_evict_first());
         if (tw_bytes)
-          ptx::bulk_load(ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R>()) + uint32_t(slo) * KT<R>::ES,
+          ptx::bulk_load(ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R, W>()) + uint32_t(slo) * KT<R>::ES,
                          static_cast<const char*>(it.tw) + size_t(slo) * KT<R>::ES, tw_bytes, full);
         inflight |= 1u << b;
         load_par = (load_par & ~(1u << b)) | (uint32_t((j / kBufs) & 1) << b);
@@ -458,16 +465,16 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
   }
 }
 
-template <class R>
-__global__ void __launch_bounds__(q_threads<R>(), 2) k_queue(const __grid_constant__ QParams prm) {
+template <class R, int W>
+__global__ void __launch_bounds__(q_threads<R, W>(), 2) k_queue(const __grid_constant__ QParams prm) {
   const QArgs& a = prm.a;
   extern __shared__ char smem_raw[];
   char* smem = align1024(smem_raw);
   const uint32_t bars = ptx::smem_addr(smem + kBufs * kTileBytes);
   const uint32_t tid = threadIdx.x;
-  constexpr uint32_t NT = KT<R>::NT;
+  constexpr uint32_t NT = tile_threads<R, W>();
   {
-    const uint32_t used = uint32_t(smem - smem_raw) + kQTwOff + kBufs * q_tw_bytes<R>();
+    const uint32_t used = uint32_t(smem - smem_raw) + kQTwOff + kBufs * q_tw_bytes<R, W>();
     int bad = 0;
     if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
     else if (reinterpret_cast<uintptr_t>(&prm.maps[0]) & 63u) bad = kBadMap;
@@ -490,7 +497,7 @@ __global__ void __launch_bounds__(q_threads<R>(), 2) k_queue(const __grid_consta
   }
   __syncthreads();
   if (tid >= NT) {                     // the producer warp
-    if (tid == NT) q_producer<R>(prm, smem, n);
+    if (tid == NT) q_producer<R, W>(prm, smem, n);
     return;
   }
   using C = typename KT<R>::C;
@@ -508,19 +515,19 @@ __global__ void __launch_bounds__(q_threads<R>(), 2) k_queue(const __grid_consta
     const C* tab = static_cast<const C*>(it.tw);
     const R sc = R(it.scale);
     char* buf = smem + b * kTileBytes;
-    const uint32_t wsm = ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R>());
+    const uint32_t wsm = ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R, W>());
     if (v == kVNop) {
       // nothing to do
     } else if (v == kVSmall) {
       run_small<R>(a, it, tid);
     } else if (v == kVFirstChunk) {
-      run_single<R, 0, TB, false>(buf, tab, sc, tid, wsm);
+      run_single<R, W, 0, TB, false>(buf, tab, sc, tid, wsm);
     } else if (v == q_variant_first(TB)) {
-      run_single<R, 0, TB, true>(buf, tab, sc, tid, wsm);
+      run_single<R, W, 0, TB, true>(buf, tab, sc, tid, wsm);
     } else if (v >= 16) {
-      dispatch_later_single<R>(v, buf, tab, sc, tid, wsm);
+      dispatch_later_single<R, W>(v, buf, tab, sc, tid, wsm);
     } else {
-      dispatch_first_q<R>(v, buf, a, it, tid);   // several instances per tile
+      dispatch_first_q<R, W>(v, buf, a, it, tid);   // several instances per tile
     }
     ptx::mbar_arrive(bars + kQEmpty + 8 * b);   // after the final pass's proxy fence and barrier
     // the next item's register and L1 twiddles, if its tile has landed already
@@ -531,8 +538,8 @@ __global__ void __launch_bounds__(q_threads<R>(), 2) k_queue(const __grid_consta
         const int nv = nx.variant;
         const C* nt = static_cast<const C*>(nx.tw);
         if (nt && nt != tab) {
-          if (nv == kVFirstChunk || nv == q_variant_first(TB)) prefetch_twiddles<R, 0, TB>(nt, tid);
-          else if (nv >= 16 && nv != kVNop) dispatch_later_prefetch<R>(nv, nt, tid);
+          if (nv == kVFirstChunk || nv == q_variant_first(TB)) prefetch_twiddles<R, W, 0, TB>(nt, tid);
+          else if (nv >= 16 && nv != kVNop) dispatch_later_prefetch<R, W>(nv, nt, tid);
         }
       }
     }
@@ -543,32 +550,33 @@ __global__ void __launch_bounds__(q_threads<R>(), 2) k_queue(const __grid_consta
 
 namespace sdft {
 
-// Host launchers (queue_f32.cu, queue_f64.cu).
-sdft_status launch_queue_f32(const QParams& prm, int grid, cudaStream_t st);
-sdft_status launch_queue_f64(const QParams& prm, int grid, cudaStream_t st);
+// Host launchers (queue_f32.cu, queue_f64.cu). `w`: stages per pass (3 or 4
+// for complex64, 4 for complex128).
+sdft_status launch_queue_f32(const QParams& prm, int grid, int w, cudaStream_t st);
+sdft_status launch_queue_f64(const QParams& prm, int grid, int w, cudaStream_t st);
 // Co-resident CTAs of the queue kernel on the current device (occupancy x SMs).
-int queue_grid_f32();
-int queue_grid_f64();
+int queue_grid_f32(int w);
+int queue_grid_f64(int w);
 
-template <class R>
+template <class R, int W>
 int queue_grid() {
-  auto fn = k_queue<R>;
-  if (ensure_smem(reinterpret_cast<const void*>(fn), int(q_smem<R>())) != SDFT_OK) return 0;
+  auto fn = k_queue<R, W>;
+  if (ensure_smem(reinterpret_cast<const void*>(fn), int(q_smem<R, W>())) != SDFT_OK) return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, q_threads<R>(), q_smem<R>()) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, q_threads<R, W>(), q_smem<R, W>()) != cudaSuccess)
     return 0;
   return per_sm * sm_count();
 }
 
-template <class R>
+template <class R, int W>
 sdft_status launch_queue(const QParams& prm, int grid, cudaStream_t st) {
-  auto fn = k_queue<R>;
-  sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(q_smem<R>()));
+  auto fn = k_queue<R, W>;
+  sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(q_smem<R, W>()));
   if (s != SDFT_OK) return s;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
-  cfg.blockDim = dim3(q_threads<R>());
-  cfg.dynamicSmemBytes = q_smem<R>();
+  cfg.blockDim = dim3(q_threads<R, W>());
+  cfg.dynamicSmemBytes = q_smem<R, W>();
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs resident: dependency waits make progress

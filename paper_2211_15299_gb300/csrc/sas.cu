@@ -363,8 +363,8 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   using C = typename KT<R>::C;
   constexpr int TB = KT<R>::TB;
   constexpr uint32_t NT = KT<R>::NT;
-  constexpr int NREG = reg_twiddles(TB, 0, TB);
-  constexpr int MLO = mid_pass_lo(TB, 0, TB), MHI = mid_pass_hi(TB, 0, TB);
+  constexpr int NREG = reg_twiddles(TB, 4, 0, TB);
+  constexpr int MLO = mid_pass_lo(TB, 4, 0, TB), MHI = mid_pass_hi(TB, 4, 0, TB);
   constexpr bool MIDSM = MLO < MHI && (1u << MHI) * sizeof(C) <= kMidTwBytes;
   extern __shared__ char smem_raw[];
   char* smem = align1024(smem_raw);
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   }
   const C* tw = static_cast<const C*>(fa.a.tw);
   C wreg[NREG > 0 ? NREG : 1];
-  load_reg_twiddles<R, 0, TB>(tw, tid, wreg);
+  load_reg_twiddles<R, 4, 0, TB>(tw, tid, wreg);
   if constexpr (MIDSM) {
     for (uint32_t e = (1u << MLO) + tid; e < (1u << MHI); e += NT) midtw[e] = tw[e];
   }
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     auto refill = [&]() {
       if (tid == 0 && j >= 1 && j + kLevelBufs - 1 < n) issue_load(j + kLevelBufs - 1);
     };
-    run_passes<R, 0, TB, true, 0, 0, MIDSM>(buf, wreg, fa.a.tw0, tw, tid, sc, midtw_addr, refill);
+    run_passes<R, 4, 0, TB, true, 0, 0, MIDSM>(buf, wreg, fa.a.tw0, tw, tid, sc, midtw_addr, refill);
     C* ob = fa.out + (blockIdx.x + j * G) * fa.k;
     for (uint64_t i = tid; i < fa.k; i += NT) {
       const C w = ws[i];
