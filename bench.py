@@ -516,6 +516,7 @@ def run_uneven(args):
     n_items, n_ctr, grid = b.stats()
     from paper_2211_15299_gb300 import _native as N
     spp_tuned = N.sdft_batch_get_stages_per_pass(b.handle)
+    staged_tuned = N.sdft_batch_get_table_staging(b.handle)
 
     def step(s=None):
         b.execute(x, y, stream=(s or stream).cuda_stream)
@@ -545,8 +546,8 @@ def run_uneven(args):
             "ms_per_step": 1e3 * mean, "alg_GBps": (16 * total + tw_bytes) / mean / 1e9,
             "alg_bytes_per_step": 16 * total + tw_bytes, "work_items": n_items,
             "dependency_counters": n_ctr, "grid": grid, "plan_build_s": t_plan,
-            "autotune": {"schedule": schedule, "grid": grid, "stages_per_pass": spp_tuned, "ms_per_run": ms_tuned,
-                         "seconds": t_tune},
+            "autotune": {"schedule": schedule, "grid": grid, "stages_per_pass": spp_tuned,
+                         "table_staging": staged_tuned, "ms_per_run": ms_tuned, "seconds": t_tune},
             "launches_per_step": 1, "graph": "one CUDA graph replay per step"}
 
 

@@ -385,6 +385,16 @@ sdft_status sdft_batch_execute_noalloc(sdft_batch batch, const void* d_samples, 
 sdft_status sdft_batch_set_stages_per_pass(sdft_batch batch, uint32_t stages_per_pass);
 sdft_status sdft_batch_get_stages_per_pass(sdft_batch batch, uint32_t* stages_per_pass);
 
+/* Where a batch's queue kernel keeps each item's twiddle table: 0 (default)
+ * registers and L1 for the last pass, shared-memory copies of the small first
+ * and middle regions, two CTAs per SM; 1 (complex64 only) the whole table
+ * (2^12 entries, 32 KiB) copied into shared memory with each tile, so no pass
+ * waits on a global load, one CTA per SM. The same bits either way. Rebuilds the
+ * item list as for sdft_batch_set_stages_per_pass. sdft_batch_autotune chooses
+ * it with the other settings. Errors: SDFT_ERR_ARG. */
+sdft_status sdft_batch_set_table_staging(sdft_batch batch, int staged);
+sdft_status sdft_batch_get_table_staging(sdft_batch batch, int* staged);
+
 /* Apply the tuning cache's choice for this batch (key: precision,
  * floor(log2 n), floor(log2 total values)) without timing; *found as for
  * sdft_plan_apply_tuning. Rebuilds the item list when the choice differs. */
@@ -420,8 +430,9 @@ sdft_status sdft_batch_set_schedule(sdft_batch batch, sdft_schedule schedule, ui
 
 /*
  * sdft_batch_autotune - time the batch under every queue shape (lanes or round
- * robin, on all co-resident CTAs or on half of them) and stages-per-pass
- * choice (4, and 3 for complex64); one warm-up and `reps` timed runs each,
+ * robin, on all co-resident CTAs or on half of them), stages-per-pass choice
+ * (4, and 3 for complex64) and table placement (sdft_batch_set_table_staging;
+ * both for complex64); one warm-up and `reps` timed runs each,
  * CUDA events on `stream`, the buffers overwritten. Keeps the fastest, reports
  * it (any output may be NULL; `ms_best` is the mean time of one run; the
  * stages per pass: sdft_batch_get_stages_per_pass) and stores it in the
@@ -601,7 +612,8 @@ sdft_status sdft_server_destroy(sdft_server srv);
  * object, one member per key ("plan/c64/s20/b6": plan of complex64, log2 k =
  * 20, batch in [64, 128); "batch/c64/n13/t26": uneven batch of 2^13..2^14 - 1
  * instances and 2^26..2^27 - 1 values), each an object with the fields
- * strategy, schedule, grid, stages_per_pass and ms (the time measured).
+ * strategy, schedule, grid, stages_per_pass, table_staging and ms (the time
+ * measured).
  * _load merges such a file into the cache (SDFT_ERR_ARG for a file that
  * cannot be read or parsed; the cache is then unchanged). _clear empties it;
  * _size reports its entries. Host-only; thread-safe. The paper has no

@@ -72,6 +72,8 @@ SIGNATURES = {
     "sdft_batch_set_stages_per_pass": (c_int, [c_vp, c_u32]),
     "sdft_batch_get_stages_per_pass": (c_int, [c_vp, P_u32]),
     "sdft_batch_apply_tuning": (c_int, [c_vp, ctypes.POINTER(c_int)]),
+    "sdft_batch_set_table_staging": (c_int, [c_vp, c_int]),
+    "sdft_batch_get_table_staging": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "sdft_autotune_cache_save": (c_int, [ctypes.c_char_p]),
     "sdft_autotune_cache_load": (c_int, [ctypes.c_char_p]),
     "sdft_autotune_cache_clear": (c_int, []),
@@ -263,6 +265,16 @@ def sdft_batch_get_stages_per_pass(batch: int) -> int:
     v = c_u32(0)
     _check(_lib.sdft_batch_get_stages_per_pass(batch, ctypes.byref(v)), "sdft_batch_get_stages_per_pass")
     return int(v.value)
+
+
+def sdft_batch_set_table_staging(batch: int, staged: bool) -> None:
+    _check(_lib.sdft_batch_set_table_staging(batch, 1 if staged else 0), "sdft_batch_set_table_staging")
+
+
+def sdft_batch_get_table_staging(batch: int) -> bool:
+    v = c_int(0)
+    _check(_lib.sdft_batch_get_table_staging(batch, ctypes.byref(v)), "sdft_batch_get_table_staging")
+    return bool(v.value)
 
 
 def sdft_batch_apply_tuning(batch: int) -> bool:

@@ -28,8 +28,9 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 # checks in every kernel (see sdft_debug_bounds_violations in include/sdft.h).
 if os.environ.get("SDFT_BOUNDS_CHECK", "0") not in ("", "0"):
     NVCC_FLAGS = NVCC_FLAGS + ["-DSDFT_BOUNDS_CHECK=1"]
-SOURCES = ["plan.cpp", "autotune.cpp", "api.cu", "batch.cu", "level_f32.cu", "level_f32w3.cu", "level_f64.cu", "queue_f32.cu",
-           "queue_f32w3.cu", "queue_f64.cu", "server.cu", "sas.cu", "inverse_f32.cu", "inverse_f64.cu", "level_df.cu"]
+SOURCES = ["plan.cpp", "autotune.cpp", "api.cu", "batch.cu", "level_f32.cu", "level_f32w3.cu", "level_f64.cu",
+           "queue_f32.cu", "queue_f32w3.cu", "queue_f32st.cu", "queue_f32w3st.cu", "queue_f64.cu", "server.cu",
+           "sas.cu", "inverse_f32.cu", "inverse_f64.cu", "level_df.cu"]
 
 
 def _nvcc() -> str:

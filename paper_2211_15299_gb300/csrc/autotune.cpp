@@ -6,7 +6,8 @@
 // sdft_plan_apply_tuning / sdft_batch_apply_tuning apply a stored choice
 // without timing; sdft_autotune_cache_save / _load keep the cache in a JSON
 // file between processes:
-//   {"plan/c64/s20/b6": {"strategy": 1, "schedule": 0, "grid": 0, "stages_per_pass": 4, "ms": 0.35}, ...}
+//   {"plan/c64/s20/b6": {"strategy": 1, "schedule": 0, "grid": 0, "stages_per_pass": 4,
+//                        "table_staging": 0, "ms": 0.35}, ...}
 #include <cctype>
 #include <cstdio>
 #include <cstdlib>
@@ -105,8 +106,9 @@ sdft_status sdft_autotune_cache_save(const char* path) {
       char buf[256];
       std::snprintf(buf, sizeof(buf),
                     "%s \"%s\": {\"strategy\": %d, \"schedule\": %d, \"grid\": %d, \"stages_per_pass\": %d, "
-                    "\"ms\": %.6g}",
-                    first ? "" : ",\n", kv.first.c_str(), t.strategy, t.schedule, t.grid, t.spp, double(t.ms));
+                    "\"table_staging\": %d, \"ms\": %.6g}",
+                    first ? "" : ",\n", kv.first.c_str(), t.strategy, t.schedule, t.grid, t.spp, t.staged,
+                    double(t.ms));
       out += buf;
       first = false;
     }
@@ -144,6 +146,7 @@ sdft_status sdft_autotune_cache_load(const char* path) {
           else if (field == "schedule") t.schedule = int(v);
           else if (field == "grid") t.grid = int(v);
           else if (field == "stages_per_pass") t.spp = int(v);
+          else if (field == "table_staging") t.staged = int(v);
           else if (field == "ms") t.ms = float(v);
           else return SDFT_ERR_ARG;
         } while (r.lit(','));

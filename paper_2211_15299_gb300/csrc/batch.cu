@@ -58,6 +58,7 @@ struct Batch {
   int grid_req = 0;                  // CTAs requested (0: every co-resident CTA)
   uint32_t* noalloc_counters = nullptr;  // device address of the library's fixed counter array
   int spp = 4;                       // stages per pass of the queue kernel (3 or 4; 3: complex64 only)
+  bool staged = false;               // whole twiddle tables in shared memory (complex64 only)
 };
 
 }  // namespace sdft
@@ -117,7 +118,7 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
   B.prec = prec;
   B.n = n;
   if (B.device >= 0) {
-    B.grid = prec == SDFT_C64 ? queue_grid_f32(B.spp) : queue_grid_f64(B.spp);
+    B.grid = prec == SDFT_C64 ? queue_grid_f32(B.spp, B.staged) : queue_grid_f64(B.spp, B.staged);
     if (B.grid <= 0) return SDFT_ERR_CUDA;
     if (B.grid_req > 0 && B.grid_req < B.grid) B.grid = B.grid_req;
   } else {
@@ -446,7 +447,8 @@ static sdft_status run_batch(Batch& B, const void* in, void* out, cudaStream_t s
     if (e != cudaSuccess) return cuda_fail(e);
   }
   const int grid = int(std::min<uint64_t>(uint64_t(B.grid), B.items.size()));
-  return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, B.spp, st) : launch_queue_f64(prm, grid, B.spp, st);
+  return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, B.spp, B.staged, st)
+                            : launch_queue_f64(prm, grid, B.spp, B.staged, st);
 }
 
 // ---- allocation-free execution ------------------------------------------------
@@ -504,7 +506,8 @@ static sdft_status run_batch_noalloc(const Batch& B, const void* in, void* out, 
     if (e != cudaSuccess) return cuda_fail(e);
   }
   const int grid = int(std::min<uint64_t>(uint64_t(B.grid), B.items.size()));
-  return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, B.spp, st) : launch_queue_f64(prm, grid, B.spp, st);
+  return B.prec == SDFT_C64 ? launch_queue_f32(prm, grid, B.spp, B.staged, st)
+                            : launch_queue_f64(prm, grid, B.spp, B.staged, st);
 }
 
 // Cached queues of strided multi-level execution, keyed by batch size.
@@ -950,11 +953,13 @@ static sdft_status rebuild_batch(sdft::Batch& B) {
 
 // Item order, CTAs and stages per pass together (one rebuild; the grid and so
 // the item list depend on the kernel's occupancy).
-static sdft_status set_schedule_spp(sdft::Batch& B, int schedule, int grid, int spp) {
-  if (B.schedule == schedule && B.grid_req == grid && B.spp == spp && B.d_items) return SDFT_OK;
+static sdft_status set_config(sdft::Batch& B, int schedule, int grid, int spp, bool staged) {
+  if (B.schedule == schedule && B.grid_req == grid && B.spp == spp && B.staged == staged && B.d_items)
+    return SDFT_OK;
   B.schedule = schedule;
   B.grid_req = grid;
   B.spp = spp;
+  B.staged = staged;
   return rebuild_batch(B);
 }
 
@@ -964,7 +969,7 @@ sdft_status sdft_batch_set_schedule(sdft_batch batch, sdft_schedule schedule, ui
     return SDFT_ERR_ARG;
   if (grid > (1u << 20)) return SDFT_ERR_ARG;
   sdft::Batch& B = batch->b;
-  return set_schedule_spp(B, int(schedule), int(grid), B.spp);
+  return set_config(B, int(schedule), int(grid), B.spp, B.staged);
 }
 
 sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d_coeffs, void* stream, int reps,
@@ -975,18 +980,21 @@ sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   struct Cand {
     int schedule, grid, spp;
+    bool staged;
   };
-  // Stages per pass (four; three as well for complex64) x item order x CTAs:
+  // Stages per pass (four; three as well for complex64) x tables in registers
+  // and L1 or staged whole in shared memory (complex64) x item order x CTAs:
   // every co-resident CTA, or half of them (fewer intermediates in flight,
   // more L1 per resident CTA).
   std::vector<Cand> cands;
-  for (int spp : {4, 3}) {
-    if (spp == 3 && B.prec != SDFT_C64) continue;
-    const int full = B.prec == SDFT_C64 ? sdft::queue_grid_f32(spp) : sdft::queue_grid_f64(spp);
-    if (full <= 0) return SDFT_ERR_CUDA;
-    for (int sched : {int(SDFT_SCHEDULE_LANES), int(SDFT_SCHEDULE_ROUND_ROBIN)})
-      for (int g : {0, full / 2}) cands.push_back(Cand{sched, g, spp});
-  }
+  for (int spp : {4, 3})
+    for (bool staged : {false, true}) {
+      if ((spp == 3 || staged) && B.prec != SDFT_C64) continue;
+      const int full = B.prec == SDFT_C64 ? sdft::queue_grid_f32(spp, staged) : sdft::queue_grid_f64(spp, staged);
+      if (full <= 0) return SDFT_ERR_CUDA;
+      for (int sched : {int(SDFT_SCHEDULE_LANES), int(SDFT_SCHEDULE_ROUND_ROBIN)})
+        for (int g : {0, full / 2}) cands.push_back(Cand{sched, g, spp, staged});
+    }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -998,7 +1006,7 @@ sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d
   float best = -1.f;
   Cand pick = cands[0];
   for (const Cand& c : cands) {
-    s = set_schedule_spp(B, c.schedule, c.grid, c.spp);
+    s = set_config(B, c.schedule, c.grid, c.spp, c.staged);
     if (s != SDFT_OK) break;
     s = sdft::run_batch(B, d_samples, d_coeffs, st);     // warm-up
     if (s != SDFT_OK) break;
@@ -1019,10 +1027,10 @@ sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != SDFT_OK) return s;
-  s = set_schedule_spp(B, pick.schedule, pick.grid, pick.spp);
+  s = set_config(B, pick.schedule, pick.grid, pick.spp, pick.staged);
   if (s != SDFT_OK) return s;
   sdft::tuning_store(sdft::batch_tuning_key(B.prec, B.n, B.total),
-                     sdft::Tuning{0, pick.schedule, pick.grid, pick.spp, best});
+                     sdft::Tuning{0, pick.schedule, pick.grid, pick.spp, best, pick.staged ? 1 : 0});
   if (chosen) *chosen = sdft_schedule(pick.schedule);
   if (chosen_grid) *chosen_grid = uint32_t(B.grid);
   if (ms_best) *ms_best = best;
@@ -1033,7 +1041,20 @@ sdft_status sdft_batch_set_stages_per_pass(sdft_batch batch, uint32_t stages_per
   if (!batch) return SDFT_ERR_ARG;
   sdft::Batch& B = batch->b;
   if (stages_per_pass != 4 && !(stages_per_pass == 3 && B.prec == SDFT_C64)) return SDFT_ERR_ARG;
-  return set_schedule_spp(B, B.schedule, B.grid_req, int(stages_per_pass));
+  return set_config(B, B.schedule, B.grid_req, int(stages_per_pass), B.staged);
+}
+
+sdft_status sdft_batch_set_table_staging(sdft_batch batch, int staged) {
+  if (!batch) return SDFT_ERR_ARG;
+  sdft::Batch& B = batch->b;
+  if (staged && B.prec != SDFT_C64) return SDFT_ERR_ARG;
+  return set_config(B, B.schedule, B.grid_req, B.spp, staged != 0);
+}
+
+sdft_status sdft_batch_get_table_staging(sdft_batch batch, int* staged) {
+  if (!batch || !staged) return SDFT_ERR_ARG;
+  *staged = batch->b.staged ? 1 : 0;
+  return SDFT_OK;
 }
 
 sdft_status sdft_batch_get_stages_per_pass(sdft_batch batch, uint32_t* stages_per_pass) {
@@ -1050,10 +1071,11 @@ sdft_status sdft_batch_apply_tuning(sdft_batch batch, int* found) {
   if (found) *found = hit ? 1 : 0;
   if (!hit) return SDFT_OK;
   if (t.spp != 4 && !(t.spp == 3 && B.prec == SDFT_C64)) return SDFT_ERR_ARG;
+  if (t.staged != 0 && !(t.staged == 1 && B.prec == SDFT_C64)) return SDFT_ERR_ARG;
   if (t.schedule != SDFT_SCHEDULE_AUTO && t.schedule != SDFT_SCHEDULE_LANES && t.schedule != SDFT_SCHEDULE_ROUND_ROBIN)
     return SDFT_ERR_ARG;
   if (t.grid < 0 || t.grid > (1 << 20)) return SDFT_ERR_ARG;
-  return set_schedule_spp(B, t.schedule, t.grid, t.spp);
+  return set_config(B, t.schedule, t.grid, t.spp, t.staged != 0);
 }
 
 sdft_status sdft_batch_destroy(sdft_batch batch) {

@@ -10,11 +10,15 @@
 // its twiddles arrive pre-scaled and the other operand is scaled by an FMA.
 //
 // Tiles: 32 KiB of complex values staged by TMA into shared memory with the
-// 128-byte swizzle (16-byte chunk index XOR row index mod 8). A thread owns 16
-// elements whose tile index differs in 4 consecutive bits [B, B+4) and runs up
-// to four stages on them in registers ("pass"); passes are separated by CTA
-// barriers. With the swizzle every pass reads and writes shared memory without
-// bank conflicts for complex64.
+// 128-byte swizzle (16-byte chunk index XOR row index mod 8). A thread owns 2^W
+// elements (W = 4 or 3) whose tile index differs in W consecutive bits [B, B+W)
+// and runs up to W stages on them in registers ("pass"); passes are separated by
+// CTA barriers. With the swizzle the address pattern of every pass maps each
+// warp access onto the minimum number of shared-memory wavefronts for complex64
+// (16-byte accesses in the first pass, 8-byte ones after). The extra wavefronts
+// ncu still counts as bank conflicts on these accesses (about a fifth) are all
+// of the arbitration type (l1tex__data_bank_conflicts_type_arbitration): the
+// tile loads and stores of the TMA engine use the same banks at the same time.
 #pragma once
 
 #include <cuda.h>
@@ -613,8 +617,10 @@ struct NoHook {
 // at `wsm` instead of global memory. `hook` runs after the first pass's
 // barrier (the level kernel issues its next load there).
 // P0SM: the first pass (B = 0) also reads the shared-memory copy at `wsm`.
+// TOPSM: the register pass (top pass) reads the shared-memory copy at `wsm`
+// too (a kernel that stages whole tables).
 template <class R, int W, int PLO, int PHI, bool LAST, int P = 0, int ROFF = 0, bool MIDSM = false,
-          class Hook = NoHook, int BAR = 0, bool P0SM = false>
+          class Hook = NoHook, int BAR = 0, bool P0SM = false, bool TOPSM = false>
 __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* wreg, const typename KT<R>::C* w0,
                                            const typename KT<R>::C* __restrict__ twg, uint32_t tid, R sc,
                                            uint32_t wsm = 0, const Hook& hook = Hook()) {
@@ -637,12 +643,15 @@ __device__ __forceinline__ void run_passes(char* buf, const typename KT<R>::C* w
         tile_pass<R, W, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc, wsm);
       else
         tile_pass<R, W, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc);
+    } else if constexpr (TOPSM) {
+      tile_pass<R, W, B, SLO, SHI, LAST && FINAL, FINAL, kTwShared, BAR, RAWIN, RAWOUT>(buf, twg, tid, sc, wsm);
     } else {
       tile_pass<R, W, B, SLO, SHI, LAST && FINAL, FINAL, SRC, BAR, RAWIN, RAWOUT>(buf, wreg + ROFF, tid, sc);
     }
     if constexpr (P == 0) hook();
     constexpr int RNEXT = (SRC == kTwReg) ? ROFF + pass_ntw(B, SLO, SHI) : ROFF;
-    run_passes<R, W, PLO, PHI, LAST, P + 1, RNEXT, MIDSM, Hook, BAR, P0SM>(buf, wreg, w0, twg, tid, sc, wsm, hook);
+    run_passes<R, W, PLO, PHI, LAST, P + 1, RNEXT, MIDSM, Hook, BAR, P0SM, TOPSM>(buf, wreg, w0, twg, tid, sc, wsm,
+                                                                                 hook);
   }
 }
 
@@ -845,18 +854,25 @@ __global__ void __launch_bounds__(tile_threads<R, W>(), 2)
   //    c, c + G, ... and their tiles in order. A CTA then reloads its group
   //    block's table once per chunk instead of once per tile, and the CTAs in
   //    flight cover whole rows of one instance block (all a for the same b).
+  //    The instance blocks run last to first: the previous level wrote them
+  //    first to last, so the first blocks read here are still in L2.
   const uint64_t G = gridDim.x;
   const uint64_t t0 = blockIdx.x;
-  const uint64_t CH = args.chunk;
+  // the walk is fixed at compile time: level 0 (PLO = 0) interleaved, later
+  // levels chunked (args.chunk > 0)
+  const uint64_t CH = PLO > 0 ? args.chunk : 0;
   const uint64_t nA = args.n_tiles / args.nB;
   const uint64_t nBB = CH ? (args.nB + CH - 1) / CH : 0;
   if (CH ? t0 >= nA * nBB : t0 >= args.n_tiles) return;
+  // chunked walk: instance block bB of the walk is block nBB - 1 - bB in memory
+  auto block_len = [&](uint64_t bB) {
+    if (bB >= nBB) return uint64_t(0);
+    const uint64_t r = nBB - 1 - bB;
+    return (r + 1) * CH <= args.nB ? CH : args.nB - r * CH;
+  };
   uint64_t n = 0;
   if (CH) {
-    for (uint64_t q = t0; q < nA * nBB; q += G) {
-      const uint64_t bB = q / nA;
-      n += (bB + 1) * CH <= args.nB ? CH : args.nB - bB * CH;
-    }
+    for (uint64_t q = t0; q < nA * nBB; q += G) n += block_len(q / nA);
   } else {
     n = (args.n_tiles - t0 + G - 1) / G;
   }
@@ -867,15 +883,15 @@ __global__ void __launch_bounds__(tile_threads<R, W>(), 2)
     uint64_t bB, t, len;   // chunked walk: chunk (a, bB), position t of len
   };
   auto cursor_at = [&](uint64_t i) {
-    if (CH) {
+    if (PLO > 0 && CH) {
       const uint64_t bB = i / nA;
-      return Cursor{i % nA, bB * CH, bB, 0, (bB + 1) * CH <= args.nB ? CH : args.nB - bB * CH};
+      return Cursor{i % nA, (nBB - 1 - bB) * CH, bB, 0, block_len(bB)};
     }
     return Cursor{i / args.nB, i % args.nB, 0, 0, 0};
   };
   const uint64_t step_a = CH ? G % nA : G / args.nB, step_b = CH ? G / nA : G % args.nB;
   auto advance = [&](Cursor& c) {
-    if (CH) {
+    if (PLO > 0 && CH) {
       if (++c.t < c.len) {
         ++c.b;
         return;
@@ -887,8 +903,8 @@ __global__ void __launch_bounds__(tile_threads<R, W>(), 2)
         ++c.bB;
       }
       c.t = 0;
-      c.b = c.bB * CH;
-      c.len = (c.bB + 1) * CH <= args.nB ? CH : (c.bB * CH < args.nB ? args.nB - c.bB * CH : 0);
+      c.len = block_len(c.bB);
+      c.b = c.len ? (nBB - 1 - c.bB) * CH : 0;
       return;
     }
     c.a += step_a;

@@ -60,6 +60,7 @@ struct Tuning {
   int grid = 0;
   int spp = 4;
   float ms = 0.f;
+  int staged = 0;    // uneven batches: whole twiddle tables in shared memory
 };
 std::string plan_tuning_key(sdft_prec prec, uint32_t s, uint64_t batch);
 std::string batch_tuning_key(sdft_prec prec, uint64_t n, uint64_t total);

@@ -72,24 +72,30 @@ static_assert(sizeof(QItem) % 16 == 0, "items are copied in 16-byte pieces");
 // middle passes read (copied by the producer with the tile, on its barrier):
 // entries below 2^8 with four stages per pass, below 2^9 with three (the two
 // middle passes of a 2^12-value tile).
-template <class R, int W>
-constexpr uint32_t q_tw_entries() { return W == 3 ? 512u : 256u; }
-template <class R, int W>
-constexpr uint32_t q_tw_bytes() { return q_tw_entries<R, W>() * KT<R>::ES; }
+// ST (staged tables): one CTA per SM, and each tile buffer's table copy holds
+// the item's whole table (2^TB entries, 32 KiB), so every pass, the top one
+// included, reads its twiddles from shared memory and no compute warp waits on
+// a global load.
+template <class R, int W, bool ST = false>
+constexpr uint32_t q_tw_entries() { return ST ? (1u << KT<R>::TB) : (W == 3 ? 512u : 256u); }
+template <class R, int W, bool ST = false>
+constexpr uint32_t q_tw_bytes() { return q_tw_entries<R, W, ST>() * KT<R>::ES; }
 constexpr uint32_t kQTwOff = kBufs * kTileBytes + 64 + kMetaSlots * sizeof(QItem);
 static_assert(kQTwOff % 16 == 0, "table copies need 16-byte alignment");
-template <class R, int W>
-constexpr uint32_t q_smem() { return kQTwOff + kBufs * q_tw_bytes<R, W>() + 1024; }
+template <class R, int W, bool ST = false>
+constexpr uint32_t q_smem() { return kQTwOff + kBufs * q_tw_bytes<R, W, ST>() + 1024; }
 
 // Entries [lo, hi) of an item's table staged in shared memory, for a tile
 // whose stages are [PLO, TB): the first pass's entries (PLO = 0) and the
 // memory-read passes', when they fit the copy; hi = 0: none.
 constexpr int q_stage_hi(int TB, int W, int PLO, int cap) {
+  if (cap >= (1 << TB)) return 1 << TB;            // staged tables: everything
   const int mlo = mid_pass_lo(TB, W, PLO, TB), mhi = mid_pass_hi(TB, W, PLO, TB);
   if (mlo >= mhi || (1 << mhi) > cap) return PLO == 0 ? (1 << W) : 0;
   return 1 << mhi;
 }
 constexpr int q_stage_lo(int TB, int W, int PLO, int cap) {
+  if (cap >= (1 << TB)) return PLO == 0 ? 0 : (1 << PLO);
   return PLO == 0 ? 0 : (q_stage_hi(TB, W, PLO, cap) ? (1 << mid_pass_lo(TB, W, PLO, TB)) : 0);
 }
 
@@ -251,30 +257,30 @@ __device__ __forceinline__ void run_small(const QArgs& a, const QItem& it, uint3
 // A single-table item (a 2^TB chunk, a one-instance tile, a later-level group
 // block): the passes of k_level with the top pass's twiddles loaded into
 // registers for this item (the previous item prefetched them into L1).
-template <class R, int W, int PLO, int PHI, bool LAST>
+template <class R, int W, int PLO, int PHI, bool LAST, bool ST = false>
 __device__ __forceinline__ void run_single(char* buf, const typename KT<R>::C* tab, R sc, uint32_t tid,
                                            uint32_t wsm) {
   using C = typename KT<R>::C;
   constexpr int TB = KT<R>::TB;
-  constexpr int NREG = reg_twiddles(TB, W, PLO, PHI);
-  constexpr int CAP = int(q_tw_entries<R, W>());
+  constexpr int NREG = ST ? 0 : reg_twiddles(TB, W, PLO, PHI);
+  constexpr int CAP = int(q_tw_entries<R, W, ST>());
   C wreg[NREG > 0 ? NREG : 1];
-  load_reg_twiddles<R, W, PLO, PHI>(tab, tid, wreg);
+  if constexpr (!ST) load_reg_twiddles<R, W, PLO, PHI>(tab, tid, wreg);
   // staged entries (q_stage_lo/hi) come from shared memory at wsm; the rest from
   // global memory (pass 0 reads entry 2^m1 + u as w0[2^m1 - 1 + u]: w0 = tab + 1)
   constexpr bool MID = q_stage_hi(TB, W, PLO, CAP) > (1 << W) || (PLO > 0 && q_stage_hi(TB, W, PLO, CAP) > 0);
   constexpr bool P0 = PLO == 0;
-  run_passes<R, W, PLO, PHI, LAST, 0, 0, MID, NoHook, 1, P0>(buf, wreg, tab + 1, tab, tid, sc, wsm);
+  run_passes<R, W, PLO, PHI, LAST, 0, 0, MID, NoHook, 1, P0, ST>(buf, wreg, tab + 1, tab, tid, sc, wsm);
 }
 
-template <class R, int W, int Q = 1>
+template <class R, int W, bool ST, int Q = 1>
 __device__ __forceinline__ void dispatch_later_single(int v, char* buf, const typename KT<R>::C* tab, R sc,
                                                       uint32_t tid, uint32_t wsm) {
   constexpr int TB = KT<R>::TB, CB = KT<R>::CB;
   if constexpr (Q <= TB - CB) {
-    if (v == q_variant_later(Q, true)) return run_single<R, W, TB - Q, TB, true>(buf, tab, sc, tid, wsm);
-    if (v == q_variant_later(Q, false)) return run_single<R, W, TB - Q, TB, false>(buf, tab, sc, tid, wsm);
-    dispatch_later_single<R, W, Q + 1>(v, buf, tab, sc, tid, wsm);
+    if (v == q_variant_later(Q, true)) return run_single<R, W, TB - Q, TB, true, ST>(buf, tab, sc, tid, wsm);
+    if (v == q_variant_later(Q, false)) return run_single<R, W, TB - Q, TB, false, ST>(buf, tab, sc, tid, wsm);
+    dispatch_later_single<R, W, ST, Q + 1>(v, buf, tab, sc, tid, wsm);
   }
 }
 
@@ -325,7 +331,7 @@ __device__ __forceinline__ bool q_item_in_bounds(const QParams& prm, const QItem
 // published before the dependency wait of the item four places later in the
 // same CTA, so items that wait on one another sit at least 4 x grid list
 // positions apart and every wait ends (all CTAs are resident).
-template <class R, int W>
+template <class R, int W, bool ST>
 __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint64_t n) {
   const uint64_t c = blockIdx.x, G = gridDim.x;
   const uint32_t bars = ptx::smem_addr(smem + kBufs * kTileBytes);
@@ -402,7 +408,7 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
         }
         const uint32_t bytes = (it.variant < 16) ? (128u << (it.map / 2)) : kTileBytes;
         // the table entries the first and middle passes read, copied with the tile
-        constexpr int TBs = KT<R>::TB, CAP = int(q_tw_entries<R, W>());
+        constexpr int TBs = KT<R>::TB, CAP = int(q_tw_entries<R, W, ST>());
         int slo = 0, shi = 0;
         if (it.variant == kVFirstChunk || it.variant == q_variant_first(TBs)) {
           slo = q_stage_lo(TBs, W, 0, CAP);
@@ -418,7 +424,7 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
         ptx::tma_load_4d_hint(ptx::smem_addr(smem + b * kTileBytes), &prm.maps[it.map], full, 0, it.c1, 0, it.c3,
                               ptx::policy_evict_first());
         if (tw_bytes)
-          ptx::bulk_load(ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R, W>()) + uint32_t(slo) * KT<R>::ES,
+          ptx::bulk_load(ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R, W, ST>()) + uint32_t(slo) * KT<R>::ES,
                          static_cast<const char*>(it.tw) + size_t(slo) * KT<R>::ES, tw_bytes, full);
         inflight |= 1u << b;
         load_par = (load_par & ~(1u << b)) | (uint32_t((j / kBufs) & 1) << b);
@@ -465,8 +471,8 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
   }
 }
 
-template <class R, int W>
-__global__ void __launch_bounds__(q_threads<R, W>(), 2) k_queue(const __grid_constant__ QParams prm) {
+template <class R, int W, bool ST>
+__global__ void __launch_bounds__(q_threads<R, W>(), ST ? 1 : 2) k_queue(const __grid_constant__ QParams prm) {
   const QArgs& a = prm.a;
   extern __shared__ char smem_raw[];
   char* smem = align1024(smem_raw);
@@ -474,7 +480,7 @@ __global__ void __launch_bounds__(q_threads<R, W>(), 2) k_queue(const __grid_con
   const uint32_t tid = threadIdx.x;
   constexpr uint32_t NT = tile_threads<R, W>();
   {
-    const uint32_t used = uint32_t(smem - smem_raw) + kQTwOff + kBufs * q_tw_bytes<R, W>();
+    const uint32_t used = uint32_t(smem - smem_raw) + kQTwOff + kBufs * q_tw_bytes<R, W, ST>();
     int bad = 0;
     if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
     else if (reinterpret_cast<uintptr_t>(&prm.maps[0]) & 63u) bad = kBadMap;
@@ -497,7 +503,7 @@ __global__ void __launch_bounds__(q_threads<R, W>(), 2) k_queue(const __grid_con
   }
   __syncthreads();
   if (tid >= NT) {                     // the producer warp
-    if (tid == NT) q_producer<R, W>(prm, smem, n);
+    if (tid == NT) q_producer<R, W, ST>(prm, smem, n);
     return;
   }
   using C = typename KT<R>::C;
@@ -515,23 +521,24 @@ __global__ void __launch_bounds__(q_threads<R, W>(), 2) k_queue(const __grid_con
     const C* tab = static_cast<const C*>(it.tw);
     const R sc = R(it.scale);
     char* buf = smem + b * kTileBytes;
-    const uint32_t wsm = ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R, W>());
+    const uint32_t wsm = ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R, W, ST>());
     if (v == kVNop) {
       // nothing to do
     } else if (v == kVSmall) {
       run_small<R>(a, it, tid);
     } else if (v == kVFirstChunk) {
-      run_single<R, W, 0, TB, false>(buf, tab, sc, tid, wsm);
+      run_single<R, W, 0, TB, false, ST>(buf, tab, sc, tid, wsm);
     } else if (v == q_variant_first(TB)) {
-      run_single<R, W, 0, TB, true>(buf, tab, sc, tid, wsm);
+      run_single<R, W, 0, TB, true, ST>(buf, tab, sc, tid, wsm);
     } else if (v >= 16) {
-      dispatch_later_single<R, W>(v, buf, tab, sc, tid, wsm);
+      dispatch_later_single<R, W, ST>(v, buf, tab, sc, tid, wsm);
     } else {
       dispatch_first_q<R, W>(v, buf, a, it, tid);   // several instances per tile
     }
     ptx::mbar_arrive(bars + kQEmpty + 8 * b);   // after the final pass's proxy fence and barrier
     // the next item's register and L1 twiddles, if its tile has landed already
-    if (j + 1 < n) {
+    // (staged tables need none)
+    if (!ST && j + 1 < n) {
       const uint32_t nb = uint32_t((j + 1) % kBufs);
       if (ptx::mbar_test_wait(bars + kQFull + 8 * nb, uint32_t(((j + 1) / kBufs) & 1))) {
         const QItem& nx = q_meta(smem, j + 1);
@@ -550,33 +557,35 @@ __global__ void __launch_bounds__(q_threads<R, W>(), 2) k_queue(const __grid_con
 
 namespace sdft {
 
-// Host launchers (queue_f32.cu, queue_f64.cu). `w`: stages per pass (3 or 4
-// for complex64, 4 for complex128).
-sdft_status launch_queue_f32(const QParams& prm, int grid, int w, cudaStream_t st);
-sdft_status launch_queue_f64(const QParams& prm, int grid, int w, cudaStream_t st);
+// Host launchers (queue_f32*.cu, queue_f64.cu). `w`: stages per pass (3 or 4
+// for complex64, 4 for complex128); `staged`: whole tables in shared memory
+// (complex64 only).
+sdft_status launch_queue_f32(const QParams& prm, int grid, int w, bool staged, cudaStream_t st);
+sdft_status launch_queue_f64(const QParams& prm, int grid, int w, bool staged, cudaStream_t st);
 // Co-resident CTAs of the queue kernel on the current device (occupancy x SMs).
-int queue_grid_f32(int w);
-int queue_grid_f64(int w);
+int queue_grid_f32(int w, bool staged);
+int queue_grid_f64(int w, bool staged);
 
-template <class R, int W>
+template <class R, int W, bool ST>
 int queue_grid() {
-  auto fn = k_queue<R, W>;
-  if (ensure_smem(reinterpret_cast<const void*>(fn), int(q_smem<R, W>())) != SDFT_OK) return 0;
+  auto fn = k_queue<R, W, ST>;
+  if (ensure_smem(reinterpret_cast<const void*>(fn), int(q_smem<R, W, ST>())) != SDFT_OK) return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, q_threads<R, W>(), q_smem<R, W>()) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, q_threads<R, W>(), q_smem<R, W, ST>()) !=
+      cudaSuccess)
     return 0;
   return per_sm * sm_count();
 }
 
-template <class R, int W>
+template <class R, int W, bool ST>
 sdft_status launch_queue(const QParams& prm, int grid, cudaStream_t st) {
-  auto fn = k_queue<R, W>;
-  sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(q_smem<R, W>()));
+  auto fn = k_queue<R, W, ST>;
+  sdft_status s = ensure_smem(reinterpret_cast<const void*>(fn), int(q_smem<R, W, ST>()));
   if (s != SDFT_OK) return s;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
   cfg.blockDim = dim3(q_threads<R, W>());
-  cfg.dynamicSmemBytes = q_smem<R, W>();
+  cfg.dynamicSmemBytes = q_smem<R, W, ST>();
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs resident: dependency waits make progress

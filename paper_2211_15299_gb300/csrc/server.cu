@@ -379,7 +379,8 @@ sdft_status launch_slot(Server& S, Slot& sl) {
   prm.a.n_insts = sl.reqs.size();
   prm.a.total = S.budget / es;
   const int grid = int(std::min<uint64_t>(uint64_t(S.grid), n_items));
-  s = S.prec == SDFT_C64 ? launch_queue_f32(prm, grid, 4, sl.stream) : launch_queue_f64(prm, grid, 4, sl.stream);
+  s = S.prec == SDFT_C64 ? launch_queue_f32(prm, grid, 4, false, sl.stream)
+                          : launch_queue_f64(prm, grid, 4, false, sl.stream);
   if (s != SDFT_OK) return s;
   for (const Req& r : sl.reqs) {
     e = cudaMemcpyAsync(r.h_out, S.d_arena + r.off, r.plan->k * es, cudaMemcpyDeviceToHost, sl.stream);
@@ -574,7 +575,7 @@ sdft_status sdft_server_create(sdft_prec prec, uint64_t budget_bytes, uint32_t n
   const uint32_t top = uint32_t(63 - __builtin_clzll(budget_bytes));
   S.budget = 1ull << top;
   S.buddy.init(7, top);
-  const int total = prec == SDFT_C64 ? queue_grid_f32(4) : queue_grid_f64(4);
+  const int total = prec == SDFT_C64 ? queue_grid_f32(4, false) : queue_grid_f64(4, false);
   S.grid = total / int(n_slots);      // in-flight launches together fit the co-resident CTAs
   sdft_status st = S.grid > 0 ? SDFT_OK : SDFT_ERR_CUDA;
   if (st == SDFT_OK) {

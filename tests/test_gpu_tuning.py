@@ -45,20 +45,34 @@ def test_stages_per_pass_bit_identical(M, s, batch):
     assert rel_l2(ref[:2].cpu().numpy(), want) < 1e-5
 
 
-def test_batch_stages_per_pass_bit_identical():
+def test_batch_queue_variants_bit_identical():
+    # three or four stages per pass x tables in registers / staged whole in
+    # shared memory: four kernels, one result
     torch = _torch()
     from paper_2211_15299_gb300 import Batch, Plan, _native as N
     insts = W.workload_uneven(count=300, salt=11)
     b = Batch([Plan(i.M, i.J, 0) for i in insts])
     x = torch.randn(b.total, dtype=torch.complex64, device="cuda")
-    N.sdft_batch_set_stages_per_pass(b.handle, 4)
-    y4 = b.execute(x)
-    N.sdft_batch_set_stages_per_pass(b.handle, 3)
-    assert N.sdft_batch_get_stages_per_pass(b.handle) == 3
-    y3 = b.execute(x)
+    outs = {}
+    for spp in (4, 3):
+        for staged in (False, True):
+            N.sdft_batch_set_stages_per_pass(b.handle, spp)
+            N.sdft_batch_set_table_staging(b.handle, staged)
+            assert N.sdft_batch_get_stages_per_pass(b.handle) == spp
+            assert N.sdft_batch_get_table_staging(b.handle) == staged
+            outs[(spp, staged)] = b.execute(x)
     torch.cuda.synchronize()
     assert b.device_status() == 0
-    assert torch.equal(y3, y4)
+    for key, y in outs.items():
+        assert torch.equal(y, outs[(4, False)]), key
+    # and against the oracle for a few instances
+    xs, ys = x.cpu().numpy(), outs[(4, True)].cpu().numpy()
+    for i in (0, 1, len(insts) // 2, len(insts) - 1):
+        inst = insts[i]
+        o, kk = int(b.offsets[i]), 1 << int(inst.s)
+        Jc = O.canonical_support_by_key(inst.J, inst.pivots)
+        ref = O.transform_levels(inst.M, inst.pivots, Jc, xs[o:o + kk][None].astype(np.complex128))[0]
+        assert rel_l2(ys[o:o + kk], ref) < 1e-5, i
 
 
 def test_autotuners_store_and_apply(tmp_path):
@@ -97,6 +111,7 @@ def test_autotuners_store_and_apply(tmp_path):
     b2 = Batch([Plan(i.M, i.J, 0) for i in insts])
     assert N.sdft_batch_apply_tuning(b2.handle)
     assert N.sdft_batch_get_stages_per_pass(b2.handle) == N.sdft_batch_get_stages_per_pass(b.handle)
+    assert N.sdft_batch_get_table_staging(b2.handle) == N.sdft_batch_get_table_staging(b.handle)
     assert torch.equal(b2.execute(xb), b.execute(xb))
     torch.cuda.synchronize()
     assert b.device_status() == 0 and b2.device_status() == 0

@@ -122,10 +122,11 @@ def test_batch_choice_applied_and_item_list_rebuilt(tmp_path):
     t_bits = int(np.floor(np.log2(b.total)))
     key = f"batch/c64/n{n_bits}/t{t_bits}"
     f = tmp_path / "tune.json"
-    f.write_text(json.dumps({key: {"schedule": 1, "grid": 100, "stages_per_pass": 3}}))
+    f.write_text(json.dumps({key: {"schedule": 1, "grid": 100, "stages_per_pass": 3, "table_staging": 1}}))
     assert not N.sdft_batch_apply_tuning(b.handle)
     N.sdft_autotune_cache_load(str(f))
     assert N.sdft_batch_apply_tuning(b.handle)
     assert N.sdft_batch_get_stages_per_pass(b.handle) == 3
+    assert N.sdft_batch_get_table_staging(b.handle)
     items, counters, grid = b.stats()
     assert grid == 100 and items > 0
