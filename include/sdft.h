@@ -542,6 +542,7 @@ typedef struct {
   uint64_t arena_bytes;      /* device arena (the admission budget)              */
   uint64_t arena_peak_bytes; /* largest arena use                                */
   uint64_t planned;          /* supports planned by the server's planner threads */
+  uint64_t injected;         /* requests dropped, failed or delayed by sdft_server_inject */
 } sdft_server_stats;
 
 /*
@@ -597,6 +598,22 @@ sdft_status sdft_server_get_stats(sdft_server srv, sdft_server_stats* stats);
 
 /* Device status word of the server's launches (as for plans). */
 sdft_status sdft_server_device_status(sdft_server srv, int clear);
+
+/*
+ * sdft_server_inject - host-side fault injection for testing a client's failure
+ * handling, with no device involvement: of the requests that reach admission
+ * after this call, every `every`-th is
+ *   SDFT_INJECT_DROP : discarded (it never completes; a client sees it only by
+ *                      its absence, for example when its own deadline passes),
+ *   SDFT_INJECT_FAIL : completed at once with SDFT_ERR_CUDA, as if its launch
+ *                      had failed (nothing of it runs),
+ *   SDFT_INJECT_DELAY: held back `delay_us` microseconds (at most 10 s) before
+ *                      it is admitted, then run normally.
+ * SDFT_INJECT_OFF (or a later call) stops it. Counted in
+ * sdft_server_stats.injected. SDFT_ERR_ARG for an unknown mode or every = 0.
+ */
+typedef enum { SDFT_INJECT_OFF = 0, SDFT_INJECT_DROP = 1, SDFT_INJECT_FAIL = 2, SDFT_INJECT_DELAY = 3 } sdft_inject;
+sdft_status sdft_server_inject(sdft_server srv, uint32_t mode, uint64_t every, uint64_t delay_us);
 
 /* Stop accepting requests, finish the queued ones, release everything. */
 sdft_status sdft_server_destroy(sdft_server srv);

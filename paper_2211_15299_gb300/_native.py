@@ -48,7 +48,7 @@ STATUS_CODE = {v: k for k, v in STATUS.items()}
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "submitted", "completed", "failed", "micro_batches", "coeffs", "inflight", "max_inflight",
-        "arena_bytes", "arena_peak_bytes", "planned")]
+        "arena_bytes", "arena_peak_bytes", "planned", "injected")]
 
 
 # Every symbol declared in include/sdft.h: name -> (restype, argtypes)
@@ -73,6 +73,7 @@ SIGNATURES = {
     "sdft_batch_get_stages_per_pass": (c_int, [c_vp, P_u32]),
     "sdft_batch_apply_tuning": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "sdft_batch_set_table_staging": (c_int, [c_vp, c_int]),
+    "sdft_server_inject": (c_int, [c_vp, c_u32, c_u64, c_u64]),
     "sdft_batch_get_table_staging": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "sdft_autotune_cache_save": (c_int, [ctypes.c_char_p]),
     "sdft_autotune_cache_load": (c_int, [ctypes.c_char_p]),
@@ -265,6 +266,13 @@ def sdft_batch_get_stages_per_pass(batch: int) -> int:
     v = c_u32(0)
     _check(_lib.sdft_batch_get_stages_per_pass(batch, ctypes.byref(v)), "sdft_batch_get_stages_per_pass")
     return int(v.value)
+
+
+SDFT_INJECT_OFF, SDFT_INJECT_DROP, SDFT_INJECT_FAIL, SDFT_INJECT_DELAY = 0, 1, 2, 3
+
+
+def sdft_server_inject(srv: int, mode: int, every: int = 0, delay_us: int = 0) -> None:
+    _check(_lib.sdft_server_inject(srv, int(mode), int(every), int(delay_us)), "sdft_server_inject")
 
 
 def sdft_batch_set_table_staging(batch: int, staged: bool) -> None:

@@ -99,6 +99,7 @@ struct Req {
   uint32_t tw_order = 0;
   bool own_tw = false;
   sdft_plan own_plan = nullptr;   // planned by the server for this request
+  bool inj_seen = false;          // counted by the fault injector already
 };
 
 struct PlanJob {
@@ -158,6 +159,10 @@ struct Server {
   std::deque<PlanJob> plan_jobs;
   std::condition_variable plan_cv;
   uint64_t planning = 0;         // jobs queued or being planned
+  // host-side fault injection (sdft_server_inject): every inj_every-th request
+  // reaching admission is dropped, failed or delayed
+  uint32_t inj_mode = 0;
+  uint64_t inj_every = 0, inj_delay_us = 0, inj_count = 0;
 };
 
 namespace {
@@ -433,6 +438,29 @@ void worker_loop(Server* S) {
     if (free_slot && !S->waiting.empty()) {
       std::vector<Req>& batch = free_slot->reqs;
       while (!S->waiting.empty() && batch.size() < S->max_batch) {
+        if (S->inj_mode && S->inj_every && !S->waiting.front().inj_seen) {
+          Req& fr = S->waiting.front();
+          fr.inj_seen = true;
+          if (++S->inj_count % S->inj_every == 0) {
+            ++S->stats.injected;
+            if (S->inj_mode == SDFT_INJECT_DROP || S->inj_mode == SDFT_INJECT_FAIL) {
+              if (S->inj_mode == SDFT_INJECT_FAIL) {   // completes at once, as if its launch had failed
+                S->done.push_back(Done{fr.tag, 0.0, int32_t(SDFT_ERR_CUDA)});
+                ++S->stats.failed;
+              }                                        // a dropped request never completes
+              if (fr.own_plan) sdft_plan_destroy(fr.own_plan);
+              S->waiting.pop_front();
+              progressed = true;
+              continue;
+            }
+            // delay: the worker holds this request back (only the worker pops
+            // the queue, so it is still at the front afterwards)
+            const uint64_t us = S->inj_delay_us;
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(us));
+            lk.lock();
+          }
+        }
         Req r = S->waiting.front();
         r.order = block_order(*S, *r.plan);
         const uint64_t tw_bytes = r.plan->deferred ? std::max<uint64_t>(r.plan->host_tables.size(), 128) : 0;
@@ -715,6 +743,19 @@ sdft_status sdft_server_drain(sdft_server srv, uint64_t timeout_ms) {
       return SDFT_ERR_TIMEOUT;
     std::this_thread::sleep_for(std::chrono::microseconds(100));
   }
+}
+
+sdft_status sdft_server_inject(sdft_server srv, uint32_t mode, uint64_t every, uint64_t delay_us) {
+  if (!srv) return SDFT_ERR_ARG;
+  if (mode > SDFT_INJECT_DELAY || (mode != SDFT_INJECT_OFF && every == 0)) return SDFT_ERR_ARG;
+  if (delay_us > 10000000ull) return SDFT_ERR_ARG;
+  sdft::Server& S = srv->s;
+  std::lock_guard<std::mutex> lk(S.mu);
+  S.inj_mode = mode;
+  S.inj_every = every;
+  S.inj_delay_us = delay_us;
+  S.inj_count = 0;
+  return SDFT_OK;
 }
 
 sdft_status sdft_server_get_stats(sdft_server srv, sdft_server_stats* st) {

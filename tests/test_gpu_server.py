@@ -155,3 +155,51 @@ def test_requests_that_bring_their_support():
     st = srv.stats()
     assert st["planned"] == len(reqs) and st["failed"] == 1
     srv.close()
+
+
+def test_host_side_fault_injection():
+    """The engine's host-side injector (no device fault): dropped requests never
+    complete and the client finds them by their absence, failed ones complete
+    at once with SDFT_ERR_CUDA, delayed ones run late; every other result is the
+    same as when nothing is injected."""
+    import time
+    from paper_2211_15299_gb300 import Server, _native as N
+    rng = np.random.default_rng(5170)
+    reqs = _requests(rng, [int(s) for s in rng.permutation([4, 6, 8, 10, 12, 13, 14, 9, 7, 5, 11, 12])])
+    srv = Server("c64", budget_bytes=64 << 20, n_slots=2, max_batch=4)
+    ref, got = _serve(srv, reqs)
+    assert all(got[i][1] == 0 for i in range(len(reqs)))
+    # drop every third request
+    N.sdft_server_inject(srv.handle, N.SDFT_INJECT_DROP, 3)
+    before = srv.stats()["injected"]
+    outs, got = _serve(srv, reqs)
+    dropped = {i for i in range(len(reqs)) if i not in got}
+    assert len(dropped) == len(reqs) // 3 and srv.stats()["injected"] - before == len(dropped)
+    for i in got:
+        assert got[i][1] == 0 and np.array_equal(outs[i].numpy(), ref[i].numpy()), i
+    # fail every fourth
+    N.sdft_server_inject(srv.handle, N.SDFT_INJECT_FAIL, 4)
+    outs, got = _serve(srv, reqs)
+    assert len(got) == len(reqs)
+    failed = {i for i, (_, st) in got.items() if st != 0}
+    assert len(failed) == len(reqs) // 4
+    assert all(got[i][1] == N.STATUS_CODE["SDFT_ERR_CUDA"] for i in failed)
+    for i in set(got) - failed:
+        assert np.array_equal(outs[i].numpy(), ref[i].numpy()), i
+    # delay every second by 20 ms: all complete, the delayed ones late
+    N.sdft_server_inject(srv.handle, N.SDFT_INJECT_DELAY, 2, 20_000)
+    t0 = time.perf_counter()
+    outs, got = _serve(srv, reqs)
+    assert len(got) == len(reqs) and all(st == 0 for _, st in got.values())
+    assert time.perf_counter() - t0 >= 0.02 * (len(reqs) // 2)
+    assert max(l for l, _ in got.values()) >= 0.02
+    for i in got:
+        assert np.array_equal(outs[i].numpy(), ref[i].numpy()), i
+    N.sdft_server_inject(srv.handle, N.SDFT_INJECT_OFF)
+    outs, got = _serve(srv, reqs)
+    assert len(got) == len(reqs) and all(np.array_equal(outs[i].numpy(), ref[i].numpy()) for i in got)
+    assert srv.device_status() == 0
+    from paper_2211_15299_gb300 import SdftError
+    with pytest.raises(SdftError):
+        N.sdft_server_inject(srv.handle, N.SDFT_INJECT_DROP, 0)
+    srv.close()
