@@ -299,8 +299,11 @@ sdft_status sdft_plan_apply_tuning(sdft_plan plan, uint64_t batch, int* found);
  * complex64 plans, 3 (8 values per thread, 512 threads, one pass more per
  * 12 stages). Every choice gives the same bits. sdft_plan_autotune chooses it
  * with the strategy. A change synchronises the device if the plan holds
- * cached work queues (they are rebuilt on next use). The paper has no
- * counterpart (Algorithm 1 is stated as a recursion). Errors: SDFT_ERR_ARG.
+ * cached work queues (they are rebuilt on next use). Like
+ * sdft_plan_set_strategy, sdft_plan_autotune and sdft_plan_apply_tuning, it
+ * changes the plan: call it while no other thread is calling an execute or
+ * synthesis entry point on the same plan. The paper has no counterpart
+ * (Algorithm 1 is stated as a recursion). Errors: SDFT_ERR_ARG.
  */
 sdft_status sdft_plan_set_stages_per_pass(sdft_plan plan, uint32_t stages_per_pass);
 sdft_status sdft_plan_get_stages_per_pass(sdft_plan plan, uint32_t* stages_per_pass);
@@ -381,7 +384,8 @@ sdft_status sdft_batch_execute_noalloc(sdft_batch batch, const void* d_samples, 
 /* Stages per pass of a batch's queue kernel (as for plans: 4, or 3 for
  * complex64; the same bits either way). Rebuilds the batch's item list (its
  * grid follows the kernel's occupancy): synchronise work using the batch
- * first, and re-capture graphs. */
+ * first, re-capture graphs, and call it (like every setter of a batch) while
+ * no other thread is launching the batch. */
 sdft_status sdft_batch_set_stages_per_pass(sdft_batch batch, uint32_t stages_per_pass);
 sdft_status sdft_batch_get_stages_per_pass(sdft_batch batch, uint32_t* stages_per_pass);
 
