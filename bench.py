@@ -5,9 +5,12 @@ resident in HBM; one step = one call of the strided transform over the whole
 batch. Prints ONE JSON line (rank 0).
 
 Legs:
-  * value        device-timed coeffs/s of the batched complex64 path (CUDA
-                 events around each step on the launching stream, L2 flushed
-                 between steps, untimed)
+  * value        device-timed coeffs/s of the batched complex64 path: the K
+                 steps run back to back as one region bracketed by CUDA events
+                 on the launching stream, rotating over 4 input/output pairs
+                 (each step's input, larger than L2, last touched 3 steps
+                 earlier: no flush); the per-step figure after a 256 MiB L2
+                 write flush is reported beside it
   * e2e          the same through the public API with pinned host buffers
                  (one sdft_execute_strided_host call: H2D of the samples, the
                  transform and D2H of the coefficients, overlapped in chunks,
@@ -45,6 +48,7 @@ import workloads as W  # noqa: E402
 METRIC = "coeffs/s batched FP32 vs plain per-instance FP64 at relL2≤1e-5; p50/p99 latency"
 UNIT = "coeffs/s"
 L2_FLUSH_BYTES = 256 << 20
+ROTATE_SETS = 4          # input/output pairs the headline steps rotate over
 
 
 def _peaks():
@@ -181,13 +185,14 @@ def run_ours(args):
     # a valid input; seeded per rank (replicas, weak scaling).
     g = torch.Generator(device=dev)
     g.manual_seed(W.BASE_SEED + 2 + 1000 * rank)
-    x32 = torch.randn((batch, k), dtype=torch.complex64, device=dev, generator=g)
-    y32 = torch.empty_like(x32)
+    xs = [torch.randn((batch, k), dtype=torch.complex64, device=dev, generator=g) for _ in range(ROTATE_SETS)]
+    ys = [torch.empty_like(xs[0]) for _ in range(ROTATE_SETS)]
+    x32, y32 = xs[0], ys[0]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(s=None):
-        plan32.execute_strided(x32, y32, stream=(s or stream).cuda_stream)
+    def step(s=None, i=0):
+        plan32.execute_strided(xs[i], ys[i], stream=(s or stream).cuda_stream)
 
     # the tile parameters (stages per pass) chosen by the library's autotuner on
     # this workload; both choices are also timed the bench's way, below
@@ -208,25 +213,29 @@ def run_ours(args):
         _barrier(ws)
         # one step = one replay of a CUDA graph holding the strided call (the
         # host-side checks and tensor-map encoding happen once, at capture)
-        times = time_graph(step, args.steps, args.warmup, flush, stream)
+        region = time_rotating([lambda s=None, i=i: step(s, i) for i in range(ROTATE_SETS)],
+                               args.steps, args.warmup, stream)
         _barrier(ws)
         torch.cuda.synchronize()
-    total = _max_over_ranks(ws, sum(times))
+    total = _max_over_ranks(ws, region)
     coeffs_per_step = batch * k
-    value = replica_throughput(ws, coeffs_per_step, args.steps, sum(times))
+    value = replica_throughput(ws, coeffs_per_step, args.steps, region)
     ms_per_step = 1e3 * total / args.steps
+    # the same steps timed one by one after a 256 MiB L2 write flush (the
+    # flush's dirty lines are written back inside each timed step)
+    flushed = time_graph(step, args.steps, args.warmup, flush, stream)
 
     # roofline of the dominant kernel (the single level-0 launch per step here)
     peak, peak_kind = _peaks()
     alg_bytes = 16 * coeffs_per_step + 8 * (k - 1)
-    kern_s = statistics.mean(times) / n_levels if n_levels == 1 else None
-    achieved = alg_bytes / statistics.mean(times) / 1e9
+    achieved = alg_bytes / (region / args.steps) / 1e9
     traffic = _committed_traffic(M, s, batch)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "k_level<float,0,12,true>" if n_levels == 1 else "multi-level",
                 "alg_bytes_per_launch": alg_bytes,
-                "frac_of_nominal_7900": round(achieved / 7900.0, 4)}
+                "frac_of_nominal_7900": round(achieved / 7900.0, 4),
+                "ms_per_step_after_l2_write_flush": 1e3 * statistics.mean(flushed)}
 
     if args.only_fp32:
         if rank == 0:
@@ -353,7 +362,8 @@ def _config(M, s, batch, ws):
     """The workload of the headline line, the same in both arms."""
     return {"workload": f"shared support N=2^{M} k=2^{s} batch {batch} complex64 (strided, one plan)",
             "log2N": M, "log2k": s, "batch": batch,
-            "l2": "flushed between steps (256 MiB write, untimed)",
+            "l2": f"inputs larger than L2, no flush: steps rotate over {ROTATE_SETS} input/output pairs, "
+                  f"each step's input last touched {ROTATE_SETS - 1} steps earlier",
             "parallelism": f"replicas x{ws}"}
 
 
@@ -374,10 +384,11 @@ def _committed_traffic(M, s, batch):
     return None
 
 
-def time_graph(fn, steps, warmup, flush, stream):
-    """Capture `fn` in a CUDA graph and time replays (events on `stream`, L2 flushed between)."""
+def _capture(fn):
+    """A CUDA graph holding one call of `fn` (called once untimed first: it
+    builds any cached work queue)."""
     import torch
-    fn()                                    # first call builds any cached work queue
+    fn()
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
@@ -386,7 +397,34 @@ def time_graph(fn, steps, warmup, flush, stream):
         with torch.cuda.graph(g, stream=s):
             fn(s)
     torch.cuda.synchronize()
+    return g
+
+
+def time_graph(fn, steps, warmup, flush, stream):
+    """Capture `fn` in a CUDA graph and time replays (events on `stream`, L2 flushed between)."""
+    g = _capture(fn)
     return time_device_steps(lambda: g.replay(), steps, warmup, flush, stream)
+
+
+def time_rotating(fns, steps, warmup, stream):
+    """Steady-state timing over inputs larger than L2: one CUDA graph per buffer
+    set, step i replays set i mod len(fns), and the `steps` replays run back to
+    back as ONE region bracketed by CUDA events on `stream` (no flush: a set's
+    input was last touched len(fns) - 1 steps earlier, with several L2
+    capacities of traffic in between, and every step writes back the dirty
+    output lines the step before it left in L2). Returns the region's seconds."""
+    import torch
+    graphs = [_capture(fn) for fn in fns]
+    for i in range(warmup):
+        graphs[i % len(graphs)].replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i in range(steps):
+        graphs[i % len(graphs)].replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) * 1e-3
 
 
 def run_single(args):
