@@ -202,7 +202,8 @@ def run_ours(args):
     by_spp = {}
     for spp in (4, 3):
         N.sdft_plan_set_stages_per_pass(plan32.handle, spp)
-        by_spp[spp] = 1e3 * statistics.mean(time_graph(step, max(5, args.steps // 2), args.warmup, flush, stream))
+        by_spp[spp] = 1e3 * time_rotating([lambda s=None, i=i: step(s, i) for i in range(ROTATE_SETS)],
+                                          max(5, args.steps // 2), args.warmup, stream) / max(5, args.steps // 2)
     N.sdft_plan_set_stages_per_pass(plan32.handle, tuned_spp)
     tuning = {"stages_per_pass": tuned_spp, "chosen_by": "sdft_plan_autotune",
               "ms_by_stages_per_pass": {str(k): v for k, v in by_spp.items()}}
@@ -273,16 +274,18 @@ def run_ours(args):
     torch.cuda.synchronize()
     rel_df_vs_fp64 = float(torch.linalg.vector_norm(y_df - y64) / torch.linalg.vector_norm(y64))
     del y_df, plan_df
-    # synthesis (the inverse map) on the same batch, graph-replayed
-    ysyn = torch.empty_like(x32)
+    # synthesis (the inverse map) on the same batches, graph-replayed, timed
+    # like the headline (rotating over the coefficient sets)
+    zs = [torch.empty_like(x32) for _ in range(ROTATE_SETS)]
 
-    def step_syn(s=None):
-        plan32.synthesize(y32, ysyn, stream=(s or stream).cuda_stream)
+    def step_syn(s=None, i=0):
+        plan32.synthesize(ys[i], zs[i], stream=(s or stream).cuda_stream)
 
-    ts = time_graph(step_syn, max(3, args.steps // 4), 3, flush, stream)
-    synthesis = {"coeffs_per_s": coeffs_per_step / statistics.mean(ts), "ms_per_step": 1e3 * statistics.mean(ts),
-                 "frac_of_peak": alg_bytes / statistics.mean(ts) / 1e9 / peak}
-    del ysyn
+    ts, ts_fl = time_steady_and_flushed([lambda s=None, i=i: step_syn(s, i) for i in range(ROTATE_SETS)],
+                                        max(3, args.steps // 4), 3, flush, stream)
+    synthesis = {"coeffs_per_s": coeffs_per_step / ts, "ms_per_step": 1e3 * ts,
+                 "frac_of_peak": alg_bytes / ts / 1e9 / peak, "ms_per_step_after_l2_write_flush": 1e3 * ts_fl}
+    del zs
     # context only: a library batched k-point C2C FFT (cuFFT through torch.fft)
     # over the same batch moves the same bytes with a regular twiddle pattern
     yfft = torch.empty_like(x32)
@@ -427,6 +430,20 @@ def time_rotating(fns, steps, warmup, stream):
     return a.elapsed_time(b) * 1e-3
 
 
+def steady_sets(bytes_per_set):
+    """Buffer sets a steady-state timing rotates over: enough that at least
+    1 GiB (several L2 capacities) of traffic passes between two uses of a set."""
+    return max(1, min(32, -(-(1 << 30) // max(1, bytes_per_set)) + 1)) if bytes_per_set < (1 << 30) else 1
+
+
+def time_steady_and_flushed(fns, steps, warmup, flush, stream):
+    """(steady-state seconds per step over the rotating sets `fns`, seconds per
+    step of set 0 timed one by one after the 256 MiB L2 write flush)."""
+    steady = time_rotating(fns, steps, warmup, stream) / steps
+    flushed = statistics.mean(time_graph(fns[0], steps, warmup, flush, stream))
+    return steady, flushed
+
+
 def run_single(args):
     """Single-instance leg: N = 2^10, k = 2^5, complex128 (latency): one
     execute per step as a CUDA-graph replay, and the relative L2 against the
@@ -476,9 +493,10 @@ def run_large(args):
             plan.execute_strided(x, y, stream=(s or stream).cuda_stream)
 
         coeffs = args.large_batch * inst.k
-        # both strategies x three or four stages per pass, each graph-replayed
-        # with the L2 flush between steps (the queue strategy's first call builds
-        # its queue, so it runs before capture); the leg reports the fastest
+        # both strategies x three or four stages per pass, each graph-replayed,
+        # steps back to back (the input, 537 MB, is far larger than L2; the
+        # queue strategy's first call builds its queue, so it runs before
+        # capture); the leg reports the fastest
         from paper_2211_15299_gb300 import _native as N
         by = {}
         for name in ("levels", "queue"):
@@ -487,12 +505,12 @@ def run_large(args):
                 N.sdft_plan_set_stages_per_pass(plan.handle, spp)
                 step()
                 torch.cuda.synchronize()
-                t = time_graph(step, args.steps, args.warmup, flush, stream)
-                by[f"{name}/{spp}"] = statistics.mean(t)
+                by[f"{name}/{spp}"] = time_rotating([step], args.steps, args.warmup, stream) / args.steps
         best = min(by, key=by.get)
         mean = by[best]
         plan.set_strategy(best.split("/")[0])
         N.sdft_plan_set_stages_per_pass(plan.handle, int(best.split("/")[1]))
+        flushed = statistics.mean(time_graph(step, args.steps, args.warmup, flush, stream))
         step()
         # the oracle on the host cores: 16 of the instances (the last strategy's output)
         torch.cuda.synchronize()
@@ -505,6 +523,7 @@ def run_large(args):
             "coeffs_per_s": coeffs / mean, "ms_per_step": 1e3 * mean, "strategy": best.split("/")[0],
             "stages_per_pass": int(best.split("/")[1]),
             "ms_by_strategy_and_stages_per_pass": {k: 1e3 * v for k, v in by.items()}, "cpu_oracle": cpu_oracle,
+            "ms_per_step_after_l2_write_flush": 1e3 * flushed,
             "alg_GBps": 16 * coeffs / mean / 1e9, "frac_of_peak": 16 * coeffs / mean / 1e9 / _peaks()[0],
             "pivots": [int(p) for p in inst.pivots]}
         assert plan.device_status() == 0
@@ -559,8 +578,8 @@ def run_uneven(args):
     def step(s=None):
         b.execute(x, y, stream=(s or stream).cuda_stream)
 
-    t = time_graph(step, args.steps, args.warmup, flush, stream)
-    mean = statistics.mean(t)
+    # steps back to back (the packed input is far larger than L2)
+    mean, flushed = time_steady_and_flushed([step], args.steps, args.warmup, flush, stream)
     total = b.total
     tw_bytes = sum(8 * (p.k - 1) for p in plans)
     # the oracle on the host cores: the first 64 instances, one call each
@@ -582,6 +601,8 @@ def run_uneven(args):
     return {"instances": len(plans), "coeffs_per_step": total, "coeffs_per_s": total / mean,
             "cpu_oracle": cpu_oracle,
             "ms_per_step": 1e3 * mean, "alg_GBps": (16 * total + tw_bytes) / mean / 1e9,
+            "frac_of_peak": (16 * total + tw_bytes) / mean / 1e9 / _peaks()[0],
+            "ms_per_step_after_l2_write_flush": 1e3 * flushed,
             "alg_bytes_per_step": 16 * total + tw_bytes, "work_items": n_items,
             "dependency_counters": n_ctr, "grid": grid, "plan_build_s": t_plan,
             "autotune": {"schedule": schedule, "grid": grid, "stages_per_pass": spp_tuned,
@@ -608,21 +629,27 @@ def run_sas(args):
         t_plan = time.perf_counter() - t0
         g = torch.Generator(device=dev)
         g.manual_seed(W.BASE_SEED + 6)
-        x = torch.randn((args.sas_batch, p.n_samples), dtype=torch.complex64, device=dev, generator=g)
-        w = torch.empty_like(x)
-        y = torch.empty((args.sas_batch, p.k), dtype=torch.complex64, device=dev)
+        # buffer sets (samples, workspace, coefficients) rotated over so that no
+        # step finds its input in L2; set 0 is checked against the oracle
+        n_sets = steady_sets(8 * args.sas_batch * (2 * p.n_samples + p.k))
+        xs = [torch.randn((args.sas_batch, p.n_samples), dtype=torch.complex64, device=dev, generator=g)
+              for _ in range(n_sets)]
+        ws_ = [torch.empty_like(xs[0]) for _ in range(n_sets)]
+        ys = [torch.empty((args.sas_batch, p.k), dtype=torch.complex64, device=dev) for _ in range(n_sets)]
+        x, y = xs[0], ys[0]
 
-        def step(s=None):
-            p.execute(x, y, work=w, stream=(s or stream).cuda_stream)
+        def step(s=None, i=0):
+            p.execute(xs[i], ys[i], work=ws_[i], stream=(s or stream).cuda_stream)
 
-        t = time_graph(step, args.steps, args.warmup, flush, stream)
-        mean = statistics.mean(t)
+        mean, flushed = time_steady_and_flushed([lambda s=None, i=i: step(s, i) for i in range(n_sets)],
+                                                args.steps, args.warmup, flush, stream)
         coeffs = args.sas_batch * p.k
         alg = 8 * args.sas_batch * (p.n_samples + p.k)        # samples in, coefficients out
         peak, peak_kind = _peaks()
         entry = {"k": p.k, "R": p.R, "mu_star": p.mu_star, "samples_per_instance": p.n_samples,
                  "max_cond": p.max_cond, "batch": args.sas_batch, "coeffs_per_s": coeffs / mean,
-                 "ms_per_step": 1e3 * mean, "plan_s": t_plan,
+                 "ms_per_step": 1e3 * mean, "plan_s": t_plan, "buffer_sets": n_sets,
+                 "ms_per_step_after_l2_write_flush": 1e3 * flushed,
                  "roofline": {"bound": "hbm", "achieved": alg / mean / 1e9, "peak": peak, "unit": "GB/s",
                               "frac": alg / mean / 1e9 / peak, "peak_kind": peak_kind,
                               "alg_bytes_per_step": alg},
