@@ -653,7 +653,8 @@ def run_sas(args):
                  "roofline": {"bound": "hbm", "achieved": alg / mean / 1e9, "peak": peak, "unit": "GB/s",
                               "frac": alg / mean / 1e9 / peak, "peak_kind": peak_kind,
                               "alg_bytes_per_step": alg},
-                 "launches_per_step": p.launches + (1 if p.R > 12 else 0)}
+                 "launches_per_step": p.launches + (1 if p.R > 12 else 0),
+                 "gathered_stage_one": p.gathered}
         if not args.no_cpu:
             # the oracle's SAS (numpy FP64) on a few of the same instances
             import oracle as O

@@ -516,12 +516,17 @@ sdft_status sdft_sas_workspace_bytes(sdft_sas sas, uint64_t batch, uint64_t* byt
  * (support_order), d_work is the workspace (it may be d_samples itself, which
  * is then overwritten; it must not overlap d_coeffs). Stage 1 runs the virtual
  * plan over the batch x mu* shifted sample sets (Algorithm 1); stage 2 solves
- * each class with its precomputed inverse. Under complete isolation (mu* = 1)
- * with one virtual instance per tile (R = 12 for complex64, 11 for complex128;
- * then k <= 2^R) both stages run in one launch that keeps the stage-1 output
- * on chip: d_work is then not touched and d_samples must not overlap d_coeffs
- * (SDFT_SAS_TWO_STAGE keeps the two launches). Both paths give the same bits. Device buffers 16-byte
- * aligned; asynchronous on `stream`. SDFT_ERR_NO_DEVICE for host-only plans.
+ * each class with its precomputed inverse. Where one to four virtual
+ * instances fill a tile (R in [10, 12] for complex64, [9, 11] for complex128):
+ *   - under complete isolation (mu* = 1, k <= 2^12 / 2^11) both stages run in
+ *     one launch that keeps the stage-1 output on chip: d_work is then not
+ *     touched and d_samples must not overlap d_coeffs;
+ *   - with mu* > 1 (k <= 8192) and d_work apart from d_samples, stage 1 writes
+ *     to d_work only the k values per instance that the class solves read
+ *     (the first batch x k values of d_work), instead of all mu* x 2^R.
+ * SDFT_SAS_TWO_STAGE keeps the two launches over the whole stage-1 output.
+ * All paths give the same bits. Device buffers 16-byte aligned; asynchronous
+ * on `stream`. SDFT_ERR_NO_DEVICE for host-only plans.
  */
 sdft_status sdft_sas_execute(sdft_sas sas, uint64_t batch, const void* d_samples, void* d_work, void* d_coeffs,
                              void* stream);

@@ -24,6 +24,7 @@
 #include <complex>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -62,6 +63,8 @@ struct Sas {
   bool two_stage = false;          // SDFT_SAS_TWO_STAGE: stage 2 as its own launch always
   uint16_t* d_col = nullptr;       // one-launch path (mu* = 1): t_i per coefficient
   void* d_w1 = nullptr;            //   and its class's 1 x 1 inverse
+  uint32_t* d_gather = nullptr;    // gathered path (mu* > 1): t_i | i << 16, grouped by u_i
+  std::vector<uint32_t> goff;      //   entries of shift a: [goff[a], goff[a + 1])
 };
 
 // Class keys of J for pivots p[0..R-1]: bit q of the key is bit p[q] of j.
@@ -287,8 +290,12 @@ sdft_status build_sas(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec,
 // thread takes coefficient i of kSasDecodeB instances b = blockIdx.y + q
 // gridDim.y (q < kSasDecodeB): its class's inverse row is read once for all of
 // them and their values are gathered together.
+// GATHERED: the stage-1 values arrive in output order, G[b][i] = Y[b][u_i][t_i]
+// (k per instance), so the mu values of coefficient i's class are
+// G[b][i - u + a], a < mu: adjacent, read from consecutive addresses by
+// consecutive threads. The sums are formed in the same order either way.
 constexpr uint32_t kSasDecodeB = 8;
-template <class R>
+template <class R, bool GATHERED = false>
 __global__ void __launch_bounds__(256) k_sas_decode(const typename KT<R>::C* __restrict__ y,
                                                     typename KT<R>::C* __restrict__ out,
                                                     const SasOut* __restrict__ meta,
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(256) k_sas_decode(const typename KT<R>::C* __r
       for (uint32_t q = 0; q < kSasDecodeB; ++q) {
         const uint64_t b = b0 + uint64_t(q) * gridDim.y;
         if (b < batch) {
-          const C v = y[(b * uint64_t(mu_star) + a) * nk + m.t];
+          const C v = GATHERED ? y[b * k + (i - m.u + a)] : y[(b * uint64_t(mu_star) + a) * nk + m.t];
           re[q] = fma(w.x, v.x, fma(-w.y, v.y, re[q]));
           im[q] = fma(w.x, v.y, fma(w.y, v.x, im[q]));
         }
@@ -334,21 +341,31 @@ __global__ void __launch_bounds__(256) k_sas_decode(const typename KT<R>::C* __r
 }
 
 // Both stages in one launch for complete isolation (mu* = 1: every class holds
-// one member, coefficient i = Winv_i Y[t_i]) when one virtual instance fills one
-// tile (R = TB) and k <= 2^TB: CTA c takes instances b = c, c + G, ... (one tile
-// each, the level kernel's passes with the last stage scaled), keeps the
+// one member, coefficient i = Winv_i Y[t_i]) when one to four virtual instances
+// fill one tile (TB - 2 <= R <= TB) and k <= 2^TB: CTA c takes tiles c, c + G,
+// ... (the level kernel's passes with the last stage scaled), keeps the
 // per-coefficient pairs (t_i, Winv_i) in shared memory for the whole launch,
 // and after the passes writes every coefficient straight from the tile. The
 // stage-1 output never leaves the SM; the product is formed as in k_sas_decode,
 // so both paths give the same bits. (With mu* > 1 the class solves need mu*
 // tiles per instance and their inverse rows: they stay a launch of their own.)
+// GATHER (mu* > 1, the same tile shape): the kernel runs stage 1 over the
+// batch x mu* shifted sample sets (tile r: instance r / mu*, shift r mod mu*)
+// and writes, from the tile of shift a, only the values the class solves
+// read: G[b][i] = Y[b][a][t_i] for every coefficient i whose place in its
+// class is u_i = a. The workspace then holds k values per instance in output
+// order instead of mu* x 2^R, and stage 2 (k_sas_decode, GATHERED) reads a
+// class's mu values side by side.
 template <class R>
 struct SasFusedArgs {
-  LevelArgs<R> a;                        // level 0 of the virtual plan over the batch
+  LevelArgs<R> a;                        // level 0 of the virtual plan over the tiles
   const uint16_t* col;                   // t_i: column of the stage-1 output
   const typename KT<R>::C* w;            // Winv_i (1 x 1 inverses)
-  typename KT<R>::C* out;                // batch x k coefficients
-  uint64_t k, batch;
+  typename KT<R>::C* out;                // batch x k coefficients (GATHER: the batch x k workspace G)
+  uint64_t k, rows;                      // coefficients per instance; tiles = batch x mu*
+  const uint32_t* gtab;                  // GATHER: t_i | i << 16, grouped by u_i
+  uint32_t mu_star;
+  uint32_t goff[kSasMaxMu + 1];          // GATHER: entries of shift a are [goff[a], goff[a + 1])
 };
 
 template <class R>
@@ -357,14 +374,19 @@ constexpr uint32_t sas_fused_smem() {
          (1u << KT<R>::TB) * uint32_t(sizeof(typename KT<R>::C) + sizeof(uint16_t)) + 1024;
 }
 
-template <class R>
+// PHI = R: a tile holds 2^(TB - R) consecutive rows (virtual instances) of
+// 2^R values; row q of tile j is row j 2^(TB - R) + q of the batch (rows past
+// the last are the zero fill of the tile's load and are skipped).
+template <class R, bool GATHER, int PHI>
 __global__ void __launch_bounds__(KT<R>::NT, 2)
     k_sas_fused(const __grid_constant__ CUtensorMap src, const __grid_constant__ SasFusedArgs<R> fa) {
   using C = typename KT<R>::C;
   constexpr int TB = KT<R>::TB;
+  static_assert(PHI >= 5 && PHI <= TB, "one or more whole rows per tile");
+  constexpr uint32_t RP = 1u << (TB - PHI);        // rows per tile
   constexpr uint32_t NT = KT<R>::NT;
-  constexpr int NREG = reg_twiddles(TB, 4, 0, TB);
-  constexpr int MLO = mid_pass_lo(TB, 4, 0, TB), MHI = mid_pass_hi(TB, 4, 0, TB);
+  constexpr int NREG = reg_twiddles(TB, 4, 0, PHI);
+  constexpr int MLO = mid_pass_lo(TB, 4, 0, PHI), MHI = mid_pass_hi(TB, 4, 0, PHI);
   constexpr bool MIDSM = MLO < MHI && (1u << MHI) * sizeof(C) <= kMidTwBytes;
   extern __shared__ char smem_raw[];
   char* smem = align1024(smem_raw);
@@ -373,6 +395,7 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   C* midtw = reinterpret_cast<C*>(smem + kLevelBufs * kTileBytes + 64);
   C* ws = reinterpret_cast<C*>(smem + kLevelBufs * kTileBytes + 64 + kMidTwBytes);
   uint16_t* cs = reinterpret_cast<uint16_t*>(ws + (1u << TB));
+  uint32_t* gs = reinterpret_cast<uint32_t*>(ws);    // GATHER: the gather table (k <= 8192 entries)
   {
     const uint32_t used = uint32_t(smem - smem_raw) + sas_fused_smem<R>() - 1024;
     int bad = 0;
@@ -385,8 +408,8 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     }
   }
   const uint64_t G = gridDim.x;
-  if (blockIdx.x >= fa.batch) return;
-  const uint64_t n = (fa.batch - blockIdx.x + G - 1) / G;     // instances (tiles) of this CTA
+  if (blockIdx.x >= fa.a.n_tiles) return;
+  const uint64_t n = (fa.a.n_tiles - blockIdx.x + G - 1) / G;     // tiles of this CTA
   uint32_t load_buf = 0;
   auto issue_load = [&](uint64_t j) {
     const uint32_t b = load_buf;
@@ -405,13 +428,17 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   }
   const C* tw = static_cast<const C*>(fa.a.tw);
   C wreg[NREG > 0 ? NREG : 1];
-  load_reg_twiddles<R, 4, 0, TB>(tw, tid, wreg);
+  load_reg_twiddles<R, 4, 0, PHI>(tw, tid, wreg);
   if constexpr (MIDSM) {
     for (uint32_t e = (1u << MLO) + tid; e < (1u << MHI); e += NT) midtw[e] = tw[e];
   }
-  for (uint64_t i = tid; i < fa.k; i += NT) {   // the decode table, once per CTA
-    ws[i] = fa.w[i];
-    cs[i] = fa.col[i];
+  for (uint64_t i = tid; i < fa.k; i += NT) {   // the decode (gather) table, once per CTA
+    if constexpr (GATHER) {
+      gs[i] = fa.gtab[i];
+    } else {
+      ws[i] = fa.w[i];
+      cs[i] = fa.col[i];
+    }
   }
   __syncthreads();
   const uint32_t midtw_addr = ptx::smem_addr(midtw);
@@ -431,17 +458,34 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
     auto refill = [&]() {
       if (tid == 0 && j >= 1 && j + kLevelBufs - 1 < n) issue_load(j + kLevelBufs - 1);
     };
-    run_passes<R, 4, 0, TB, true, 0, 0, MIDSM>(buf, wreg, fa.a.tw0, tw, tid, sc, midtw_addr, refill);
-    C* ob = fa.out + (blockIdx.x + j * G) * fa.k;
-    for (uint64_t i = tid; i < fa.k; i += NT) {
-      const C w = ws[i];
-      uint32_t t = cs[i];
-      if (!in_bounds(t < (1u << TB), fa.a.status)) t = 0;   // debug build
-      const C v = *reinterpret_cast<const C*>(buf + row_part<R>(t) + xor_part<R>(t));
-      C o;
-      o.x = fma(w.x, v.x, fma(-w.y, v.y, R(0)));
-      o.y = fma(w.x, v.y, fma(w.y, v.x, R(0)));
-      ob[i] = o;
+    run_passes<R, 4, 0, PHI, true, 0, 0, MIDSM>(buf, wreg, fa.a.tw0, tw, tid, sc, midtw_addr, refill);
+#pragma unroll 1
+    for (uint32_t q = 0; q < RP; ++q) {
+      const uint64_t r = (blockIdx.x + j * G) * RP + q;
+      if (r >= fa.rows) break;
+      const uint32_t base = q << PHI;                 // the row's first value in the tile
+      if constexpr (GATHER) {
+        const uint32_t a = uint32_t(r % fa.mu_star);
+        C* gb = fa.out + (r / fa.mu_star) * fa.k;
+        for (uint32_t e = fa.goff[a] + tid; e < fa.goff[a + 1]; e += NT) {
+          const uint32_t g = gs[e];
+          const uint32_t t = g & 0xffffu, i = g >> 16;
+          if (!in_bounds(t < (1u << PHI) && i < fa.k, fa.a.status)) continue;   // debug build
+          gb[i] = *reinterpret_cast<const C*>(buf + row_part<R>(base + t) + xor_part<R>(base + t));
+        }
+      } else {
+        C* ob = fa.out + r * fa.k;
+        for (uint64_t i = tid; i < fa.k; i += NT) {
+          const C w = ws[i];
+          uint32_t t = cs[i];
+          if (!in_bounds(t < (1u << PHI), fa.a.status)) t = 0;   // debug build
+          const C v = *reinterpret_cast<const C*>(buf + row_part<R>(base + t) + xor_part<R>(base + t));
+          C o;
+          o.x = fma(w.x, v.x, fma(-w.y, v.y, R(0)));
+          o.y = fma(w.x, v.y, fma(w.y, v.x, R(0)));
+          ob[i] = o;
+        }
+      }
     }
   }
   if (tid == 0 && aborted) {
@@ -454,36 +498,58 @@ __global__ void __launch_bounds__(KT<R>::NT, 2)
   }
 }
 
+// One launch of k_sas_fused over the batch: the coefficients (mu* = 1) or,
+// with `gather`, the gathered stage-1 values G into d_out (mu* > 1).
 template <class R>
-sdft_status launch_sas_fused(const Sas& S, uint64_t batch, const void* d_samples, void* d_coeffs,
+sdft_status launch_sas_fused(const Sas& S, uint64_t batch, const void* d_samples, void* d_out, bool gather,
                              cudaStream_t st) {
   const Plan& vp = S.vplan->p;
+  const uint64_t rows = batch * (gather ? S.mu_star : 1u);
   CUtensorMap ms, md;
   SasFusedArgs<R> fa{};
-  sdft_status s = level0_setup<R>(vp, batch, d_samples, const_cast<void*>(d_samples), ms, md, fa.a);
+  sdft_status s = level0_setup<R>(vp, rows, d_samples, const_cast<void*>(d_samples), ms, md, fa.a);
   if (s != SDFT_OK) return s;
   fa.col = S.d_col;
   fa.w = static_cast<const typename KT<R>::C*>(S.d_w1);
-  fa.out = static_cast<typename KT<R>::C*>(d_coeffs);
+  fa.out = static_cast<typename KT<R>::C*>(d_out);
   fa.k = S.k;
-  fa.batch = batch;
-  auto fn = k_sas_fused<R>;
+  fa.rows = rows;
+  fa.gtab = S.d_gather;
+  fa.mu_star = gather ? S.mu_star : 1u;
+  if (gather)
+    for (uint32_t a = 0; a <= S.mu_star; ++a) fa.goff[a] = S.goff[a];
+  constexpr int TB = KT<R>::TB;
+  const int d = int(TB) - int(S.R);                 // R in [TB - 2, TB] (sas_*_shape)
+  auto fn = gather ? (d == 0 ? k_sas_fused<R, true, TB> : d == 1 ? k_sas_fused<R, true, TB - 1>
+                                                                 : k_sas_fused<R, true, TB - 2>)
+                   : (d == 0 ? k_sas_fused<R, false, TB> : d == 1 ? k_sas_fused<R, false, TB - 1>
+                                                                  : k_sas_fused<R, false, TB - 2>);
   s = ensure_smem(reinterpret_cast<const void*>(fn), int(sas_fused_smem<R>()));
   if (s != SDFT_OK) return s;
   const uint64_t max_grid = 2ull * uint64_t(sm_count());
-  const unsigned grid = unsigned(batch < max_grid ? batch : max_grid);
+  const unsigned grid = unsigned(fa.a.n_tiles < max_grid ? fa.a.n_tiles : max_grid);
   fn<<<grid, KT<R>::NT, sas_fused_smem<R>(), st>>>(ms, fa);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
 }
 
-// Complete isolation, one virtual instance per tile, at most a tile's worth of
-// coefficients.
-bool sas_fused_shape(const Sas& S) {
+// Complete isolation, one to four virtual instances per tile (R in
+// [TB - 2, TB]), at most a tile's worth of coefficients.
+bool sas_tile_shape(const Sas& S) {
   const uint32_t TB = S.prec == SDFT_C64 ? KT<float>::TB : KT<double>::TB;
-  return S.mu_star == 1 && S.R == TB && S.k <= (1ull << TB);
+  return S.R <= TB && S.R + 2 >= TB && S.k <= (1ull << TB);
 }
+bool sas_fused_shape(const Sas& S) { return S.mu_star == 1 && sas_tile_shape(S); }
 bool sas_fused_applies(const Sas& S) { return !S.two_stage && S.d_col && S.d_w1 && sas_fused_shape(S); }
+// mu* > 1 with the same tile shape: stage 1 writes only the values stage 2 reads.
+// The gather table (one 32-bit entry per coefficient) sits in the shared
+// memory of the mu* = 1 table, 2^TB complex values: up to 8192 coefficients.
+bool sas_gather_shape(const Sas& S) {
+  const uint32_t TB = S.prec == SDFT_C64 ? KT<float>::TB : KT<double>::TB;
+  const uint64_t cap = (uint64_t(1) << TB) * uint64_t(elem_bytes(S.prec)) / sizeof(uint32_t);
+  return S.mu_star > 1 && S.mu_star <= kSasMaxMu && S.R <= TB && S.R + 2 >= TB && S.k <= cap;
+}
+bool sas_gather_applies(const Sas& S) { return !S.two_stage && S.d_gather && sas_gather_shape(S); }
 
 void free_sas(Sas& S) {
   if (S.vplan) sdft_plan_destroy(S.vplan);
@@ -491,6 +557,8 @@ void free_sas(Sas& S) {
   if (S.d_winv) cudaFree(S.d_winv);
   if (S.d_col) cudaFree(S.d_col);
   if (S.d_w1) cudaFree(S.d_w1);
+  if (S.d_gather) cudaFree(S.d_gather);
+  S.d_gather = nullptr;
   S.d_col = nullptr;
   S.d_w1 = nullptr;
   S.vplan = nullptr;
@@ -567,6 +635,22 @@ sdft_status sdft_sas_create(uint32_t log2N, const uint64_t* J, uint64_t k, sdft_
         }
       }
     }
+    // the gathered path's table: coefficient i (its column t_i) in the group of
+    // the shift u_i, the place of i in its class
+    if (st == SDFT_OK && e == cudaSuccess && sas_gather_shape(S)) {
+      std::vector<uint32_t> g;
+      g.reserve(S.k);
+      S.goff.assign(S.mu_star + 1, 0);
+      for (uint32_t a = 0; a < S.mu_star; ++a) {
+        S.goff[a] = uint32_t(g.size());
+        for (uint64_t i = 0; i < S.k; ++i)
+          if (S.meta[i].u == a) g.push_back(S.meta[i].t | uint32_t(i) << 16);
+      }
+      S.goff[S.mu_star] = uint32_t(g.size());
+      e = cudaMalloc(reinterpret_cast<void**>(&S.d_gather), sizeof(uint32_t) * g.size());
+      if (e == cudaSuccess)
+        e = cudaMemcpy(S.d_gather, g.data(), sizeof(uint32_t) * g.size(), cudaMemcpyHostToDevice);
+    }
     if (st == SDFT_OK && e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? SDFT_ERR_NOMEM : cuda_fail(e);
   }
   if (st != SDFT_OK) {
@@ -634,23 +718,38 @@ sdft_status sdft_sas_execute(sdft_sas sas, uint64_t batch, const void* d_samples
     if (reinterpret_cast<uintptr_t>(d_samples) & 15u) return SDFT_ERR_ARG;
     const uintptr_t in = reinterpret_cast<uintptr_t>(d_samples);
     if (in < o + obytes && o < in + wbytes) return SDFT_ERR_ARG;   // samples are read while coeffs are written
-    return S.prec == SDFT_C64 ? launch_sas_fused<float>(S, batch, d_samples, d_coeffs, st)
-                              : launch_sas_fused<double>(S, batch, d_samples, d_coeffs, st);
+    return S.prec == SDFT_C64 ? launch_sas_fused<float>(S, batch, d_samples, d_coeffs, false, st)
+                              : launch_sas_fused<double>(S, batch, d_samples, d_coeffs, false, st);
   }
-  sdft_status s = sdft_execute_strided(S.vplan, batch * S.mu_star, d_samples, d_work, stream);
+  // gathered stage 1 where the workspace is not the samples buffer (tiles of
+  // later instances are still to be read when earlier ones are written)
+  const uintptr_t in = reinterpret_cast<uintptr_t>(d_samples);
+  const bool gather = sas_gather_applies(S) && !(in < w + wbytes && w < in + wbytes) && !(in & 15u);
+  sdft_status s = SDFT_OK;
+  if (gather)
+    s = S.prec == SDFT_C64 ? launch_sas_fused<float>(S, batch, d_samples, d_work, true, st)
+                           : launch_sas_fused<double>(S, batch, d_samples, d_work, true, st);
+  else
+    s = sdft_execute_strided(S.vplan, batch * S.mu_star, d_samples, d_work, stream);
   if (s != SDFT_OK) return s;
   const dim3 block(256);
   const uint64_t rows = (batch + kSasDecodeB - 1) / kSasDecodeB;
   const dim3 grid(unsigned((S.k + 255) / 256), unsigned(std::min<uint64_t>(rows, 65535)));
+  auto decode = [&](auto* work, auto* coeffs, auto* winv) {
+    using C = std::remove_const_t<std::remove_pointer_t<decltype(work)>>;
+    using RR = decltype(C{}.x);
+    if (gather)
+      k_sas_decode<RR, true><<<grid, block, 0, st>>>(work, coeffs, S.d_meta, winv, S.k, nk, S.mu_star, batch,
+                                                     S.winv.size(), S.vplan->p.d_status);
+    else
+      k_sas_decode<RR, false><<<grid, block, 0, st>>>(work, coeffs, S.d_meta, winv, S.k, nk, S.mu_star, batch,
+                                                      S.winv.size(), S.vplan->p.d_status);
+  };
   if (S.prec == SDFT_C64)
-    k_sas_decode<float><<<grid, block, 0, st>>>(static_cast<const float2*>(d_work), static_cast<float2*>(d_coeffs),
-                                                S.d_meta, static_cast<const float2*>(S.d_winv), S.k, nk, S.mu_star,
-                                                batch, S.winv.size(), S.vplan->p.d_status);
+    decode(static_cast<const float2*>(d_work), static_cast<float2*>(d_coeffs), static_cast<const float2*>(S.d_winv));
   else
-    k_sas_decode<double><<<grid, block, 0, st>>>(static_cast<const double2*>(d_work),
-                                                 static_cast<double2*>(d_coeffs), S.d_meta,
-                                                 static_cast<const double2*>(S.d_winv), S.k, nk, S.mu_star, batch,
-                                                 S.winv.size(), S.vplan->p.d_status);
+    decode(static_cast<const double2*>(d_work), static_cast<double2*>(d_coeffs),
+           static_cast<const double2*>(S.d_winv));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
 }

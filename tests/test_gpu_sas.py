@@ -147,3 +147,48 @@ def test_one_launch_and_two_launch_paths_agree_bitwise(kind, k, prec, batch):
     for b in (0, batch - 1):
         ref = O.sas_transform(20, order, r, f_in[b])
         assert rel_l2(got[b], ref) < _tol(prec, one.max_cond)
+
+
+@pytest.mark.parametrize("kind,k,prec,batch", [("subset", 3000, "c64", 700), ("subset", 3000, "c64", 1),
+                                               ("subset", 4000, "c64", 33), ("uoh", 3000, "c64", 301),
+                                               ("uoh", 2000, "c64", 51), ("subset", 3000, "c128", 45),
+                                               ("subset", 2000, "c128", 19),
+                                               ("ap", 2000, "c64", 301), ("ap", 1000, "c64", 7)])
+def test_tile_paths_agree_bitwise_with_the_two_launch_path(kind, k, prec, batch):
+    """Where one to four virtual instances fill a tile (TB - 2 <= R <= TB):
+    with mu* > 1 (k <= 8192), stage 1 writes only the k values per instance
+    that the class solves read (in output order), and with mu* = 1 (k <= 2^TB)
+    both stages share one launch. Each gives the same bits as the two-launch path over the whole
+    stage-1 output, as the in-place call (samples buffer as workspace, which
+    takes the whole-output path), and matches the oracle on a few rows. The
+    batches leave the last tile part-filled where a tile holds several rows."""
+    torch = _torch()
+    from paper_2211_15299_gb300 import Sas
+    J = [int(j) for j in W.workload_sas(kind, k=k)]
+    one = Sas(20, J, prec)
+    two = Sas(20, J, prec, two_stage=True)
+    tb = 12 if prec == "c64" else 11
+    assert tb - 2 <= one.R <= tb
+    assert (one.gathered, one.launches) == ((True, 2) if one.mu_star > 1 else (False, 1))
+    dt = torch.complex64 if prec == "c64" else torch.complex128
+    g = torch.Generator(device="cuda")
+    g.manual_seed(78)
+    x = torch.randn((batch, one.n_samples), dtype=dt, device="cuda", generator=g)
+    x_keep = x.clone()
+    y1 = one.execute(x)
+    y1b = one.execute(x)                       # a second call on the same workspace sizes
+    y2 = two.execute(x)
+    torch.cuda.synchronize()
+    assert torch.equal(x, x_keep)
+    assert torch.equal(y1, y2) and torch.equal(y1b, y1)
+    x3 = x.clone()
+    y3 = one.execute(x3, work=x3)               # in place
+    torch.cuda.synchronize()
+    assert torch.equal(y3, y1)
+    order = [int(j) for j in one.support_order]
+    r = [int(v) for v in one.pivots]
+    f_in = x.cpu().numpy().astype(np.complex128).reshape(batch, one.mu_star, -1)
+    got = y1.cpu().numpy().astype(np.complex128)
+    for b in sorted({0, batch // 2, batch - 1}):
+        ref = O.sas_transform(20, order, r, f_in[b])
+        assert rel_l2(got[b], ref) < _tol(prec, one.max_cond)
