@@ -510,6 +510,15 @@ sdft_status sdft_sas_support_order(sdft_sas sas, uint64_t* J);
 /* Device workspace that sdft_sas_execute needs for `batch` instances. */
 sdft_status sdft_sas_workspace_bytes(sdft_sas sas, uint64_t batch, uint64_t* bytes);
 
+/* How sdft_sas_execute runs this plan when d_samples, d_work and d_coeffs do
+ * not overlap (an implementation property, not part of Algorithm
+ * "shift-sample"): *launches = 1 where both stages share one launch, else 2
+ * (the strided transform itself takes more than one for R > 12);
+ * *work_values = the values per instance that stage 1 leaves in d_work: 0
+ * (none: one launch, mu* = 1), k (only those the class solves read) or
+ * mu* x 2^R (the whole stage-1 output). Either output may be NULL. */
+sdft_status sdft_sas_path(sdft_sas sas, uint32_t* launches, uint64_t* work_values);
+
 /*
  * sdft_sas_execute - coefficients of `batch` instances: d_samples holds
  * batch x mu* x 2^R values (sample_indices order), d_coeffs receives batch x k
@@ -524,7 +533,8 @@ sdft_status sdft_sas_workspace_bytes(sdft_sas sas, uint64_t batch, uint64_t* byt
  *   - with mu* > 1 (k <= 8192) and d_work apart from d_samples, stage 1 writes
  *     to d_work only the k values per instance that the class solves read
  *     (the first batch x k values of d_work), instead of all mu* x 2^R.
- * SDFT_SAS_TWO_STAGE keeps the two launches over the whole stage-1 output.
+ * sdft_sas_path tells which applies. SDFT_SAS_TWO_STAGE keeps the two
+ * launches over the whole stage-1 output.
  * All paths give the same bits. Device buffers 16-byte aligned; asynchronous
  * on `stream`. SDFT_ERR_NO_DEVICE for host-only plans.
  */

@@ -106,6 +106,7 @@ SIGNATURES = {
     "sdft_sas_sample_indices": (c_int, [c_vp, P_u64]),
     "sdft_sas_support_order": (c_int, [c_vp, P_u64]),
     "sdft_sas_workspace_bytes": (c_int, [c_vp, c_u64, P_u64]),
+    "sdft_sas_path": (c_int, [c_vp, P_u32, P_u64]),
     "sdft_sas_execute": (c_int, [c_vp, c_u64, c_vp, c_vp, c_vp, c_vp]),
     "sdft_sas_destroy": (c_int, [c_vp]),
     "sdft_server_create": (c_int, [c_int, c_u64, c_u32, c_u32, c_u32, ctypes.POINTER(c_vp)]),
@@ -460,6 +461,13 @@ def sdft_sas_workspace_bytes(sas: int, batch: int) -> int:
     out = c_u64()
     _check(_lib.sdft_sas_workspace_bytes(sas, int(batch), ctypes.byref(out)), "sdft_sas_workspace_bytes")
     return int(out.value)
+
+
+def sdft_sas_path(sas: int):
+    """Returns (launches per call, values per instance stage 1 leaves in the workspace)."""
+    l, v = c_u32(), c_u64()
+    _check(_lib.sdft_sas_path(sas, ctypes.byref(l), ctypes.byref(v)), "sdft_sas_path")
+    return int(l.value), int(v.value)
 
 
 def sdft_sas_execute(sas: int, batch: int, d_samples, d_work, d_coeffs, stream=None) -> None:

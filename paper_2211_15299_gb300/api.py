@@ -311,14 +311,11 @@ class Sas:
         flags = (N.SDFT_PLAN_HOST_ONLY if host_only else 0) | (N.SDFT_SAS_TWO_STAGE if two_stage else 0)
         self.handle = N.sdft_sas_create(log2N, J, self.prec, R, flags)
         self.R, self.mu_star, self.n_samples, self.occupied, self.max_cond = N.sdft_sas_info(self.handle)
-        # launches per execute: one under complete isolation with one to four
-        # virtual instances per tile (the rule of sdft_sas_execute), else two
-        tb = 12 if self.prec == N.SDFT_C64 else 11
-        tile = tb - 2 <= self.R <= tb
-        self.launches = 1 if (not two_stage and self.mu_star == 1 and tile and self.k <= (1 << tb)) else 2
-        # stage 1 writes only the values the class solves read (mu* > 1, the
-        # same tile shapes, k <= 8192, workspace apart from the samples)
-        self.gathered = not two_stage and 1 < self.mu_star <= 64 and tile and self.k <= 8192
+        # launches per execute and the values per instance that stage 1 leaves
+        # in the workspace, with the three buffers apart (sdft_sas_path)
+        self.launches, self.work_values = N.sdft_sas_path(self.handle)
+        # stage 1 writes only the values the class solves read
+        self.gathered = self.mu_star > 1 and self.work_values == self.k
 
     @property
     def pivots(self) -> np.ndarray:

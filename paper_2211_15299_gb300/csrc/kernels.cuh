@@ -125,7 +125,6 @@ constexpr int kBadTable = 0x103;  // twiddle table not 16-byte aligned
 // caused the abort; the CTA only releases its shared memory once they landed.
 constexpr uint64_t kDrainNs = 2000000000ull;
 __host__ __device__ constexpr uint64_t drain_bound(uint64_t t) { return t > kDrainNs ? t : kDrainNs; }
-constexpr int kBufs = 3;                                             // tile buffers per work-queue CTA
 // Tile buffers per level-kernel CTA. Two keep the level kernel at the speed of a
 // copy-only variant of itself (TMA in and out, no passes) on the 2^12-point
 // batches, and leave more of the SM's combined L1/shared storage to the L1 cache

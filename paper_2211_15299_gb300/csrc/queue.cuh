@@ -24,6 +24,10 @@
 namespace sdft {
 
 constexpr uint32_t kNone = 0xffffffffu;
+// Tile buffers per CTA. Two leave the L1 room for the next item's table
+// entries, which the compute warps prefetch there; the dependency distance of
+// four items per CTA (see above) stays above the buffers plus one.
+constexpr int kQBufs = 2;
 
 struct QItem {            // 48 bytes
   uint16_t variant;       // kind and template variant, see q_variant_*
@@ -80,10 +84,10 @@ template <class R, int W, bool ST = false>
 constexpr uint32_t q_tw_entries() { return ST ? (1u << KT<R>::TB) : (W == 3 ? 512u : 256u); }
 template <class R, int W, bool ST = false>
 constexpr uint32_t q_tw_bytes() { return q_tw_entries<R, W, ST>() * KT<R>::ES; }
-constexpr uint32_t kQTwOff = kBufs * kTileBytes + 64 + kMetaSlots * sizeof(QItem);
+constexpr uint32_t kQTwOff = kQBufs * kTileBytes + 64 + kMetaSlots * sizeof(QItem);
 static_assert(kQTwOff % 16 == 0, "table copies need 16-byte alignment");
 template <class R, int W, bool ST = false>
-constexpr uint32_t q_smem() { return kQTwOff + kBufs * q_tw_bytes<R, W, ST>() + 1024; }
+constexpr uint32_t q_smem() { return kQTwOff + kQBufs * q_tw_bytes<R, W, ST>() + 1024; }
 
 // Entries [lo, hi) of an item's table staged in shared memory, for a tile
 // whose stages are [PLO, TB): the first pass's entries (PLO = 0) and the
@@ -303,7 +307,7 @@ constexpr uint32_t q_threads() { return tile_threads<R, W>() + 32; }   // comput
 __device__ __forceinline__ bool q_is_tma(const QItem& it) { return it.variant != kVSmall && it.variant != kVNop; }
 
 __device__ __forceinline__ const QItem& q_meta(char* smem, uint64_t j) {
-  return reinterpret_cast<const QItem*>(smem + kBufs * kTileBytes + 64)[j % kMetaSlots];
+  return reinterpret_cast<const QItem*>(smem + kQBufs * kTileBytes + 64)[j % kMetaSlots];
 }
 
 // Range checks of a work-item record (debug build): map slots, tile origins
@@ -324,18 +328,19 @@ __device__ __forceinline__ bool q_item_in_bounds(const QParams& prm, const QItem
 }
 
 // The producer warp's loop (lane 0). CTA c takes items c, c + G, ... Iteration
-// j: (1) once item i = j - 3 is computed (empty[i % 3]), store it from its
-// buffer, commit one bulk group, and publish item i - 1's counter (its store
-// complete); (2) load item j into the freed buffer (after its dependency, if
-// any, is met) and announce it on full[j % 3]; fetch record j + 3. A counter is
-// published before the dependency wait of the item four places later in the
-// same CTA, so items that wait on one another sit at least 4 x grid list
-// positions apart and every wait ends (all CTAs are resident).
+// j: (1) once item i = j - kQBufs is computed (empty[i % kQBufs]), store it
+// from its buffer, commit one bulk group, and publish item i - 1's counter (its
+// store complete); (2) load item j into the freed buffer (after its
+// dependency, if any, is met) and announce it on full[j % kQBufs]; fetch record
+// j + 3 (into the slot of item j - 3, stored already). A counter is published
+// before the dependency wait of the item kQBufs + 1 places later in the same
+// CTA; the host places items that wait on one another at least 4 x grid list
+// positions apart, so every wait ends (all CTAs are resident).
 template <class R, int W, bool ST>
 __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint64_t n) {
   const uint64_t c = blockIdx.x, G = gridDim.x;
-  const uint32_t bars = ptx::smem_addr(smem + kBufs * kTileBytes);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kBufs * kTileBytes + kQAbort);
+  const uint32_t bars = ptx::smem_addr(smem + kQBufs * kTileBytes);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kQBufs * kTileBytes + kQAbort);
   const uint64_t tmo = prm.a.timeout_ns;
   auto fetch_record = [&](uint64_t j) {
     if (j < n) {
@@ -353,11 +358,11 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
   const void* last_tab = nullptr;     // table of the last item whose tables were prefetched
   bool failed = false;
   uint64_t j = 0;
-  for (; j < n + kBufs; ++j) {
-    const uint32_t b = uint32_t(j % kBufs);
-    if (j >= kBufs) {
-      const uint64_t i = j - kBufs;
-      if (!ptx::mbar_wait_bounded(bars + kQEmpty + 8 * b, uint32_t((i / kBufs) & 1), tmo)) {
+  for (; j < n + kQBufs; ++j) {
+    const uint32_t b = uint32_t(j % kQBufs);
+    if (j >= kQBufs) {
+      const uint64_t i = j - kQBufs;
+      if (!ptx::mbar_wait_bounded(bars + kQEmpty + 8 * b, uint32_t((i / kQBufs) & 1), tmo)) {
         failed = true;
         break;
       }
@@ -427,7 +432,7 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
           ptx::bulk_load(ptx::smem_addr(smem + kQTwOff + b * q_tw_bytes<R, W, ST>()) + uint32_t(slo) * KT<R>::ES,
                          static_cast<const char*>(it.tw) + size_t(slo) * KT<R>::ES, tw_bytes, full);
         inflight |= 1u << b;
-        load_par = (load_par & ~(1u << b)) | (uint32_t((j / kBufs) & 1) << b);
+        load_par = (load_par & ~(1u << b)) | (uint32_t((j / kQBufs) & 1) << b);
         // the item's tables into L2 while its tile is in flight (once per table
         // in a row of items: repeated bulk prefetches of the same lines queue in
         // front of the tile copies)
@@ -460,7 +465,7 @@ __device__ __forceinline__ void q_producer(const QParams& prm, char* smem, uint6
   ptx::cp_async_wait<0>();
   if (failed) {
     // let every issued load land before the CTA's shared memory is released
-    for (int q = 0; q < kBufs; ++q)
+    for (int q = 0; q < kQBufs; ++q)
       if (inflight >> q & 1u) ptx::mbar_wait_bounded(bars + kQFull + 8 * q, (load_par >> q) & 1u, drain_bound(tmo));
     atomicExch(prm.a.status, int(SDFT_ERR_TIMEOUT));
   }
@@ -476,11 +481,11 @@ __global__ void __launch_bounds__(q_threads<R, W>(), ST ? 1 : 2) k_queue(const _
   const QArgs& a = prm.a;
   extern __shared__ char smem_raw[];
   char* smem = align1024(smem_raw);
-  const uint32_t bars = ptx::smem_addr(smem + kBufs * kTileBytes);
+  const uint32_t bars = ptx::smem_addr(smem + kQBufs * kTileBytes);
   const uint32_t tid = threadIdx.x;
   constexpr uint32_t NT = tile_threads<R, W>();
   {
-    const uint32_t used = uint32_t(smem - smem_raw) + kQTwOff + kBufs * q_tw_bytes<R, W, ST>();
+    const uint32_t used = uint32_t(smem - smem_raw) + kQTwOff + kQBufs * q_tw_bytes<R, W, ST>();
     int bad = 0;
     if (ptx::dynamic_smem_size() < used) bad = kBadSmem;
     else if (reinterpret_cast<uintptr_t>(&prm.maps[0]) & 63u) bad = kBadMap;
@@ -494,11 +499,11 @@ __global__ void __launch_bounds__(q_threads<R, W>(), ST ? 1 : 2) k_queue(const _
   const uint64_t n = (a.n_items > c) ? (a.n_items - c + G - 1) / G : 0;
   if (n == 0) return;
   if (tid == 0) {
-    for (int b = 0; b < kBufs; ++b) {
+    for (int b = 0; b < kQBufs; ++b) {
       ptx::mbar_init(bars + kQFull + 8 * b, 1);        // the producer's arrival (+ the tile's bytes)
       ptx::mbar_init(bars + kQEmpty + 8 * b, NT);      // every compute thread, once done with the buffer
     }
-    *reinterpret_cast<volatile int*>(smem + kBufs * kTileBytes + kQAbort) = 0;
+    *reinterpret_cast<volatile int*>(smem + kQBufs * kTileBytes + kQAbort) = 0;
     ptx::fence_mbar_init();
   }
   __syncthreads();
@@ -508,10 +513,10 @@ __global__ void __launch_bounds__(q_threads<R, W>(), ST ? 1 : 2) k_queue(const _
   }
   using C = typename KT<R>::C;
   constexpr int TB = KT<R>::TB;
-  const volatile int* abort_flag = reinterpret_cast<const volatile int*>(smem + kBufs * kTileBytes + kQAbort);
+  const volatile int* abort_flag = reinterpret_cast<const volatile int*>(smem + kQBufs * kTileBytes + kQAbort);
   for (uint64_t j = 0; j < n; ++j) {
-    const uint32_t b = uint32_t(j % kBufs);
-    const bool ok = ptx::mbar_wait_bounded(bars + kQFull + 8 * b, uint32_t((j / kBufs) & 1), a.timeout_ns);
+    const uint32_t b = uint32_t(j % kQBufs);
+    const bool ok = ptx::mbar_wait_bounded(bars + kQFull + 8 * b, uint32_t((j / kQBufs) & 1), a.timeout_ns);
     if (ptx::named_bar_or(1, NT, !ok || *abort_flag != 0)) {
       if (tid == 0 && !ok) atomicExch(a.status, int(SDFT_ERR_TIMEOUT));
       break;
@@ -539,8 +544,8 @@ __global__ void __launch_bounds__(q_threads<R, W>(), ST ? 1 : 2) k_queue(const _
     // the next item's register and L1 twiddles, if its tile has landed already
     // (staged tables need none)
     if (!ST && j + 1 < n) {
-      const uint32_t nb = uint32_t((j + 1) % kBufs);
-      if (ptx::mbar_test_wait(bars + kQFull + 8 * nb, uint32_t(((j + 1) / kBufs) & 1))) {
+      const uint32_t nb = uint32_t((j + 1) % kQBufs);
+      if (ptx::mbar_test_wait(bars + kQFull + 8 * nb, uint32_t(((j + 1) / kQBufs) & 1))) {
         const QItem& nx = q_meta(smem, j + 1);
         const int nv = nx.variant;
         const C* nt = static_cast<const C*>(nx.tw);

@@ -754,6 +754,23 @@ sdft_status sdft_sas_execute(sdft_sas sas, uint64_t batch, const void* d_samples
   return e == cudaSuccess ? SDFT_OK : cuda_fail(e);
 }
 
+sdft_status sdft_sas_path(sdft_sas sas, uint32_t* launches, uint64_t* work_values) {
+  using namespace sdft;
+  if (!sas) return SDFT_ERR_ARG;
+  const Sas& S = sas->s;
+  uint32_t l = 2;
+  uint64_t v = uint64_t(S.mu_star) << S.R;
+  if (!S.two_stage && sas_fused_shape(S)) {
+    l = 1;
+    v = 0;
+  } else if (!S.two_stage && sas_gather_shape(S)) {
+    v = S.k;
+  }
+  if (launches) *launches = l;
+  if (work_values) *work_values = v;
+  return SDFT_OK;
+}
+
 sdft_status sdft_sas_destroy(sdft_sas sas) {
   if (!sas) return SDFT_ERR_ARG;
   sdft::free_sas(sas->s);

@@ -152,16 +152,18 @@ def test_one_launch_and_two_launch_paths_agree_bitwise(kind, k, prec, batch):
 @pytest.mark.parametrize("kind,k,prec,batch", [("subset", 3000, "c64", 700), ("subset", 3000, "c64", 1),
                                                ("subset", 4000, "c64", 33), ("uoh", 3000, "c64", 301),
                                                ("uoh", 2000, "c64", 51), ("subset", 3000, "c128", 45),
-                                               ("subset", 2000, "c128", 19),
+                                               ("subset", 2000, "c128", 19), ("subset", 1000, "c128", 37),
+                                               ("subset", 1000, "c64", 99),
                                                ("ap", 2000, "c64", 301), ("ap", 1000, "c64", 7)])
 def test_tile_paths_agree_bitwise_with_the_two_launch_path(kind, k, prec, batch):
     """Where one to four virtual instances fill a tile (TB - 2 <= R <= TB):
-    with mu* > 1 (k <= 8192), stage 1 writes only the k values per instance
-    that the class solves read (in output order), and with mu* = 1 (k <= 2^TB)
-    both stages share one launch. Each gives the same bits as the two-launch path over the whole
-    stage-1 output, as the in-place call (samples buffer as workspace, which
-    takes the whole-output path), and matches the oracle on a few rows. The
-    batches leave the last tile part-filled where a tile holds several rows."""
+    with mu* = 1 (k <= 2^TB) both stages share one launch; with mu* > 1
+    (k <= 8192) stage 1 writes only the values the class solves read, k per
+    instance in output order, for the decoder launch. Each gives the same bits
+    as the two-launch path over the whole stage-1 output, as a second call, as
+    the in-place call (samples buffer as workspace, which takes the
+    whole-output path), and matches the oracle on a few rows. The batches leave
+    the last tile part-filled where a tile holds several rows."""
     torch = _torch()
     from paper_2211_15299_gb300 import Sas
     J = [int(j) for j in W.workload_sas(kind, k=k)]
@@ -169,7 +171,11 @@ def test_tile_paths_agree_bitwise_with_the_two_launch_path(kind, k, prec, batch)
     two = Sas(20, J, prec, two_stage=True)
     tb = 12 if prec == "c64" else 11
     assert tb - 2 <= one.R <= tb
-    assert (one.gathered, one.launches) == ((True, 2) if one.mu_star > 1 else (False, 1))
+    if one.mu_star == 1:
+        assert (one.launches, one.work_values) == (1, 0)
+    else:
+        assert (one.launches, one.work_values, one.gathered) == (2, one.k, True)
+    assert (two.launches, two.work_values) == (2, one.mu_star << one.R)
     dt = torch.complex64 if prec == "c64" else torch.complex128
     g = torch.Generator(device="cuda")
     g.manual_seed(78)
