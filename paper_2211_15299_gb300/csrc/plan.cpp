@@ -201,11 +201,16 @@ sdft_status build_plan(uint32_t M, const uint64_t* J, uint64_t k, sdft_prec prec
   for (uint32_t q = 0; q < s; ++q) ibits[q] = M - 1 - p.pivots[q];
 
   // Pivoted sampling pattern (Definition "r_sampling_pattern"), sample order t:
-  // I[t] = sum_q bit_q(t) 2^(M-1-r_{q+1}).
-  BitGather index_of;
-  index_of.build(qbits.data(), ibits.data(), s, s);
+  // I[t] = sum_q bit_q(t) 2^(M-1-r_{q+1}), built by doubling: the indices with
+  // key bit q set are those below 2^q with that bit added.
   p.I.resize(k);
-  for (uint64_t t = 0; t < k; ++t) p.I[t] = index_of(t);
+  p.I[0] = 0;
+  for (uint32_t q = 0; q < s; ++q) {
+    const uint64_t half = 1ull << q, bit = 1ull << ibits[q];
+    uint64_t* out = p.I.data() + half;
+    const uint64_t* in = p.I.data();
+    for (uint64_t t = 0; t < half; ++t) out[t] = in[t] | bit;
+  }
 
   // Level schedule.
   p.levels.clear();
