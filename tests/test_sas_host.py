@@ -109,3 +109,29 @@ def test_random_subset_at_the_theorems_pivot_count():
         assert p.mu_star < (4 + 3 * np.log(2)) * log2k
         auto = Sas(18, [int(j) for j in J], prec, host_only=True)
         assert auto.max_cond <= (32.0 if prec == "c64" else 100.0)
+
+
+@pytest.mark.parametrize("kind,k,prec", [("ap", 3000, "c64"), ("ap", 1000, "c64"), ("subset", 3000, "c64"),
+                                         ("uoh", 2000, "c64"), ("subset", 3000, "c128"), ("ap", 3000, "c128"),
+                                         ("subset", 600, "c64")])
+def test_execution_path_follows_the_tile_shapes(kind, k, prec):
+    """sdft_sas_path: one launch and no workspace under complete isolation with
+    one to four virtual instances per tile (R in [TB - 2, TB], k <= 2^TB); two
+    launches with only the k gathered values per instance in the workspace for
+    mu* > 1 on those shapes (k <= 8192); the whole mu* x 2^R stage-1 output
+    otherwise and always under SDFT_SAS_TWO_STAGE."""
+    from paper_2211_15299_gb300 import Sas
+    J = [int(j) for j in W.workload_sas(kind, k=k)]
+    p = Sas(20, J, prec, host_only=True)
+    two = Sas(20, J, prec, host_only=True, two_stage=True)
+    tb = 12 if prec == "c64" else 11
+    tile = tb - 2 <= p.R <= tb
+    whole = p.mu_star << p.R
+    if tile and p.mu_star == 1 and p.k <= (1 << tb):
+        want = (1, 0)
+    elif tile and 1 < p.mu_star <= 64 and p.k <= 8192:
+        want = (2, p.k)
+    else:
+        want = (2, whole)
+    assert (p.launches, p.work_values) == want, (p.R, p.mu_star, p.k)
+    assert (two.launches, two.work_values) == (2, whole)
