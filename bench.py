@@ -574,6 +574,7 @@ def run_uneven(args):
     from paper_2211_15299_gb300 import _native as N
     spp_tuned = N.sdft_batch_get_stages_per_pass(b.handle)
     staged_tuned = N.sdft_batch_get_table_staging(b.handle)
+    lag_tuned = N.sdft_batch_get_lag(b.handle)
 
     def step(s=None):
         b.execute(x, y, stream=(s or stream).cuda_stream)
@@ -606,7 +607,8 @@ def run_uneven(args):
             "alg_bytes_per_step": 16 * total + tw_bytes, "work_items": n_items,
             "dependency_counters": n_ctr, "grid": grid, "plan_build_s": t_plan,
             "autotune": {"schedule": schedule, "grid": grid, "stages_per_pass": spp_tuned,
-                         "table_staging": staged_tuned, "ms_per_run": ms_tuned, "seconds": t_tune},
+                         "table_staging": staged_tuned, "lag": lag_tuned, "ms_per_run": ms_tuned,
+                         "seconds": t_tune},
             "launches_per_step": 1, "graph": "one CUDA graph replay per step"}
 
 

@@ -399,6 +399,17 @@ sdft_status sdft_batch_get_stages_per_pass(sdft_batch batch, uint32_t* stages_pe
 sdft_status sdft_batch_set_table_staging(sdft_batch batch, int staged);
 sdft_status sdft_batch_get_table_staging(sdft_batch batch, int* staged);
 
+/* Dependency distance of the batch's item list (an implementation setting of
+ * the work queue, not part of the paper's method): an item of a later level of
+ * an instance is placed at least `lag` x grid list places after the last item
+ * of the level before it (4 <= lag <= 64; default 6). 4 is the least for
+ * which every dependency wait of the persistent launch ends; a larger lag
+ * means fewer waits but an intermediate that stays longer in L2. Rebuilds the
+ * item list as for sdft_batch_set_stages_per_pass; sdft_batch_autotune chooses
+ * it (4, 6 or 8) with the other settings. Errors: SDFT_ERR_ARG. */
+sdft_status sdft_batch_set_lag(sdft_batch batch, uint32_t lag);
+sdft_status sdft_batch_get_lag(sdft_batch batch, uint32_t* lag);
+
 /* Apply the tuning cache's choice for this batch (key: precision,
  * floor(log2 n), floor(log2 total values)) without timing; *found as for
  * sdft_plan_apply_tuning. Rebuilds the item list when the choice differs. */
@@ -435,8 +446,9 @@ sdft_status sdft_batch_set_schedule(sdft_batch batch, sdft_schedule schedule, ui
 /*
  * sdft_batch_autotune - time the batch under every queue shape (lanes or round
  * robin, on all co-resident CTAs or on half of them), stages-per-pass choice
- * (4, and 3 for complex64) and table placement (sdft_batch_set_table_staging;
- * both for complex64); one warm-up and `reps` timed runs each,
+ * (4, and 3 for complex64), table placement (sdft_batch_set_table_staging;
+ * both for complex64) and dependency distance (sdft_batch_set_lag: 4, 6 or
+ * 8); one warm-up and `reps` timed runs each,
  * CUDA events on `stream`, the buffers overwritten. Keeps the fastest, reports
  * it (any output may be NULL; `ms_best` is the mean time of one run; the
  * stages per pass: sdft_batch_get_stages_per_pass) and stores it in the

@@ -75,6 +75,8 @@ SIGNATURES = {
     "sdft_batch_set_table_staging": (c_int, [c_vp, c_int]),
     "sdft_server_inject": (c_int, [c_vp, c_u32, c_u64, c_u64]),
     "sdft_batch_get_table_staging": (c_int, [c_vp, ctypes.POINTER(c_int)]),
+    "sdft_batch_set_lag": (c_int, [c_vp, c_u32]),
+    "sdft_batch_get_lag": (c_int, [c_vp, P_u32]),
     "sdft_autotune_cache_save": (c_int, [ctypes.c_char_p]),
     "sdft_autotune_cache_load": (c_int, [ctypes.c_char_p]),
     "sdft_autotune_cache_clear": (c_int, []),
@@ -284,6 +286,16 @@ def sdft_batch_get_table_staging(batch: int) -> bool:
     v = c_int(0)
     _check(_lib.sdft_batch_get_table_staging(batch, ctypes.byref(v)), "sdft_batch_get_table_staging")
     return bool(v.value)
+
+
+def sdft_batch_set_lag(batch: int, lag: int) -> None:
+    _check(_lib.sdft_batch_set_lag(batch, int(lag)), "sdft_batch_set_lag")
+
+
+def sdft_batch_get_lag(batch: int) -> int:
+    v = c_u32(0)
+    _check(_lib.sdft_batch_get_lag(batch, ctypes.byref(v)), "sdft_batch_get_lag")
+    return int(v.value)
 
 
 def sdft_batch_apply_tuning(batch: int) -> bool:

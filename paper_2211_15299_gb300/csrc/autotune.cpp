@@ -7,7 +7,7 @@
 // without timing; sdft_autotune_cache_save / _load keep the cache in a JSON
 // file between processes:
 //   {"plan/c64/s20/b6": {"strategy": 1, "schedule": 0, "grid": 0, "stages_per_pass": 4,
-//                        "table_staging": 0, "ms": 0.35}, ...}
+//                        "table_staging": 0, "lag": 6, "ms": 0.35}, ...}
 #include <cctype>
 #include <cstdio>
 #include <cstdlib>
@@ -106,8 +106,8 @@ sdft_status sdft_autotune_cache_save(const char* path) {
       char buf[256];
       std::snprintf(buf, sizeof(buf),
                     "%s \"%s\": {\"strategy\": %d, \"schedule\": %d, \"grid\": %d, \"stages_per_pass\": %d, "
-                    "\"table_staging\": %d, \"ms\": %.6g}",
-                    first ? "" : ",\n", kv.first.c_str(), t.strategy, t.schedule, t.grid, t.spp, t.staged,
+                    "\"table_staging\": %d, \"lag\": %d, \"ms\": %.6g}",
+                    first ? "" : ",\n", kv.first.c_str(), t.strategy, t.schedule, t.grid, t.spp, t.staged, t.lag,
                     double(t.ms));
       out += buf;
       first = false;
@@ -147,6 +147,7 @@ sdft_status sdft_autotune_cache_load(const char* path) {
           else if (field == "grid") t.grid = int(v);
           else if (field == "stages_per_pass") t.spp = int(v);
           else if (field == "table_staging") t.staged = int(v);
+          else if (field == "lag") t.lag = int(v);
           else if (field == "ms") t.ms = float(v);
           else return SDFT_ERR_ARG;
         } while (r.lit(','));

@@ -37,6 +37,14 @@ struct BatchMap {
 // Grid size assumed when a batch is built from host-only plans (2 CTAs x 152 SMs).
 constexpr int kHostOnlyGrid = 304;
 
+// Distance, in list places per CTA, at which a dependent item follows the
+// last item it waits on: at least 4 (the queue kernel's publication order,
+// check_items); 6 by default, the fastest of 4, 6, 8 and 12 on the
+// 10,000-instance uneven batch (0.4531, 0.4409, 0.4474 and 0.4641 ms): later
+// items find their counters already published, and the intermediates they
+// read are still in L2.
+constexpr int kMinLag = 4, kDefaultLag = 6, kMaxLag = 64;
+
 struct Batch {
   int device = -1;
   sdft_prec prec = SDFT_C64;
@@ -59,6 +67,7 @@ struct Batch {
   uint32_t* noalloc_counters = nullptr;  // device address of the library's fixed counter array
   int spp = 4;                       // stages per pass of the queue kernel (3 or 4; 3: complex64 only)
   bool staged = false;               // whole twiddle tables in shared memory (complex64 only)
+  int lag = kDefaultLag;             // a dependent item sits at least lag x grid list places after its producers
 };
 
 }  // namespace sdft
@@ -285,7 +294,8 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
 
   // Phase 2: order the items. Every dependency must sit at least 4 x grid list
   // positions behind the item that waits on it (CTA c takes positions c, c + G,
-  // ...; a CTA issues item j's load after publishing item j - 4's store).
+  // ...; a CTA issues item j's load after publishing item j - 4's store); the
+  // orders place it lag x grid positions behind (lag >= 4).
   QItem nop{};
   nop.variant = uint16_t(kVNop);
   nop.dep = kNone;
@@ -304,7 +314,7 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
   if (use_lanes) {
     // Lanes: a unit runs entirely in one CTA (its tables stay in registers and
     // L1, its intermediate in L2); units go to the least-loaded lane, largest
-    // first, and a unit's next stage starts 4 lane positions after its last item.
+    // first, and a unit's next stage starts lag lane positions after its last item.
     std::vector<size_t> by_cost(units.size());
     for (size_t u = 0; u < units.size(); ++u) by_cost[u] = u;
     std::stable_sort(by_cost.begin(), by_cost.end(),
@@ -335,12 +345,12 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
           const auto& st = units[pd.unit].stages[pd.stage];
           for (const QItem& x : st) lane.push_back(x);
           if (pd.stage + 1 < units[pd.unit].stages.size())
-            pend.push_back(Pending{lane.size() + 3, pd.unit, pd.stage + 1});
+            pend.push_back(Pending{lane.size() + uint64_t(B.lag) - 1, pd.unit, pd.stage + 1});
         }
       };
       for (size_t u : lane_units[l]) {
         for (const QItem& it : units[u].stages[0]) put(it);
-        if (units[u].stages.size() > 1) pend.push_back(Pending{lane.size() + 3, u, 1});
+        if (units[u].stages.size() > 1) pend.push_back(Pending{lane.size() + uint64_t(B.lag) - 1, u, 1});
       }
       while (!pend.empty()) put(nop);
       longest = std::max(longest, lane.size());
@@ -350,9 +360,9 @@ static sdft_status build_batch(Batch& B, const sdft_plan* plans, uint64_t n) {
       for (size_t idx = 0; idx < lanes[l].size(); ++idx) items[idx * G + l] = lanes[l][idx];
     while (!items.empty() && items.back().variant == kVNop) items.pop_back();
   } else {
-    // Round robin in unit order: a unit's next stage is held back until 4 x grid
-    // more items exist (consecutive items go to consecutive CTAs).
-    const uint64_t lag = 4ull * G;
+    // Round robin in unit order: a unit's next stage is held back until lag x
+    // grid more items exist (consecutive items go to consecutive CTAs).
+    const uint64_t lag = uint64_t(B.lag) * G;
     std::deque<Pending> pend;
     std::function<void(const QItem&)> put = [&](const QItem& it) {
       items.push_back(it);
@@ -953,13 +963,15 @@ static sdft_status rebuild_batch(sdft::Batch& B) {
 
 // Item order, CTAs and stages per pass together (one rebuild; the grid and so
 // the item list depend on the kernel's occupancy).
-static sdft_status set_config(sdft::Batch& B, int schedule, int grid, int spp, bool staged) {
-  if (B.schedule == schedule && B.grid_req == grid && B.spp == spp && B.staged == staged && B.d_items)
+static sdft_status set_config(sdft::Batch& B, int schedule, int grid, int spp, bool staged, int lag) {
+  if (B.schedule == schedule && B.grid_req == grid && B.spp == spp && B.staged == staged && B.lag == lag &&
+      B.d_items)
     return SDFT_OK;
   B.schedule = schedule;
   B.grid_req = grid;
   B.spp = spp;
   B.staged = staged;
+  B.lag = lag;
   return rebuild_batch(B);
 }
 
@@ -969,7 +981,7 @@ sdft_status sdft_batch_set_schedule(sdft_batch batch, sdft_schedule schedule, ui
     return SDFT_ERR_ARG;
   if (grid > (1u << 20)) return SDFT_ERR_ARG;
   sdft::Batch& B = batch->b;
-  return set_config(B, int(schedule), int(grid), B.spp, B.staged);
+  return set_config(B, int(schedule), int(grid), B.spp, B.staged, B.lag);
 }
 
 sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d_coeffs, void* stream, int reps,
@@ -981,11 +993,12 @@ sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d
   struct Cand {
     int schedule, grid, spp;
     bool staged;
+    int lag;
   };
   // Stages per pass (four; three as well for complex64) x tables in registers
   // and L1 or staged whole in shared memory (complex64) x item order x CTAs:
   // every co-resident CTA, or half of them (fewer intermediates in flight,
-  // more L1 per resident CTA).
+  // more L1 per resident CTA) x dependency distance (4, 6 or 8 x grid).
   std::vector<Cand> cands;
   for (int spp : {4, 3})
     for (bool staged : {false, true}) {
@@ -993,7 +1006,8 @@ sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d
       const int full = B.prec == SDFT_C64 ? sdft::queue_grid_f32(spp, staged) : sdft::queue_grid_f64(spp, staged);
       if (full <= 0) return SDFT_ERR_CUDA;
       for (int sched : {int(SDFT_SCHEDULE_LANES), int(SDFT_SCHEDULE_ROUND_ROBIN)})
-        for (int g : {0, full / 2}) cands.push_back(Cand{sched, g, spp, staged});
+        for (int g : {0, full / 2})
+          for (int lag : {sdft::kDefaultLag, 4, 8}) cands.push_back(Cand{sched, g, spp, staged, lag});
     }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
@@ -1006,7 +1020,7 @@ sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d
   float best = -1.f;
   Cand pick = cands[0];
   for (const Cand& c : cands) {
-    s = set_config(B, c.schedule, c.grid, c.spp, c.staged);
+    s = set_config(B, c.schedule, c.grid, c.spp, c.staged, c.lag);
     if (s != SDFT_OK) break;
     s = sdft::run_batch(B, d_samples, d_coeffs, st);     // warm-up
     if (s != SDFT_OK) break;
@@ -1027,10 +1041,11 @@ sdft_status sdft_batch_autotune(sdft_batch batch, const void* d_samples, void* d
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != SDFT_OK) return s;
-  s = set_config(B, pick.schedule, pick.grid, pick.spp, pick.staged);
+  s = set_config(B, pick.schedule, pick.grid, pick.spp, pick.staged, pick.lag);
   if (s != SDFT_OK) return s;
-  sdft::tuning_store(sdft::batch_tuning_key(B.prec, B.n, B.total),
-                     sdft::Tuning{0, pick.schedule, pick.grid, pick.spp, best, pick.staged ? 1 : 0});
+  sdft::Tuning tn{0, pick.schedule, pick.grid, pick.spp, best, pick.staged ? 1 : 0};
+  tn.lag = pick.lag;
+  sdft::tuning_store(sdft::batch_tuning_key(B.prec, B.n, B.total), tn);
   if (chosen) *chosen = sdft_schedule(pick.schedule);
   if (chosen_grid) *chosen_grid = uint32_t(B.grid);
   if (ms_best) *ms_best = best;
@@ -1041,14 +1056,26 @@ sdft_status sdft_batch_set_stages_per_pass(sdft_batch batch, uint32_t stages_per
   if (!batch) return SDFT_ERR_ARG;
   sdft::Batch& B = batch->b;
   if (stages_per_pass != 4 && !(stages_per_pass == 3 && B.prec == SDFT_C64)) return SDFT_ERR_ARG;
-  return set_config(B, B.schedule, B.grid_req, int(stages_per_pass), B.staged);
+  return set_config(B, B.schedule, B.grid_req, int(stages_per_pass), B.staged, B.lag);
 }
 
 sdft_status sdft_batch_set_table_staging(sdft_batch batch, int staged) {
   if (!batch) return SDFT_ERR_ARG;
   sdft::Batch& B = batch->b;
   if (staged && B.prec != SDFT_C64) return SDFT_ERR_ARG;
-  return set_config(B, B.schedule, B.grid_req, B.spp, staged != 0);
+  return set_config(B, B.schedule, B.grid_req, B.spp, staged != 0, B.lag);
+}
+
+sdft_status sdft_batch_set_lag(sdft_batch batch, uint32_t lag) {
+  if (!batch || lag < uint32_t(sdft::kMinLag) || lag > uint32_t(sdft::kMaxLag)) return SDFT_ERR_ARG;
+  sdft::Batch& B = batch->b;
+  return set_config(B, B.schedule, B.grid_req, B.spp, B.staged, int(lag));
+}
+
+sdft_status sdft_batch_get_lag(sdft_batch batch, uint32_t* lag) {
+  if (!batch || !lag) return SDFT_ERR_ARG;
+  *lag = uint32_t(batch->b.lag);
+  return SDFT_OK;
 }
 
 sdft_status sdft_batch_get_table_staging(sdft_batch batch, int* staged) {
@@ -1075,7 +1102,8 @@ sdft_status sdft_batch_apply_tuning(sdft_batch batch, int* found) {
   if (t.schedule != SDFT_SCHEDULE_AUTO && t.schedule != SDFT_SCHEDULE_LANES && t.schedule != SDFT_SCHEDULE_ROUND_ROBIN)
     return SDFT_ERR_ARG;
   if (t.grid < 0 || t.grid > (1 << 20)) return SDFT_ERR_ARG;
-  return set_config(B, t.schedule, t.grid, t.spp, t.staged != 0);
+  if (t.lag < sdft::kMinLag || t.lag > sdft::kMaxLag) return SDFT_ERR_ARG;
+  return set_config(B, t.schedule, t.grid, t.spp, t.staged != 0, t.lag);
 }
 
 sdft_status sdft_batch_destroy(sdft_batch batch) {

@@ -61,6 +61,7 @@ struct Tuning {
   int spp = 4;
   float ms = 0.f;
   int staged = 0;    // uneven batches: whole twiddle tables in shared memory
+  int lag = 6;       // uneven batches: dependency distance (x grid list places)
 };
 std::string plan_tuning_key(sdft_prec prec, uint32_t s, uint64_t batch);
 std::string batch_tuning_key(sdft_prec prec, uint64_t n, uint64_t total);

@@ -86,3 +86,26 @@ def test_unknown_schedule_rejected():
     with pytest.raises(SdftError) as ei:
         N.sdft_batch_set_schedule(b.handle, 7, 0)
     assert ei.value.name == "SDFT_ERR_ARG"
+
+
+@pytest.mark.parametrize("schedule", ["lanes", "round_robin"])
+def test_dependency_distance(schedule):
+    # a later level follows its producers by lag x grid list places (default 6,
+    # at least 4): every choice keeps the ordering invariants, and a longer lag
+    # only adds places (padding) to the list
+    from paper_2211_15299_gb300 import Batch, SdftError, _native as N
+    b = Batch(_plans(W.workload_uneven(count=600, salt=13)))
+    assert N.sdft_batch_get_lag(b.handle) == 6
+    b.set_schedule(schedule)
+    counts = []
+    for lag in (4, 6, 8, 12):
+        N.sdft_batch_set_lag(b.handle, lag)
+        assert N.sdft_batch_get_lag(b.handle) == lag
+        n_items, n_ctr, grid = b.stats()       # raises if a dependency is closer than 4 x grid
+        counts.append(n_items)
+    assert counts == sorted(counts)
+    for bad in (0, 3, 65):
+        with pytest.raises(SdftError) as ei:
+            N.sdft_batch_set_lag(b.handle, bad)
+        assert ei.value.name == "SDFT_ERR_ARG"
+    assert N.sdft_batch_get_lag(b.handle) == 12

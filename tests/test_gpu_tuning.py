@@ -47,7 +47,7 @@ def test_stages_per_pass_bit_identical(M, s, batch):
 
 def test_batch_queue_variants_bit_identical():
     # three or four stages per pass x tables in registers / staged whole in
-    # shared memory: four kernels, one result
+    # shared memory: four kernels, one result; also every dependency distance
     torch = _torch()
     from paper_2211_15299_gb300 import Batch, Plan, _native as N
     insts = W.workload_uneven(count=300, salt=11)
@@ -61,6 +61,12 @@ def test_batch_queue_variants_bit_identical():
             assert N.sdft_batch_get_stages_per_pass(b.handle) == spp
             assert N.sdft_batch_get_table_staging(b.handle) == staged
             outs[(spp, staged)] = b.execute(x)
+    # the dependency distance reorders the items and changes no bits either
+    N.sdft_batch_set_stages_per_pass(b.handle, 4)
+    N.sdft_batch_set_table_staging(b.handle, False)
+    for lag in (4, 8, 12):
+        N.sdft_batch_set_lag(b.handle, lag)
+        outs[("lag", lag)] = b.execute(x)
     torch.cuda.synchronize()
     assert b.device_status() == 0
     for key, y in outs.items():

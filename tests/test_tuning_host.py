@@ -29,7 +29,8 @@ def test_cache_file_round_trip(tmp_path):
     from paper_2211_15299_gb300 import _native as N
     src = {"plan/c64/s12/b12": {"strategy": 1, "schedule": 0, "grid": 0, "stages_per_pass": 3, "ms": 0.05},
            "plan/c128/s20/b6": {"strategy": 2, "schedule": 0, "grid": 0, "stages_per_pass": 4, "ms": 1.5},
-           "batch/c64/n13/t26": {"strategy": 0, "schedule": 2, "grid": 152, "stages_per_pass": 4, "ms": 0.46}}
+           "batch/c64/n13/t26": {"strategy": 0, "schedule": 2, "grid": 152, "stages_per_pass": 4, "lag": 8,
+                                 "ms": 0.46}}
     f = tmp_path / "tune.json"
     f.write_text(json.dumps(src))
     N.sdft_autotune_cache_load(str(f))
@@ -122,11 +123,29 @@ def test_batch_choice_applied_and_item_list_rebuilt(tmp_path):
     t_bits = int(np.floor(np.log2(b.total)))
     key = f"batch/c64/n{n_bits}/t{t_bits}"
     f = tmp_path / "tune.json"
-    f.write_text(json.dumps({key: {"schedule": 1, "grid": 100, "stages_per_pass": 3, "table_staging": 1}}))
+    f.write_text(json.dumps({key: {"schedule": 1, "grid": 100, "stages_per_pass": 3, "table_staging": 1,
+                                   "lag": 5}}))
     assert not N.sdft_batch_apply_tuning(b.handle)
     N.sdft_autotune_cache_load(str(f))
     assert N.sdft_batch_apply_tuning(b.handle)
     assert N.sdft_batch_get_stages_per_pass(b.handle) == 3
     assert N.sdft_batch_get_table_staging(b.handle)
+    assert N.sdft_batch_get_lag(b.handle) == 5
     items, counters, grid = b.stats()
     assert grid == 100 and items > 0
+
+
+def test_cached_dependency_distance_below_the_minimum_is_rejected(tmp_path):
+    # a lag under 4 would let a persistent launch wait on a counter that is
+    # never published in time: the cache entry is refused, the batch unchanged
+    from paper_2211_15299_gb300 import Batch, Plan, SdftError, _native as N
+    insts = W.workload_uneven(count=200, salt=5)
+    b = Batch([Plan(i.M, i.J, "c64", host_only=True) for i in insts])
+    key = f"batch/c64/n{int(np.floor(np.log2(len(insts))))}/t{int(np.floor(np.log2(b.total)))}"
+    f = tmp_path / "tune.json"
+    f.write_text(json.dumps({key: {"schedule": 1, "grid": 100, "stages_per_pass": 4, "lag": 3}}))
+    N.sdft_autotune_cache_load(str(f))
+    with pytest.raises(SdftError) as ei:
+        N.sdft_batch_apply_tuning(b.handle)
+    assert ei.value.name == "SDFT_ERR_ARG"
+    assert N.sdft_batch_get_lag(b.handle) == 6
