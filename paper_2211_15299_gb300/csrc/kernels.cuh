@@ -928,7 +928,8 @@ __global__ void __launch_bounds__(tile_threads<R, W>(), 2)
     level_coords_in_bounds(args, c1, c3);
     advance(load_cur);
     ptx::mbar_arrive_expect_tx(bar, kTileBytes);
-    ptx::tma_load_4d(ptx::smem_addr(smem + b * kTileBytes), &src, bar, 0, c1, 0, c3);
+    // every tile is read once: first out of L2
+    ptx::tma_load_4d_hint(ptx::smem_addr(smem + b * kTileBytes), &src, bar, 0, c1, 0, c3, ptx::policy_evict_first());
   };
 
   if (tid == 0) {
@@ -990,7 +991,11 @@ __global__ void __launch_bounds__(tile_threads<R, W>(), 2)
       int c1, c3;
       coords(cur, c1, c3);
       level_coords_in_bounds(args, c1, c3);
-      ptx::tma_store_4d(&dst, ptx::smem_addr(buf), 0, c1, 0, c3);
+      // the final output leaves L2 first; an intermediate stays for the next level
+      if constexpr (LAST)
+        ptx::tma_store_4d_hint(&dst, ptx::smem_addr(buf), 0, c1, 0, c3, ptx::policy_evict_first());
+      else
+        ptx::tma_store_4d(&dst, ptx::smem_addr(buf), 0, c1, 0, c3);
       ptx::bulk_commit();
     }
   }
