@@ -238,6 +238,10 @@ def run_ours(args):
                 "frac_of_nominal_7900": round(achieved / 7900.0, 4),
                 "ms_per_step_after_l2_write_flush": 1e3 * statistics.mean(flushed)}
 
+    # context for the ridge point: the FP32 CUDA-core rate, an 8192^3 FP32 matrix
+    # product with TF32 off (a cuBLAS library call on the FMA pipes, no tensor cores)
+    roofline["fp32_fma_peak"] = _fp32_fma_peak(dev, stream, peak)
+
     if args.only_fp32:
         if rank == 0:
             print(json.dumps({"value": value, "unit": UNIT, "ms_per_step": ms_per_step, "roofline": roofline,
@@ -385,6 +389,37 @@ def _committed_traffic(M, s, batch):
     except Exception:
         pass
     return None
+
+
+def _fp32_fma_peak(dev, stream, hbm_gbs):
+    """Measured FP32 CUDA-core throughput (TFLOP/s) of a square FP32 matrix product
+    with TF32 disabled, and the ridge point it gives against the HBM peak."""
+    import torch
+    n = 8192
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        g = torch.Generator(device=dev)
+        g.manual_seed(W.BASE_SEED + 9)
+        a = torch.randn((n, n), dtype=torch.float32, device=dev, generator=g)
+        b = torch.randn((n, n), dtype=torch.float32, device=dev, generator=g)
+        c = torch.empty_like(a)
+        for _ in range(2):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3 / reps
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    tflops = 2.0 * n ** 3 / sec / 1e12
+    return {"tflops": tflops, "how": f"torch.matmul float32 {n}^3, TF32 off (cuBLAS), mean of {reps}",
+            "ridge_flop_per_byte": tflops * 1e12 / (hbm_gbs * 1e9)}
 
 
 def _capture(fn):
