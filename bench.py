@@ -349,6 +349,7 @@ def run_ours(args):
         "gpu_launches": int(args.steps * n_levels),
         "roofline": roofline,
         "fp64": {"batched_coeffs_per_s": fp64_batched, "per_instance_coeffs_per_s": fp64_per_instance,
+                 "fp64_fma_peak": _fp32_fma_peak(dev, stream, peak, torch.float64, 4096),
                  "per_instance_sample": n_pi, "fp32_speedup_vs_per_instance": value / ws / fp64_per_instance,
                  "batched_double_float_coeffs_per_s": fp64_df, "rel_l2_double_float_vs_fp64": rel_df_vs_fp64},
         "rel_l2_fp32_vs_fp64": rel_fp32_vs_fp64,
@@ -391,18 +392,19 @@ def _committed_traffic(M, s, batch):
     return None
 
 
-def _fp32_fma_peak(dev, stream, hbm_gbs):
-    """Measured FP32 CUDA-core throughput (TFLOP/s) of a square FP32 matrix product
-    with TF32 disabled, and the ridge point it gives against the HBM peak."""
+def _fp32_fma_peak(dev, stream, hbm_gbs, dtype=None, n=8192):
+    """Measured CUDA-core throughput (TFLOP/s) of a square matrix product in
+    `dtype` (FP32 by default, TF32 disabled; FP64 for the complex128 path), and
+    the ridge point it gives against the HBM peak."""
     import torch
-    n = 8192
+    dtype = dtype or torch.float32
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
         g = torch.Generator(device=dev)
         g.manual_seed(W.BASE_SEED + 9)
-        a = torch.randn((n, n), dtype=torch.float32, device=dev, generator=g)
-        b = torch.randn((n, n), dtype=torch.float32, device=dev, generator=g)
+        a = torch.randn((n, n), dtype=dtype, device=dev, generator=g)
+        b = torch.randn((n, n), dtype=dtype, device=dev, generator=g)
         c = torch.empty_like(a)
         for _ in range(2):
             torch.matmul(a, b, out=c)
@@ -418,7 +420,8 @@ def _fp32_fma_peak(dev, stream, hbm_gbs):
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
     tflops = 2.0 * n ** 3 / sec / 1e12
-    return {"tflops": tflops, "how": f"torch.matmul float32 {n}^3, TF32 off (cuBLAS), mean of {reps}",
+    name = str(dtype).replace("torch.", "")
+    return {"tflops": tflops, "how": f"torch.matmul {name} {n}^3, TF32 off (cuBLAS), mean of {reps}",
             "ridge_flop_per_byte": tflops * 1e12 / (hbm_gbs * 1e9)}
 
 
