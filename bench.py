@@ -738,19 +738,22 @@ def run_serving(args):
     res_out = [torch.empty(p.k, dtype=torch.complex64).pin_memory() for p in resident]
     pool = {}                                  # s -> list of free (in, out) pinned pairs
     pool_mu = th.Lock()
+    late_allocs = [0]                          # pinned pairs allocated during the arrivals
 
     def take(s):
         with pool_mu:
             lst = pool.setdefault(s, [])
             if lst:
                 return lst.pop()
+            late_allocs[0] += 1
         return pinned(1 << s), torch.empty(1 << s, dtype=torch.complex64).pin_memory()
 
-    # pinned buffers for fresh requests, allocated before the arrivals start
-    # (a pinned allocation takes milliseconds and would stall the client)
+    # pinned buffers for fresh requests, allocated before the arrivals start (a
+    # pinned allocation takes milliseconds and would stall the client): enough
+    # per size for the most requests the engine holds in flight at this load
     for s_ in sorted(set(int(trace.plans[int(p)].s) for p in trace.plan_ids if p >= 256)):
         pool[s_] = [(pinned(1 << s_), torch.empty(1 << s_, dtype=torch.complex64).pin_memory())
-                    for _ in range(8)]
+                    for _ in range(32)]
     # fresh supports are planned by the engine's own planner threads (deferred
     # plans: tables built on the host, uploaded into the arena with the request)
     srv = Server("c64", budget_bytes=args.serve_budget << 20, n_slots=2, max_batch=args.serve_batch,
@@ -845,7 +848,8 @@ def run_serving(args):
            "planner_threads": args.serve_planners,
            "micro_batches": st["micro_batches"], "max_inflight": st["max_inflight"],
            "arena_peak_MiB": st["arena_peak_bytes"] / 2**20, "budget_MiB": args.serve_budget,
-           "resident_plan_build_s": t_resident, "device_status": srv.device_status()}
+           "resident_plan_build_s": t_resident, "device_status": srv.device_status(),
+           "client_pinned_allocs_during_run": late_allocs[0]}
     srv.close()
     return out
 
