@@ -406,7 +406,10 @@ void worker_loop(Server* S) {
   std::unique_lock<std::mutex> lk(S->mu);
   while (true) {
     bool progressed = false;
-    // Reap finished slots.
+    // Reap finished slots. Finished fresh plans are destroyed after the lock is
+    // released (freeing their host tables takes time the submitters should not
+    // wait for).
+    std::vector<sdft_plan> finished;
     for (Slot* sl : S->slots) {
       if (!sl->busy || !sl->done.load(std::memory_order_acquire)) continue;
       for (const Req& r : sl->reqs) {
@@ -416,12 +419,17 @@ void worker_loop(Server* S) {
         S->done.push_back(Done{r.tag, lat, int32_t(SDFT_OK)});
         ++S->stats.completed;
         S->stats.coeffs += r.plan->k;
-        if (r.own_plan) sdft_plan_destroy(r.own_plan);   // host tables only: no device work
+        if (r.own_plan) finished.push_back(r.own_plan);   // host tables only: no device work
       }
       S->stats.inflight -= sl->reqs.size();
       sl->reqs.clear();
       sl->busy = false;
       progressed = true;
+    }
+    if (!finished.empty()) {
+      lk.unlock();
+      for (sdft_plan h : finished) sdft_plan_destroy(h);
+      lk.lock();
     }
     if (S->stop && S->waiting.empty() && S->planning == 0) {
       bool idle = true;
