@@ -103,3 +103,16 @@ def test_cpu_baseline_leg():
     assert d["rel_l2_gpu_fp32_vs_oracle"] < 1e-6
     assert d["dense_solve"]["rel_l2_gpu_fp32_vs_oracle"] < 1e-6
     assert d["alg1_numpy"]["rel_l2_gpu_fp32_vs_oracle"] < 1e-6
+
+
+@pytest.mark.parametrize("per_set", [1, 58 << 20, 92 << 20, 225 << 20, 268 << 20, 1 << 30, 3 << 30])
+def test_rotating_sets_keep_inputs_out_of_l2(per_set):
+    # the steady-state timing rotates over enough buffer sets that at least
+    # 1 GiB (several L2 capacities) passes between two uses of one set; a set
+    # of 1 GiB or more is used alone
+    n = bench.steady_sets(per_set)
+    assert 1 <= n <= 32
+    if per_set >= 1 << 30:
+        assert n == 1
+    else:
+        assert (n - 1) * per_set >= 1 << 30 or n == 32
