@@ -349,11 +349,11 @@ __global__ void __launch_bounds__(256) k_sas_decode(const typename KT<R>::C* __r
 // stage-1 output never leaves the SM; the product is formed as in k_sas_decode,
 // so both paths give the same bits. (With mu* > 1 the class solves need mu*
 // tiles per instance and their inverse rows: they stay a launch of their own.)
-// GATHER (mu* > 1, the same tile shape): the kernel runs stage 1 over the
-// batch x mu* shifted sample sets (tile r: instance r / mu*, shift r mod mu*)
-// and writes, from the tile of shift a, only the values the class solves
-// read: G[b][i] = Y[b][a][t_i] for every coefficient i whose place in its
-// class is u_i = a. The workspace then holds k values per instance in output
+// GATHER (mu* > 1, the same tile shapes, k <= 8192): the kernel runs stage 1
+// over the batch x mu* shifted sample sets (row r: instance r / mu*, shift
+// r mod mu*) and writes, from the row of shift a, only the values the class
+// solves read: G[b][i] = Y[b][a][t_i] for every coefficient i whose place in
+// its class is u_i = a. The workspace then holds k values per instance in output
 // order instead of mu* x 2^R, and stage 2 (k_sas_decode, GATHERED) reads a
 // class's mu values side by side.
 template <class R>
@@ -362,7 +362,7 @@ struct SasFusedArgs {
   const uint16_t* col;                   // t_i: column of the stage-1 output
   const typename KT<R>::C* w;            // Winv_i (1 x 1 inverses)
   typename KT<R>::C* out;                // batch x k coefficients (GATHER: the batch x k workspace G)
-  uint64_t k, rows;                      // coefficients per instance; tiles = batch x mu*
+  uint64_t k, rows;                      // coefficients per instance; rows (virtual instances): batch x mu*
   const uint32_t* gtab;                  // GATHER: t_i | i << 16, grouped by u_i
   uint32_t mu_star;
   uint32_t goff[kSasMaxMu + 1];          // GATHER: entries of shift a are [goff[a], goff[a + 1])
