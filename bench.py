@@ -803,38 +803,40 @@ def run_serving(args):
     sys.setswitchinterval(0.0002)
     gc_was = gc.isenabled()
     gc.disable()
-    pt = th.Thread(target=poller, daemon=True)
-    pt.start()
-    start = time.perf_counter() + 0.05
-    for r in range(n_req):
-        t_arr = start + trace.arrivals[r]
-        arrival[r] = t_arr
-        while True:
-            now = time.perf_counter()
-            if now >= t_arr:
-                break
-            if t_arr - now > 0.0005:
-                time.sleep(t_arr - now - 0.0003)
-        pid = int(trace.plan_ids[r])
-        if pid < 256:
-            submit_t[r] = time.perf_counter()
-            N.sdft_server_submit(h, resident[pid].handle, res_in[pid].data_ptr(), res_out[pid].data_ptr(), r)
-        else:
-            inst = trace.plans[pid]
-            s_ = int(inst.s)
-            bi, bo = take(s_)
-            fresh_bufs[r] = (bi, bo)
-            fresh_s[r] = s_
-            submit_t[r] = time.perf_counter()
-            N.sdft_server_submit_support(h, inst.M, fresh_J[pid], bi.data_ptr(), bo.data_ptr(), r)
-    srv.drain(timeout_ms=600_000)
-    end = time.perf_counter()
-    deadline = end + 5.0
-    stop.set()
-    pt.join(timeout=10)
-    sys.setswitchinterval(switch)
-    if gc_was:
-        gc.enable()
+    try:
+        pt = th.Thread(target=poller, daemon=True)
+        pt.start()
+        start = time.perf_counter() + 0.05
+        for r in range(n_req):
+            t_arr = start + trace.arrivals[r]
+            arrival[r] = t_arr
+            while True:
+                now = time.perf_counter()
+                if now >= t_arr:
+                    break
+                if t_arr - now > 0.0005:
+                    time.sleep(t_arr - now - 0.0003)
+            pid = int(trace.plan_ids[r])
+            if pid < 256:
+                submit_t[r] = time.perf_counter()
+                N.sdft_server_submit(h, resident[pid].handle, res_in[pid].data_ptr(), res_out[pid].data_ptr(), r)
+            else:
+                inst = trace.plans[pid]
+                s_ = int(inst.s)
+                bi, bo = take(s_)
+                fresh_bufs[r] = (bi, bo)
+                fresh_s[r] = s_
+                submit_t[r] = time.perf_counter()
+                N.sdft_server_submit_support(h, inst.M, fresh_J[pid], bi.data_ptr(), bo.data_ptr(), r)
+        srv.drain(timeout_ms=600_000)
+        end = time.perf_counter()
+        deadline = end + 5.0
+        stop.set()
+        pt.join(timeout=10)
+    finally:
+        sys.setswitchinterval(switch)
+        if gc_was:
+            gc.enable()
     st = srv.stats()
     ok = status == 0
     ks = np.array([(resident[int(p)].k if p < 256 else (1 << trace.plans[int(p)].s)) for p in trace.plan_ids])
